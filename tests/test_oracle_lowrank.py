@@ -1,0 +1,66 @@
+"""Oracle pins for qr / svd / id (Secs. 2.2-2.4, 2.6)."""
+import numpy as np
+import pytest
+
+from oracle.lowrank import interp_decomp, pivoted_qr, qr_basis, svd_trunc
+
+
+def _lowrank(m, n, k, seed, decay=1e-3):
+    rng = np.random.default_rng(seed)
+    Q1, _ = np.linalg.qr(rng.standard_normal((m, min(m, n))))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, min(m, n))))
+    s = np.array([1.0 if i < k else decay ** (1 + i - k) for i in range(min(m, n))])
+    return (Q1 * s) @ Q2.T, s
+
+
+def test_qr_basis_orthonormal_and_spanning():
+    A, _ = _lowrank(50, 12, 12, 1)
+    Q = qr_basis(A)
+    assert np.allclose(Q.T @ Q, np.eye(12), atol=1e-14)
+    assert np.linalg.norm(A - Q @ (Q.T @ A)) < 1e-13
+
+
+def test_svd_eckart_young():
+    A, s = _lowrank(40, 30, 5, 2, decay=1e-2)
+    U, sv, Vt = svd_trunc(A, eps=1e-3)
+    # eps mode: keep sigma > eps -> 5 + 1 terms (1e-2 > 1e-3 > 1e-4)
+    assert sv.size == 6
+    assert abs(np.linalg.norm(A - (U * sv) @ Vt, 2) - s[6]) < 1e-12
+    U, sv, Vt = svd_trunc(A, k=3)
+    assert sv.size == 3
+    assert abs(np.linalg.norm(A - (U * sv) @ Vt, 2) - s[3]) < 1e-12
+
+
+def test_pivoted_qr_matches_lapack_diagonal():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((20, 35)) * np.logspace(0, -6, 35)[None, :]
+    R, perm, rdiag = pivoted_qr(A)
+    _, R2, perm2 = scipy_linalg.qr(A, pivoting=True, mode="economic")
+    assert np.allclose(rdiag, np.abs(np.diag(R2)), rtol=1e-10)
+    assert np.array_equal(perm[:20], perm2[:20])
+    Q = qr_basis(A[:, perm])
+    assert np.allclose(np.abs(Q.T @ A[:, perm]), np.abs(R), atol=1e-12)
+
+
+def test_interp_decomp_properties():
+    A, s = _lowrank(30, 60, 7, 4, decay=1e-4)
+    J, T = interp_decomp(A, eps=1e-2)
+    k = J.size
+    assert k == 7
+    assert np.allclose(T[:, J], np.eye(k), atol=1e-14)
+    assert np.max(np.abs(T)) <= 2.0
+    err = np.linalg.norm(A - A[:, J] @ T, 2)
+    assert err <= np.sqrt(1 + k * (60 - k)) * 10 * s[7]
+    J2, T2 = interp_decomp(A, k=3)
+    assert J2.size == 3 and T2.shape == (3, 60)
+
+
+def test_interp_decomp_brute_force_tiny():
+    # rank-2 4x6 matrix: columns 0 and 3 span, ID must reproduce exactly
+    a = np.array([1.0, 2.0, 0.0, -1.0])
+    b = np.array([0.0, 1.0, 1.0, 3.0])
+    A = np.stack([a, 2 * a, a + b, b, -b, 3 * a - 2 * b], axis=1)
+    J, T = interp_decomp(A, eps=1e-12)
+    assert J.size == 2
+    assert np.allclose(A[:, J] @ T, A, atol=1e-13)
