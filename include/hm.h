@@ -1,0 +1,297 @@
+/*
+ * hm.h - C ABI of the GB300 library for randomized compression of
+ * rank-structured matrices (Martinsson, "Compressing rank-structured matrices
+ * via randomized sampling", arXiv:1503.07152).
+ *
+ * The library sees the N x N operator A only through a black box that applies
+ * A or A^T to a block of vectors (Sec. 1; Sec. 3: "black-box matrix-matrix
+ * multiplier"; Sec. 5.3: the black box acts on N x l blocks), and returns a
+ * HODLR (Sec. 2.8, Sec. 3) or HBS / HBS-ID (Secs. 2.9, 4) representation that
+ * can be applied, transposed and read back block by block.
+ *
+ * Conventions for every entry point:
+ *  - Matrices of vectors (X, Y, sample blocks) are column-major with a leading
+ *    dimension ld >= rows; element (i, j) is at ptr[i + j * ld].
+ *  - Dense operators handed to hm_dense_operator_create are row-major:
+ *    element (i, j) is at A[i * lda + j].
+ *  - "device pointer" means memory of the current CUDA device; "host pointer"
+ *    means ordinary (pageable or pinned) host memory.
+ *  - Element type follows the precision of the call: HM_FP64 -> double,
+ *    HM_MIXED -> float.
+ *  - Work is enqueued on the caller's stream (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  Unless stated otherwise a call returns
+ *    after enqueueing (asynchronous); the compress calls synchronize the stream
+ *    once at their end to read device-side status flags.
+ *  - Every entry point returns an hm_status.  On failure nothing is returned
+ *    through output handles (no partial handles), and hm_last_error() gives a
+ *    thread-local message describing the first error of the failing call.
+ */
+#ifndef HM_H_
+#define HM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HM_OK = 0,
+  HM_EINVAL = 1,           /* bad argument (null pointer, size, ld, mode) */
+  HM_ENOMEM = 2,           /* device or host allocation failed */
+  HM_ECUDA = 3,            /* a CUDA runtime call or kernel launch failed */
+  HM_ECALLBACK = 4,        /* the black-box apply returned non-zero */
+  HM_ERANK_SATURATED = 5,  /* strict mode only: an adaptive rank reached r */
+  HM_ENONFINITE = 6,       /* NaN/Inf detected in the samples */
+  HM_ETIMEOUT = 7,         /* a bounded device-side wait gave up */
+  HM_EUNSUPPORTED = 8      /* valid request outside what this build supports */
+} hm_status;
+
+typedef enum { HM_FP64 = 0, HM_MIXED = 1 } hm_precision;
+typedef enum { HM_FORMAT_HODLR = 0, HM_FORMAT_HBS = 1, HM_FORMAT_HBSID = 2 } hm_format;
+
+/*
+ * Black box (Sec. 1, T_mult; Fig. "Randomized compression of a HODLR matrix":
+ * the products A*Omega and A^*Omega).  Computes Y(0:n, 0:ncols) = op(A) X with
+ * op = A (trans = 0) or A^T (trans = 1).  X and Y are device pointers,
+ * column-major, element type double (HM_FP64) or float (HM_MIXED).  The
+ * callback must enqueue its work on `stream` (a cudaStream_t) and return 0; any
+ * other value aborts the compression with HM_ECALLBACK.  X is read-only and is
+ * not retained after the call returns.
+ */
+typedef int (*hm_apply_fn)(void* ctx, int trans, int64_t n, int64_t ncols,
+                           const void* X, int64_t ldx, void* Y, int64_t ldy,
+                           void* stream);
+
+typedef struct {
+  hm_apply_fn apply;  /* required */
+  void* ctx;          /* passed through unchanged; owned by the caller */
+  int64_t n;          /* operator size N */
+} hm_operator;
+
+/*
+ * Compression options.  Mode 2 / mode 3 of Sec. 2.6: fixed rank k
+ * (mode_tol = 0) or tolerance tol (mode_tol = 1).  r = k + p random vectors
+ * per level (p: oversampling, Sec. 2.5, default 10).  In tolerance mode r is
+ * given directly by `r` (must be > 0).  leaf_size: the tree's m (Sec. 2.7).
+ * seed: key of the Philox4x32-10 test matrices.  prec: HM_FP64 or HM_MIXED.
+ * hbs_id: for hm_compress_hbs, 1 converts to HBS-ID with adaptive ranks
+ * (Sec. 4.3), 0 keeps the fixed-rank HBS form.  strict_rank: 1 makes a
+ * saturated adaptive rank an error (HM_ERANK_SATURATED) instead of a counter
+ * in hm_info.
+ */
+typedef struct {
+  int32_t mode_tol;
+  int32_t k;
+  double tol;
+  int32_t p;
+  int32_t r;
+  int32_t leaf_size;
+  uint64_t seed;
+  int32_t prec;
+  int32_t hbs_id;
+  int32_t strict_rank;
+} hm_opts;
+
+typedef struct hm_tree hm_tree;
+typedef struct hm_handle hm_handle;
+
+typedef struct {
+  int32_t format;          /* hm_format */
+  int32_t prec;            /* hm_precision */
+  int64_t n;
+  int32_t levels;          /* L */
+  int32_t r;               /* random vectors per level and side */
+  int32_t max_rank;        /* largest rank kept in any block */
+  int32_t min_rank;
+  int32_t saturated;       /* number of blocks whose adaptive rank hit r */
+  int64_t cols_A;          /* black-box columns applied with A */
+  int64_t cols_At;         /* black-box columns applied with A^T */
+  int64_t bytes;           /* device bytes held by the representation (M) */
+  double eps_abs;          /* absolute truncation threshold used (mode 3) */
+  double t_compress_ms;    /* wall time of the compress call */
+  double t_blackbox_ms;    /* time inside the black box (T_compress - T_net) */
+  int32_t launches;        /* kernels launched by the last compress call */
+} hm_info_t;
+
+/* ---------------------------------------------------------------- tree --- */
+
+/*
+ * Binary tree over [0, n) (Sec. 2.7, Fig. 1): uniform depth
+ * L = ceil(log2(n / leaf_size)), a node of size s splits into floor(s/2)
+ * (left) and s - floor(s/2) (right); heap numbering, root = 1.  Host-side
+ * object (plus a small device copy of the node table); owned by the caller.
+ */
+hm_status hm_tree_create(int64_t n, int32_t leaf_size, hm_tree** out);
+void hm_tree_destroy(hm_tree* t);
+/* Levels below the root (L). */
+int32_t hm_tree_levels(const hm_tree* t);
+/* Index range [start, start + size) of heap node `node` (1 <= node < 2^(L+1)). */
+hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* size);
+
+/* --------------------------------------------------------- black boxes --- */
+
+/*
+ * Dense test operator: wraps a row-major N x N device matrix A (lda >= N;
+ * dtype 0 = double, 1 = float) as a black box whose apply is the library's
+ * sampling GEMM.  The matrix is NOT copied or owned: it must outlive the
+ * operator.  A float matrix serves HM_MIXED compressions (samples in float);
+ * a double matrix serves HM_FP64.  The returned operator's ctx is released by
+ * hm_dense_operator_destroy.
+ */
+hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,
+                                   hm_operator* out);
+void hm_dense_operator_destroy(hm_operator* op);
+
+/*
+ * The sampling GEMM behind the dense operator, callable directly:
+ * Y = op(A) X for the row-major dense A above.  Same argument rules as
+ * hm_apply_fn.  Returns HM_OK or an error status.
+ */
+hm_status hm_dense_apply(const hm_operator* op, int trans, int64_t ncols, const void* X,
+                         int64_t ldx, void* Y, int64_t ldy, void* stream);
+
+/*
+ * The level-`level` test matrix X = [Omega_2 | Omega_1] (n x 2r, column-major,
+ * device, ldx >= n) of the compression sweeps (Fig. "Randomized compression of
+ * a HODLR matrix": Omega_1 = randn on the left child of every parent on
+ * `level`, Omega_2 = randn on the right child; both zero elsewhere).  Entry
+ * (i, c) of the level's Gaussian field is Philox4x32-10 (key = seed, counter =
+ * (i, c / 2, level, 0)) followed by Box-Muller in FP64; HM_MIXED rounds it to
+ * FP32 and then to BF16 (round to nearest even) and stores float, HM_FP64
+ * stores double.  Right children get columns [0, r), left children [r, 2r).
+ */
+hm_status hm_gaussian_test_matrix(const hm_tree* tree, int32_t level, int32_t r, uint64_t seed,
+                                  int32_t prec, void* X, int64_t ldx, void* stream);
+
+/* ---------------------------------------------------------- compression --- */
+
+/*
+ * HODLR compression by randomized peeling (Sec. 3, Fig. "Randomized
+ * compression of a HODLR matrix", diagonal-B variant of Remark 4).  op->n must
+ * equal the tree's n.  On success *out owns all device memory of the
+ * representation.  Synchronizes `stream` once at the end.
+ */
+hm_status hm_compress_hodlr(const hm_operator* op, const hm_tree* tree, const hm_opts* opts,
+                            void* stream, hm_handle** out);
+
+/*
+ * HBS compression with nested bases (Sec. 4.2, Fig. "A storage efficient
+ * algorithm for compressing an HBS matrix"), followed when opts->hbs_id = 1 by
+ * the upward sweep that converts it to HBS-ID with adaptive ranks (Sec. 4.3,
+ * Fig. "An algorithm for computing the HBS-ID representation").  Every leaf
+ * must hold at least r indices.  Synchronizes `stream` once at the end.
+ */
+hm_status hm_compress_hbs(const hm_operator* op, const hm_tree* tree, const hm_opts* opts,
+                          void* stream, hm_handle** out);
+
+/* ---------------------------------------------------------- using it ----- */
+
+/*
+ * Y = A_c X (trans = 0) or A_c^T X (trans = 1) for the compressed A_c: the
+ * HODLR product of Sec. 2.8 (block diagonal plus every sibling block), or the
+ * HBS / HBS-ID product of Fig. "Application of A^(m) in the HBS framework"
+ * with m = L plus the leaf blocks.  X, Y: device, column-major, n x ncols,
+ * element type of the handle's precision.  X and Y must not overlap.
+ */
+hm_status hm_apply(const hm_handle* h, int trans, int64_t ncols, const void* X, int64_t ldx,
+                   void* Y, int64_t ldy, void* stream);
+
+/*
+ * Same product with HOST buffers: copies X to the device, applies, copies Y
+ * back, and synchronizes the stream before returning.  Scratch is allocated
+ * and released inside the call.
+ */
+hm_status hm_apply_host(const hm_handle* h, int trans, int64_t ncols, const void* X_host,
+                        int64_t ldx, void* Y_host, int64_t ldy, void* stream);
+
+/*
+ * Dense block A_c(r0:r1, c0:c1) of the compressed matrix written to `out`
+ * (device, column-major, ld >= r1 - r0, handle's element type).
+ * 0 <= r0 <= r1 <= n, 0 <= c0 <= c1 <= n.
+ */
+hm_status hm_reconstruct_block(const hm_handle* h, int64_t r0, int64_t r1, int64_t c0,
+                               int64_t c1, void* out, int64_t ld, void* stream);
+
+/*
+ * ||A - A_c||_F / ||A||_F for a dense row-major device matrix A (dtype 0 =
+ * double, 1 = float), streamed tile by tile with FP64 accumulation (Sec. 5
+ * error measure; no N x N scratch).  Writes the result to *err (host) and
+ * synchronizes the stream.
+ */
+hm_status hm_rel_frob_error(const hm_handle* h, const void* A, int64_t lda, int32_t dtype,
+                            double* err, void* stream);
+
+/*
+ * Copies the HODLR factors of node level `level` (1..L): U gets U_a B_ab for
+ * every node a of the level (the sibling matrix absorbed into the column
+ * basis), V gets V_a; both n x r, column-major (ld n), rows I_a of node a,
+ * columns past the block's rank zero.  A_c(I_a, I_b) = U(I_a,:) V(I_b,:)^T for
+ * siblings a, b (Sec. 2.8).  Device buffers of the handle's element type.
+ */
+hm_status hm_hodlr_export_level(const hm_handle* h, int32_t level, void* U, void* V,
+                                void* stream);
+
+/* Summary of the representation (ranks, black-box column counts, bytes M). */
+hm_status hm_info(const hm_handle* h, hm_info_t* out);
+/* Rank of the sibling block (node, node ^ 1) (HODLR) or of node's basis (HBS,
+ * HBS-ID incoming skeleton).  Synchronous small read. */
+hm_status hm_node_rank(const hm_handle* h, int64_t node, int32_t* rank);
+void hm_destroy(hm_handle* h);
+
+/* ------------------------------------------- factored HODLR and adjoint --- */
+
+/*
+ * Factored HODLR apply with explicit factors (the HODLR product of Sec. 2.8
+ * with sibling matrices B = I): for every level j = 1..L and sibling pair
+ * (a, b) on level j, y(I_a) += U_j(I_a, :) (V_j(I_b, :)^T x(I_b)), plus
+ * y(I_t) += D_t x(I_t) for every leaf t.
+ *  U, V: device float, L blocks of N x k, column-major each (ld N), level j
+ *        at offset (j - 1) * N * k.
+ *  D:    device float, one n_max x n_max column-major block per leaf
+ *        (ld n_max, entries beyond the leaf size are ignored).
+ *  x, y: device float vectors of length N (y is overwritten).
+ * trans = 1 applies H^T.  1 <= k <= 64.  Stream-ordered scratch as for the
+ * adjoint below.
+ */
+hm_status hm_hodlr_factored_apply(const hm_tree* tree, int32_t k, const float* U,
+                                  const float* V, const float* D, int trans, const float* x,
+                                  float* y, void* stream);
+
+/*
+ * Hand-written adjoint (vector-Jacobian product) of y = H x at the factors
+ * above.  Given r (device, length N), writes
+ *   gx = scale * H^T r,            gU_j(I_a) = scale * r(I_a) (V_j(I_b)^T x(I_b))^T,
+ *   gV_j(I_b) = scale * x(I_b) (U_j(I_a)^T r(I_a))^T,   gD_t = scale * r(I_t) x(I_t)^T
+ * (same layouts as x, U, V, D; outputs are overwritten; any output may be NULL
+ * to skip it; gD entries beyond a leaf's size are written as zero).  With
+ * r = H x - b and scale = 2 these are the gradients of ||H x - b||^2.
+ * Stream-ordered scratch of O(k * (N / 256 * L + 2^(L+1))) floats is taken
+ * from the CUDA memory pool of the stream's device and released in order.
+ */
+hm_status hm_hodlr_factored_adjoint(const hm_tree* tree, int32_t k, const float* U,
+                                    const float* V, const float* D, const float* x,
+                                    const float* r, float scale, float* gx, float* gU,
+                                    float* gV, float* gD, void* stream);
+
+/* ------------------------------------------------------ workload helpers --- */
+
+/*
+ * Writes the FP32 log-kernel test operator: points x_i = (cos t_i, 0.5 sin t_i),
+ * t_i = 2 pi i / n; A(i, j) = log |x_i - x_j| (FP64, rounded once to FP32),
+ * A(i, i) = 1.  Row-major, device, lda >= n.  An input generator, not part of
+ * the compression method.
+ */
+hm_status hm_gen_log_kernel(float* A, int64_t n, int64_t lda, void* stream);
+
+/* Thread-local description of the last error ("" if none). */
+const char* hm_last_error(void);
+/* Library version string. */
+const char* hm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HM_H_ */

@@ -1,0 +1,17 @@
+"""GB300 (sm_103a) randomized compression of rank-structured matrices.
+
+Thin Python binding over the C ABI in ``include/hm.h`` (``libhm.so``, built
+in-tree by ``paper_1503_07152_gb300.build``).  Every step of the compression,
+apply and adjoint runs in the library's CUDA kernels; this module only
+marshals arguments (PyTorch tensors provide device memory and streams).
+Importing this package loads ``libhm.so`` and fails loudly if it is missing:
+there is no CPU fallback.
+"""
+from ._lib import (  # noqa: F401
+    HM_FP64, HM_MIXED, HM_FORMAT_HODLR, HM_FORMAT_HBS, HM_FORMAT_HBSID, HmError, Opts, Tree,
+    Operator, Handle, lib, library_path, hm_tree_create, hm_dense_operator_create,
+    hm_dense_apply, hm_compress_hodlr, hm_compress_hbs, hm_apply, hm_apply_host,
+    hm_reconstruct_block, hm_rel_frob_error, hm_info, hm_node_rank, hm_hodlr_factored_apply,
+    hm_hodlr_factored_adjoint, hm_gen_log_kernel, hm_gaussian_test_matrix, hm_hodlr_export_level, hm_version, callback_operator,
+)
+from .autograd import HodlrApply  # noqa: F401

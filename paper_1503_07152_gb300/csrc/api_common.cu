@@ -1,0 +1,396 @@
+// Host side shared by the entry points: error state, tree construction and the
+// per-level work plans (row chunks, TSQR merge schedules) uploaded once per tree,
+// the dense black box, and a small device workspace helper.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "hm_api.h"
+
+namespace hm {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) {
+  if (g_err.empty()) g_err = msg;
+}
+const char* get_error() { return g_err.c_str(); }
+void clear_error() { g_err.clear(); }
+
+hm_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return HM_ECUDA;
+  }
+  return HM_OK;
+}
+
+// ------------------------------------------------------------ workspace ----
+hm_status Workspace::reserve(size_t bytes, cudaStream_t st) {
+  (void)st;
+  if (bytes <= cap) return HM_OK;
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc(&ptr, bytes);
+  if (e != cudaSuccess) {
+    set_error(std::string("workspace allocation of ") + std::to_string(bytes) + " bytes: " +
+              cudaGetErrorString(e));
+    return HM_ENOMEM;
+  }
+  cap = bytes;
+  return HM_OK;
+}
+Workspace::~Workspace() {
+  if (ptr) cudaFree(ptr);
+}
+
+hm_status device_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return HM_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " +
+              cudaGetErrorString(e));
+    return HM_ENOMEM;
+  }
+  return HM_OK;
+}
+
+// ----------------------------------------------------------------- plans ----
+static void build_chunks(const hm_tree* t, int lv, int64_t maxrows, std::vector<Chunk>& out,
+                         std::vector<int32_t>* begin) {
+  const int n0 = 1 << lv, n1 = 1 << (lv + 1);
+  if (begin) begin->clear();
+  for (int node = n0; node < n1; ++node) {
+    if (begin) begin->push_back((int32_t)out.size());
+    const int64_t s = t->start[node], e = s + t->size[node];
+    for (int64_t r = s; r < e; r += maxrows) {
+      Chunk c;
+      c.node = node;
+      c.pad = 0;
+      c.r0 = r;
+      c.r1 = std::min(e, r + maxrows);
+      out.push_back(c);
+    }
+  }
+  if (begin) begin->push_back((int32_t)out.size());
+}
+
+static void build_tsqr(const hm_tree* t, int lv, int64_t brows, LevelPlan& lp) {
+  const int n0 = 1 << lv, n1 = 1 << (lv + 1);
+  std::vector<std::vector<int32_t>> cur(n1 - n0);
+  std::vector<TsqrTask> round0;
+  int32_t next_slot = 0;
+  for (int node = n0; node < n1; ++node) {
+    const int64_t s = t->start[node], e = s + t->size[node];
+    for (int64_t r = s; r < e; r += brows) {
+      TsqrTask tk;
+      std::memset(&tk, 0, sizeof(tk));
+      tk.node = node;
+      tk.nsrc = 1;
+      tk.kind[0] = 0;
+      tk.r0[0] = r;
+      tk.r1[0] = std::min(e, r + brows);
+      tk.out_slot = next_slot++;
+      cur[node - n0].push_back(tk.out_slot);
+      round0.push_back(tk);
+    }
+  }
+  lp.tsqr_rounds.clear();
+  lp.tsqr_rounds.push_back(round0);
+  for (;;) {
+    std::vector<TsqrTask> rnd;
+    bool any = false;
+    for (int i = 0; i < n1 - n0; ++i) {
+      auto& v = cur[i];
+      if (v.size() <= 1) continue;
+      any = true;
+      std::vector<int32_t> nv;
+      for (size_t j = 0; j + 1 < v.size(); j += 2) {
+        TsqrTask tk;
+        std::memset(&tk, 0, sizeof(tk));
+        tk.node = n0 + i;
+        tk.nsrc = 2;
+        tk.kind[0] = tk.kind[1] = 1;
+        tk.slot[0] = v[j];
+        tk.slot[1] = v[j + 1];
+        tk.out_slot = next_slot++;
+        nv.push_back(tk.out_slot);
+        rnd.push_back(tk);
+      }
+      if (v.size() % 2) nv.push_back(v.back());
+      v.swap(nv);
+    }
+    if (!any) break;
+    lp.tsqr_rounds.push_back(rnd);
+  }
+  lp.final_slot.resize(n1 - n0);
+  for (int i = 0; i < n1 - n0; ++i) lp.final_slot[i] = cur[i][0];
+  lp.nslots = next_slot;
+}
+
+}  // namespace hm
+
+using namespace hm;
+
+hm_status tree_build(int64_t n, int32_t leaf, hm_tree* t) {
+  t->n = n;
+  t->leaf = leaf;
+  int L = 0;
+  while ((n + ((int64_t)1 << L) - 1) / ((int64_t)1 << L) > leaf) ++L;
+  if (L > 24) {
+    set_error("tree too deep");
+    return HM_EINVAL;
+  }
+  t->L = L;
+  const int64_t nn = (int64_t)1 << (L + 1);
+  t->start.assign(nn, 0);
+  t->size.assign(nn, 0);
+  t->size[1] = n;
+  for (int64_t tau = 1; tau < ((int64_t)1 << L); ++tau) {
+    const int64_t s = t->size[tau];
+    t->start[2 * tau] = t->start[tau];
+    t->size[2 * tau] = s / 2;
+    t->start[2 * tau + 1] = t->start[tau] + s / 2;
+    t->size[2 * tau + 1] = s - s / 2;
+  }
+  t->nmax = 0;
+  for (int64_t x = (int64_t)1 << L; x < nn; ++x) t->nmax = std::max(t->nmax, t->size[x]);
+  return HM_OK;
+}
+
+void tree_free(hm_tree* t) {
+  if (t->fdev) cudaFree(t->fdev);
+  t->fdev = nullptr;
+  if (t->d_start) cudaFree(t->d_start);
+  if (t->d_size) cudaFree(t->d_size);
+  for (auto& lp : t->plans) {
+    if (lp.dev) cudaFree(lp.dev);
+    lp.dev = nullptr;
+  }
+  t->plans.clear();
+  t->d_start = t->d_size = nullptr;
+}
+
+static void fact_plan_host(hm_tree* t) {
+  t->fchunks.clear();
+  const int64_t nn = (int64_t)1 << (t->L + 1);
+  t->fbegin.assign(nn + 1, 0);
+  for (int64_t node = 2; node < nn; ++node) {
+    t->fbegin[node] = (int32_t)t->fchunks.size();
+    int lv = 0;
+    while (((int64_t)1 << (lv + 1)) <= node) ++lv;
+    const int64_t s = t->start[node], e = s + t->size[node];
+    for (int64_t r = s; r < e; r += 256) {
+      FactChunk c;
+      c.level = lv;
+      c.node = (int32_t)node;
+      c.r0 = r;
+      c.r1 = std::min(e, r + 256);
+      t->fchunks.push_back(c);
+    }
+  }
+  t->fbegin[nn] = (int32_t)t->fchunks.size();
+  t->n_fchunks = (int)t->fchunks.size();
+}
+
+hm_status tree_plans(hm_tree* t) {
+  if (!t->plans.empty()) return HM_OK;
+  if (t->L >= 1) fact_plan_host(t);
+  t->plans.resize(t->L + 1);
+  for (int lv = 1; lv <= t->L; ++lv) {
+    LevelPlan& lp = t->plans[lv];
+    lp.nnodes = 1 << lv;
+    lp.node0 = 1 << lv;
+    build_chunks(t, lv, 256, lp.tn, &lp.tn_begin);
+    build_chunks(t, lv, 64, lp.nn, nullptr);
+    build_tsqr(t, lv, 128, lp);
+    lp.n_tn = (int)lp.tn.size();
+    lp.n_nn = (int)lp.nn.size();
+  }
+  return HM_OK;
+}
+
+// Uploads the node table and the level plans on first use (needs a device).
+hm_status tree_device(hm_tree* t) {
+  if (t->d_start) return HM_OK;
+  const int64_t nn = (int64_t)1 << (t->L + 1);
+  HM_TRY(tree_plans(t));
+  auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  int64_t* ds = nullptr;
+  int64_t* dz = nullptr;
+  HM_TRY(device_alloc((void**)&ds, nn * sizeof(int64_t)));
+  HM_TRY(device_alloc((void**)&dz, nn * sizeof(int64_t)));
+  HM_CUDA_TRY(cudaMemcpy(ds, t->start.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice));
+  HM_CUDA_TRY(cudaMemcpy(dz, t->size.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice));
+  t->d_size = dz;
+  if (t->L >= 1) {
+    const size_t b0 = align(t->fchunks.size() * sizeof(FactChunk));
+    const size_t bytes = b0 + t->fbegin.size() * sizeof(int32_t);
+    HM_TRY(device_alloc(&t->fdev, bytes));
+    HM_CUDA_TRY(cudaMemcpy(t->fdev, t->fchunks.data(), t->fchunks.size() * sizeof(FactChunk),
+                           cudaMemcpyHostToDevice));
+    HM_CUDA_TRY(cudaMemcpy((unsigned char*)t->fdev + b0, t->fbegin.data(),
+                           t->fbegin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    t->d_fchunks = (const FactChunk*)t->fdev;
+    t->d_fbegin = (const int32_t*)((unsigned char*)t->fdev + b0);
+  }
+  for (int lv = 1; lv <= t->L; ++lv) {
+    LevelPlan& lp = t->plans[lv];
+    size_t bytes = 0;
+    const size_t o_tn = bytes; bytes = align(bytes + lp.tn.size() * sizeof(Chunk));
+    const size_t o_tnb = bytes; bytes = align(bytes + lp.tn_begin.size() * sizeof(int32_t));
+    const size_t o_nn = bytes; bytes = align(bytes + lp.nn.size() * sizeof(Chunk));
+    std::vector<size_t> o_rounds;
+    for (auto& r : lp.tsqr_rounds) {
+      o_rounds.push_back(bytes);
+      bytes = align(bytes + r.size() * sizeof(TsqrTask));
+    }
+    const size_t o_fs = bytes; bytes = align(bytes + lp.final_slot.size() * sizeof(int32_t));
+    HM_TRY(device_alloc(&lp.dev, bytes));
+    std::vector<unsigned char> host(bytes, 0);
+    std::memcpy(host.data() + o_tn, lp.tn.data(), lp.tn.size() * sizeof(Chunk));
+    std::memcpy(host.data() + o_tnb, lp.tn_begin.data(), lp.tn_begin.size() * sizeof(int32_t));
+    std::memcpy(host.data() + o_nn, lp.nn.data(), lp.nn.size() * sizeof(Chunk));
+    for (size_t i = 0; i < lp.tsqr_rounds.size(); ++i)
+      std::memcpy(host.data() + o_rounds[i], lp.tsqr_rounds[i].data(),
+                  lp.tsqr_rounds[i].size() * sizeof(TsqrTask));
+    std::memcpy(host.data() + o_fs, lp.final_slot.data(), lp.final_slot.size() * sizeof(int32_t));
+    HM_CUDA_TRY(cudaMemcpy(lp.dev, host.data(), bytes, cudaMemcpyHostToDevice));
+    auto base = (unsigned char*)lp.dev;
+    lp.d_tn = (const Chunk*)(base + o_tn);
+    lp.d_tn_begin = (const int32_t*)(base + o_tnb);
+    lp.d_nn = (const Chunk*)(base + o_nn);
+    lp.d_rounds.clear();
+    for (size_t i = 0; i < lp.tsqr_rounds.size(); ++i)
+      lp.d_rounds.push_back((const TsqrTask*)(base + o_rounds[i]));
+    lp.d_final_slot = (const int32_t*)(base + o_fs);
+  }
+  t->d_start = ds;  // set last: marks the upload complete
+  return HM_OK;
+}
+
+extern "C" {
+
+const char* hm_last_error(void) { return get_error(); }
+const char* hm_version(void) { return "hm 0.1 (sm_103a)"; }
+
+hm_status hm_tree_create(int64_t n, int32_t leaf_size, hm_tree** out) {
+  clear_error();
+  if (!out || n < 1 || leaf_size < 1) {
+    set_error("hm_tree_create: need n >= 1, leaf_size >= 1 and a non-null out");
+    return HM_EINVAL;
+  }
+  *out = nullptr;
+  hm_tree* t = new hm_tree();
+  hm_status s = tree_build(n, leaf_size, t);
+  if (s == HM_OK) s = tree_plans(t);
+  if (s != HM_OK) {
+    tree_free(t);
+    delete t;
+    return s;
+  }
+  *out = t;
+  return HM_OK;
+}
+
+void hm_tree_destroy(hm_tree* t) {
+  if (!t) return;
+  tree_free(t);
+  delete t;
+}
+
+int32_t hm_tree_levels(const hm_tree* t) { return t ? t->L : -1; }
+
+hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* size) {
+  clear_error();
+  if (!t || !start || !size || node < 1 || node >= ((int64_t)1 << (t->L + 1))) {
+    set_error("hm_tree_node: bad tree, node or output pointer");
+    return HM_EINVAL;
+  }
+  *start = t->start[node];
+  *size = t->size[node];
+  return HM_OK;
+}
+
+// ---------------------------------------------------------- dense box ------
+static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* X, int64_t ldx,
+                    void* Y, int64_t ldy, void* stream) {
+  hm_dense_ctx* d = (hm_dense_ctx*)ctx;
+  if (!d || n != d->n || ncols < 0) return 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int64_t c0 = 0; c0 < ncols; c0 += 1024) {
+    const int64_t w = std::min<int64_t>(1024, ncols - c0);
+    if (d->dtype == 0)
+      launch_dense_gemm<double>((const double*)d->A, d->lda, trans, n, w,
+                                (const double*)X + c0 * ldx, ldx, (double*)Y + c0 * ldy, ldy,
+                                d->flags, st);
+    else
+      launch_dense_gemm<float>((const float*)d->A, d->lda, trans, n, w,
+                               (const float*)X + c0 * ldx, ldx, (float*)Y + c0 * ldy, ldy,
+                               d->flags, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,
+                                   hm_operator* out) {
+  clear_error();
+  if (!A || !out || n < 1 || lda < n || (dtype != 0 && dtype != 1)) {
+    set_error("hm_dense_operator_create: need A, out, n >= 1, lda >= n, dtype 0|1");
+    return HM_EINVAL;
+  }
+  hm_dense_ctx* d = new hm_dense_ctx();
+  d->A = A;
+  d->n = n;
+  d->lda = lda;
+  d->dtype = dtype;
+  d->flags_bytes = dense_flags_bytes(n, 1024, dtype == 0);
+  hm_status s = device_alloc((void**)&d->flags, (size_t)d->flags_bytes);
+  if (s != HM_OK) {
+    delete d;
+    return s;
+  }
+  out->apply = dense_cb;
+  out->ctx = d;
+  out->n = n;
+  return HM_OK;
+}
+
+void hm_dense_operator_destroy(hm_operator* op) {
+  if (!op || !op->ctx) return;
+  hm_dense_ctx* d = (hm_dense_ctx*)op->ctx;
+  if (d->flags) cudaFree(d->flags);
+  delete d;
+  op->ctx = nullptr;
+  op->apply = nullptr;
+}
+
+hm_status hm_dense_apply(const hm_operator* op, int trans, int64_t ncols, const void* X,
+                         int64_t ldx, void* Y, int64_t ldy, void* stream) {
+  clear_error();
+  if (!op || !op->ctx || op->apply != dense_cb || !X || !Y || ncols < 0 || ldx < op->n ||
+      ldy < op->n || (trans != 0 && trans != 1)) {
+    set_error("hm_dense_apply: need a dense operator, X, Y, ncols >= 0, ld >= n, trans 0|1");
+    return HM_EINVAL;
+  }
+  if (dense_cb(op->ctx, trans, op->n, ncols, X, ldx, Y, ldy, stream) != 0) {
+    return check_launch("hm_dense_apply") == HM_OK ? HM_ECUDA : HM_ECUDA;
+  }
+  return HM_OK;
+}
+
+hm_status hm_gen_log_kernel(float* A, int64_t n, int64_t lda, void* stream) {
+  clear_error();
+  if (!A || n < 1 || lda < n) {
+    set_error("hm_gen_log_kernel: need A, n >= 1, lda >= n");
+    return HM_EINVAL;
+  }
+  launch_gen_log_kernel(A, n, lda, (cudaStream_t)stream);
+  return check_launch("hm_gen_log_kernel");
+}
+
+}  // extern "C"

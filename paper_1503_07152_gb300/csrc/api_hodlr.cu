@@ -1,0 +1,428 @@
+// HODLR compression (Sec. 3, Fig. "Randomized compression of a HODLR matrix")
+// and the operations on a compressed handle (apply, transpose apply, block
+// reconstruction, Frobenius error, info).
+//
+// Level l (parents on l, children on l + 1):
+//   X = [Omega_2 | Omega_1]                         (Gaussian, Philox)
+//   S(:, 0:r) = A Omega_2, S(:, r:2r) = A Omega_1   (two black-box calls, Y_1, Y_2)
+//   S -= A^(l) X                                    (peel, levels 1..l)
+//   U_child = orth(S(I_child, sample half))         (TSQR + Jacobi + CholQR)
+//   X' = [0 U_beta | U_alpha 0]; S = A^T X' - (A^(l))^T X'
+//   [V_alpha, B, \hat U_beta] = svd(S(I_alpha, sample half), k | eps)
+//   U_beta <- U_beta \hat U_beta B  (the sibling matrix is absorbed into U)
+// then the identity probe gives the leaf blocks D.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hm_api.h"
+#include "hm_hodlr.h"
+
+using namespace hm;
+
+namespace hm {
+
+constexpr double kEpsScale = 0.1;  // eps_abs = 0.1 * tol * nu (tolerance reading)
+
+template <typename T>
+hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c.st);
+  const int rc = c.op->apply(c.op->ctx, trans, c.N, ncols, X, c.N, Y, c.N, c.st);
+  cudaEventRecord(e1, c.st);
+  c.box_events.push_back({e0, e1});
+  if (rc != 0) {
+    set_error("black-box apply returned " + std::to_string(rc));
+    return HM_ECALLBACK;
+  }
+  if (trans) c.cols_At += ncols; else c.cols_A += ncols;
+  ++c.launches;
+  return check_launch("black-box apply");
+}
+
+// S(:, 0:ncols) -= A^(level) X (or the transpose), node levels 1..level.
+template <typename T>
+hm_status hodlr_peel(Ctx<T>& c, const T* U, const T* V, int level, const T* X, T* S,
+                     int64_t ncols, int trans, double sign) {
+  const int64_t N = c.N;
+  const int r = c.r;
+  for (int j = 1; j <= level; ++j) {
+    const LevelPlan& lp = c.tree->plans[j];
+    const T* Uj = U + (int64_t)(j - 1) * N * r;
+    const T* Vj = V + (int64_t)(j - 1) * N * r;
+    const T* Proj = trans ? Uj : Vj;  // projected on the source rows
+    const T* Expd = trans ? Vj : Uj;  // expanded on the target rows
+    for (int64_t cb = 0; cb < ncols; cb += 128) {
+      const int w = (int)std::min<int64_t>(128, ncols - cb);
+      launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Proj, N, 0, 0, r,
+                       X + cb * N, N, 0, 0, w, c.partial, c.coef, c.st);
+      launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Expd, N, 0, 0, r, c.coef, (int64_t)r * w, r,
+                       1, S + cb * N, N, 0, 0, w, (T)sign, (T)1, c.st);
+      c.launches += 3;
+    }
+  }
+  return check_launch("peel");
+}
+
+// Orthonormal basis / truncated SVD of the panel P (N x pc) per node of level lv.
+// Writes Q (N x r) and, when want_m, the coefficients M (pc x r per node).
+template <typename T>
+hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
+                    T* Q, bool want_m, int32_t* rank_lv) {
+  const LevelPlan& lp = c.tree->plans[lv];
+  const int64_t N = c.N;
+  const int r = c.r;
+  const int rows_max = std::max(128, 2 * pc);
+  if ((size_t)rows_max * pc * sizeof(T) > 220 * 1024 || (size_t)2 * pc * pc * sizeof(T) > 220 * 1024) {
+    set_error("panel too wide for the shared-memory QR in this precision");
+    return HM_EUNSUPPORTED;
+  }
+  for (size_t rd = 0; rd < lp.d_rounds.size(); ++rd)
+    launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rows_max, P, N, pc, c.Rw,
+                   c.st);
+  launch_jacobi<T>(lp.d_final_slot, lp.nnodes, c.Rw, pc, c.W, c.sig, c.st);
+  // directions below one unit roundoff of the panel's largest singular value are
+  // rounding noise of the working precision
+  const double floor_rel = (sizeof(T) == 4 ? 5.960464477539063e-08 : 1.1102230246251565e-16);
+  launch_truncate<T>(lp.nnodes, c.W, c.sig, pc, r, mode, kfix, kEpsScale * c.tol, c.eps_dev,
+                     set_eps ? 1 : 0, floor_rel, rank_lv, c.T1, c.flags_dev + 1, c.st);
+  launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, P, N, 0, 0, pc, c.T1, (int64_t)pc * r, pc, 0, Q,
+                   N, 0, 0, r, (T)1, (T)0, c.st);
+  launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Q, N, 0, 0, r, Q, N, 0,
+                   0, r, c.partial, c.G, c.st);
+  launch_cholqr<T>(lp.nnodes, c.G, r, rank_lv, c.T2, c.W, c.sig, pc, c.M, want_m ? 1 : 0, c.st);
+  launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Q, N, 0, 0, r, c.T2, (int64_t)r * r, r, 0, Q, N, 0,
+                   0, r, (T)1, (T)0, c.st);
+  c.launches += (int)lp.d_rounds.size() + 8;
+  return check_launch("panel svd");
+}
+
+template <typename T>
+hm_status ctx_alloc(Ctx<T>& c, int pc_max, int64_t extra_cols) {
+  const int64_t N = c.N;
+  const int r = c.r;
+  const hm_tree* t = c.tree;
+  int max_slots = 0, max_tn = 0;
+  for (int lv = 1; lv <= t->L; ++lv) {
+    max_slots = std::max(max_slots, t->plans[lv].nslots);
+    max_tn = std::max(max_tn, t->plans[lv].n_tn);
+  }
+  const int64_t nn = (int64_t)1 << t->L;  // most nodes on a level
+  auto layout = [&](Arena& a) {
+    c.X = a.take<T>(N * 2 * r);
+    c.S = a.take<T>(N * 2 * r);
+    c.P = a.take<T>(N * pc_max);
+    c.Rw = a.take<T>((size_t)max_slots * pc_max * pc_max);
+    c.W = a.take<T>(nn * pc_max * pc_max);
+    c.sig = a.take<T>(nn * pc_max);
+    c.T1 = a.take<T>(nn * pc_max * r);
+    c.G = a.take<T>(nn * r * r);
+    c.T2 = a.take<T>(nn * r * r);
+    c.M = a.take<T>(nn * pc_max * r);
+    c.coef = a.take<T>(nn * r * 128);
+    c.partial = a.take<double>((size_t)max_tn * 128 * 128);
+    c.flags_dev = a.take<int32_t>(4);
+    c.eps_dev = a.take<double>(2);
+    c.XI = a.take<T>(N * extra_cols);
+    c.YI = a.take<T>(N * extra_cols);
+  };
+  HM_TRY(arena_alloc(&c.block, layout));
+  HM_CUDA_TRY(cudaMemsetAsync(c.flags_dev, 0, 4 * sizeof(int32_t), c.st));
+  HM_CUDA_TRY(cudaMemsetAsync(c.eps_dev, 0, 2 * sizeof(double), c.st));
+  return HM_OK;
+}
+
+template <typename T>
+void ctx_free(Ctx<T>& c) {
+  for (auto& e : c.box_events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  c.box_events.clear();
+  if (c.block) cudaFree(c.block);
+  c.block = nullptr;
+}
+
+template <typename T>
+double box_ms(Ctx<T>& c) {
+  double ms = 0.0;
+  for (auto& e : c.box_events) {
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, e.first, e.second) == cudaSuccess) ms += f;
+  }
+  return ms;
+}
+
+template <typename T>
+hm_status compress_hodlr_t(Ctx<T>& c, hm_handle* h) {
+  const int64_t N = c.N;
+  const int r = c.r;
+  const int L = c.tree->L;
+  const int nmax = (int)c.tree->nmax;
+  T* U = (T*)h->U;
+  T* V = (T*)h->V;
+  const bool bf16 = (sizeof(T) == 4);
+  for (int level = 0; level < L; ++level) {
+    const int lv = level + 1;
+    T* Ulv = U + (int64_t)(lv - 1) * N * r;
+    T* Vlv = V + (int64_t)(lv - 1) * N * r;
+    int32_t* rank_lv = c.rank_dev + ((int64_t)1 << lv);
+    launch_gauss_fill<T>(c.X, N, N, r, level, c.seed, bf16, c.tree->d_start, L, c.st);
+    HM_TRY(box(c, 0, c.X, c.S, r));                      // Y_1 = A Omega_2
+    HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));      // Y_2 = A Omega_1
+    nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+    HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 0, -1.0));
+    launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
+    HM_TRY(panel_svd(c, lv, c.P, r, 0, 0, false, Ulv, false, c.rank_tmp));
+    launch_scatter_probe<T>(Ulv, N, c.X, N, N, r, lv, c.tree->d_start, L, c.st);
+    HM_TRY(box(c, 1, c.X, c.S, r));                      // Z_1 = A^T Omega_2
+    HM_TRY(box(c, 1, c.X + N * r, c.S + N * r, r));      // Z_2 = A^T Omega_1
+    nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+    HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 1, -1.0));
+    launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
+    const int mode = c.mode_tol ? 1 : 2;
+    HM_TRY(panel_svd(c, lv, c.P, r, mode, c.kfix, level == 0, Vlv, true, rank_lv));
+    // U_beta <- U_beta (W_k S_k R2^T) with the coefficients of the sibling's panel
+    const LevelPlan& lp = c.tree->plans[lv];
+    launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Ulv, N, 0, 0, r, c.M, (int64_t)r * r, r, 1, Ulv,
+                     N, 0, 0, r, (T)1, (T)0, c.st);
+    c.launches += 6;
+    HM_TRY(check_launch("hodlr level"));
+  }
+  // leaf blocks through the identity probe
+  launch_identity_probe<T>(c.XI, N, N, nmax, c.tree->d_start, L, c.st);
+  HM_TRY(box(c, 0, c.XI, c.YI, nmax));
+  HM_TRY(hodlr_peel(c, U, V, L, c.XI, c.YI, nmax, 0, -1.0));
+  launch_extract_diag<T>(c.YI, N, (T*)h->D, nmax, c.tree->d_start, c.tree->d_size, L, c.st);
+  c.launches += 2;
+  return check_launch("hodlr diagonal");
+}
+
+// --------------------------------------------------------------- apply -----
+template <typename T>
+hm_status hodlr_apply_t(const hm_handle* h, int trans, int64_t ncols, const T* X, int64_t ldx,
+                        T* Y, int64_t ldy, cudaStream_t st) {
+  const int64_t N = h->n;
+  const int r = h->r;
+  const hm_tree* t = &h->tree;
+  int max_tn = 0;
+  for (int lv = 1; lv <= t->L; ++lv) max_tn = std::max(max_tn, t->plans[lv].n_tn);
+  const int64_t nn = (int64_t)1 << t->L;
+  // contiguous copies of X / Y blocks so that the kernels see ld = N
+  const int64_t cbw = 128;
+  double* partial = nullptr;
+  T *coef = nullptr, *Xc = nullptr, *Yc = nullptr;
+  auto layout = [&](Arena& a) {
+    partial = a.take<double>((size_t)max_tn * r * cbw);
+    coef = a.take<T>(nn * r * cbw);
+    Xc = a.take<T>(N * cbw);
+    Yc = a.take<T>(N * cbw);
+  };
+  Arena m;
+  layout(m);
+  void* blk = nullptr;
+  HM_CUDA_TRY(cudaMallocAsync(&blk, m.off + 256, st));
+  Arena a;
+  a.base = (unsigned char*)blk;
+  a.cap = m.off + 256;
+  layout(a);
+  const T* U = (const T*)h->U;
+  const T* V = (const T*)h->V;
+  for (int64_t cb = 0; cb < ncols; cb += cbw) {
+    const int w = (int)std::min<int64_t>(cbw, ncols - cb);
+    launch_copy_cols<T>(X + cb * ldx, ldx, Xc, N, N, w, st);
+    launch_fill<T>(Yc, N * w, (T)0, st);
+    launch_blockdiag_apply<T>((const T*)h->D, (int)t->nmax, trans, Xc, N, Yc, N, w, t->d_start,
+                              t->d_size, t->L, st);
+    for (int j = 1; j <= t->L; ++j) {
+      const LevelPlan& lp = t->plans[j];
+      const T* Uj = U + (int64_t)(j - 1) * N * r;
+      const T* Vj = V + (int64_t)(j - 1) * N * r;
+      const T* Proj = trans ? Uj : Vj;
+      const T* Expd = trans ? Vj : Uj;
+      launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Proj, N, 0, 0, r, Xc,
+                       N, 0, 0, w, partial, coef, st);
+      launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Expd, N, 0, 0, r, coef, (int64_t)r * w, r, 1,
+                       Yc, N, 0, 0, w, (T)1, (T)1, st);
+    }
+    launch_copy_cols<T>(Yc, N, Y + cb * ldy, ldy, N, w, st);
+  }
+  HM_CUDA_TRY(cudaFreeAsync(blk, st));
+  return check_launch("hodlr apply");
+}
+
+template hm_status hodlr_apply_t<float>(const hm_handle*, int, int64_t, const float*, int64_t,
+                                        float*, int64_t, cudaStream_t);
+template hm_status hodlr_apply_t<double>(const hm_handle*, int, int64_t, const double*, int64_t,
+                                         double*, int64_t, cudaStream_t);
+
+}  // namespace hm
+
+// ------------------------------------------------------------ C entry ------
+static hm_status check_opts(const hm_operator* op, const hm_tree* tree, const hm_opts* o,
+                            hm_handle** out) {
+  if (!op || !op->apply || !tree || !o || !out) {
+    set_error("compress: null operator, tree, opts or out");
+    return HM_EINVAL;
+  }
+  if (op->n != tree->n) {
+    set_error("compress: operator size differs from the tree size");
+    return HM_EINVAL;
+  }
+  if (o->prec != HM_FP64 && o->prec != HM_MIXED) {
+    set_error("compress: prec must be HM_FP64 or HM_MIXED");
+    return HM_EINVAL;
+  }
+  if (o->mode_tol) {
+    if (!(o->tol > 0.0 && o->tol < 1.0) || o->r < 1) {
+      set_error("compress: tolerance mode needs 0 < tol < 1 and r >= 1");
+      return HM_EINVAL;
+    }
+  } else if (o->k < 1 || o->p < 0) {
+    set_error("compress: fixed-rank mode needs k >= 1 and p >= 0");
+    return HM_EINVAL;
+  }
+  if (tree->L < 1) {
+    set_error("compress: the tree must have at least one level below the root");
+    return HM_EINVAL;
+  }
+  return HM_OK;
+}
+
+int opts_r(const hm_opts* o) { return o->mode_tol ? o->r : o->k + o->p; }
+
+template <typename T>
+static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, const hm_opts* o,
+                                      cudaStream_t st, hm_handle** out) {
+  const int r = opts_r(o);
+  if (r > 128 || 2 * r > 256) {
+    set_error("compress: r must be at most 128");
+    return HM_EUNSUPPORTED;
+  }
+  hm_handle* h = new hm_handle();
+  h->format = HM_FORMAT_HODLR;
+  h->prec = o->prec;
+  h->n = tree->n;
+  h->L = tree->L;
+  h->r = r;
+  hm_status s = tree_build(tree->n, tree->leaf, &h->tree);
+  if (s == HM_OK) s = tree_plans(&h->tree);
+  if (s == HM_OK) s = tree_device(&h->tree);
+  const int64_t N = tree->n;
+  if (s == HM_OK) s = device_alloc(&h->U, sizeof(T) * (size_t)tree->L * N * r);
+  if (s == HM_OK) s = device_alloc(&h->V, sizeof(T) * (size_t)tree->L * N * r);
+  if (s == HM_OK)
+    s = device_alloc(&h->D, sizeof(T) * ((size_t)1 << tree->L) * tree->nmax * tree->nmax);
+  Ctx<T> c;
+  c.op = op;
+  c.tree = &h->tree;
+  c.st = st;
+  c.N = N;
+  c.r = r;
+  c.seed = o->seed;
+  c.mode_tol = o->mode_tol;
+  c.kfix = o->k;
+  c.tol = o->tol;
+  int32_t* rank_block = nullptr;
+  if (s == HM_OK) s = device_alloc((void**)&rank_block, sizeof(int32_t) * 2 * ((size_t)1 << (tree->L + 1)));
+  c.rank_dev = rank_block;
+  c.rank_tmp = rank_block + ((size_t)1 << (tree->L + 1));
+  if (s == HM_OK) s = ctx_alloc(c, r, tree->nmax);
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  if (s == HM_OK) {
+    cudaMemsetAsync(h->U, 0, sizeof(T) * (size_t)tree->L * N * r, st);
+    cudaMemsetAsync(h->V, 0, sizeof(T) * (size_t)tree->L * N * r, st);
+    cudaMemsetAsync(rank_block, 0, sizeof(int32_t) * 2 * ((size_t)1 << (tree->L + 1)), st);
+    cudaEventRecord(t0, st);
+    s = compress_hodlr_t<T>(c, h);
+    cudaEventRecord(t1, st);
+  }
+  if (s == HM_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error(std::string("compress: ") + cudaGetErrorString(e));
+      s = HM_ECUDA;
+    }
+  }
+  int32_t flags[4] = {0, 0, 0, 0};
+  double eps[2] = {0, 0};
+  if (s == HM_OK) {
+    cudaMemcpy(flags, c.flags_dev, sizeof(flags), cudaMemcpyDeviceToHost);
+    cudaMemcpy(eps, c.eps_dev, sizeof(eps), cudaMemcpyDeviceToHost);
+    h->rank.assign((size_t)1 << (tree->L + 1), 0);
+    cudaMemcpy(h->rank.data(), rank_block, sizeof(int32_t) * h->rank.size(),
+               cudaMemcpyDeviceToHost);
+    if (flags[0]) {
+      set_error("compress: NaN or Inf in the black-box samples");
+      s = HM_ENONFINITE;
+    } else if (flags[1] && o->strict_rank) {
+      set_error("compress: an adaptive rank reached r (raise r)");
+      s = HM_ERANK_SATURATED;
+    }
+  }
+  if (s == HM_OK) {
+    hm_info_t& in = h->info;
+    std::memset(&in, 0, sizeof(in));
+    in.format = HM_FORMAT_HODLR;
+    in.prec = o->prec;
+    in.n = N;
+    in.levels = tree->L;
+    in.r = r;
+    in.max_rank = 0;
+    in.min_rank = r;
+    for (int64_t a = 2; a < ((int64_t)1 << (tree->L + 1)); ++a) {
+      in.max_rank = std::max(in.max_rank, h->rank[a]);
+      in.min_rank = std::min(in.min_rank, h->rank[a]);
+    }
+    in.saturated = flags[1];
+    in.cols_A = c.cols_A;
+    in.cols_At = c.cols_At;
+    in.bytes = (int64_t)(2 * sizeof(T) * (size_t)tree->L * N * r +
+                         sizeof(T) * ((size_t)1 << tree->L) * tree->nmax * tree->nmax);
+    in.eps_abs = eps[0];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    in.t_compress_ms = ms;
+    in.t_blackbox_ms = box_ms(c);
+    in.launches = c.launches;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  ctx_free(c);
+  if (rank_block) cudaFree(rank_block);
+  if (s != HM_OK) {
+    hm_destroy(h);
+    return s;
+  }
+  *out = h;
+  return HM_OK;
+}
+
+extern "C" hm_status hm_compress_hodlr(const hm_operator* op, const hm_tree* tree,
+                                       const hm_opts* opts, void* stream, hm_handle** out) {
+  clear_error();
+  HM_TRY(check_opts(op, tree, opts, out));
+  *out = nullptr;
+  hm_tree* t = const_cast<hm_tree*>(tree);
+  if (opts->prec == HM_FP64)
+    return compress_hodlr_entry<double>(op, t, opts, (cudaStream_t)stream, out);
+  return compress_hodlr_entry<float>(op, t, opts, (cudaStream_t)stream, out);
+}
+
+namespace hm {
+#define HM_INST(T)                                                                          \
+  template hm_status box<T>(Ctx<T>&, int, const T*, T*, int64_t);                           \
+  template hm_status panel_svd<T>(Ctx<T>&, int, const T*, int, int, int, bool, T*, bool,    \
+                                  int32_t*);                                                \
+  template hm_status ctx_alloc<T>(Ctx<T>&, int, int64_t);                                   \
+  template void ctx_free<T>(Ctx<T>&);                                                       \
+  template double box_ms<T>(Ctx<T>&);
+HM_INST(float)
+HM_INST(double)
+#undef HM_INST
+}  // namespace hm

@@ -1,0 +1,52 @@
+// Compression context shared by the HODLR and HBS drivers.
+#pragma once
+
+#include <utility>
+#include <vector>
+
+#include "hm_api.h"
+
+namespace hm {
+
+template <typename T>
+struct Ctx {
+  const hm_operator* op = nullptr;
+  hm_tree* tree = nullptr;
+  cudaStream_t st = nullptr;
+  int64_t N = 0;
+  int r = 0;
+  uint64_t seed = 0;
+  int mode_tol = 0, kfix = 0;
+  double tol = 0.0;
+  void* block = nullptr;
+  T *X = nullptr, *S = nullptr, *P = nullptr, *Rw = nullptr, *W = nullptr, *sig = nullptr;
+  T *T1 = nullptr, *G = nullptr, *T2 = nullptr, *M = nullptr, *coef = nullptr;
+  T *XI = nullptr, *YI = nullptr;
+  double* partial = nullptr;
+  int32_t* flags_dev = nullptr;  // [0] non-finite, [1] saturated ranks
+  double* eps_dev = nullptr;
+  int32_t* rank_dev = nullptr;   // per heap id
+  int32_t* rank_tmp = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> box_events;
+  int64_t cols_A = 0, cols_At = 0;
+  int launches = 0;
+};
+
+template <typename T>
+hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols);
+template <typename T>
+hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
+                    T* Q, bool want_m, int32_t* rank_lv);
+template <typename T>
+hm_status ctx_alloc(Ctx<T>& c, int pc_max, int64_t extra_cols);
+template <typename T>
+void ctx_free(Ctx<T>& c);
+template <typename T>
+double box_ms(Ctx<T>& c);
+template <typename T>
+hm_status hodlr_apply_t(const hm_handle* h, int trans, int64_t ncols, const T* X, int64_t ldx,
+                        T* Y, int64_t ldy, cudaStream_t st);
+
+}  // namespace hm
+
+int opts_r(const hm_opts* o);

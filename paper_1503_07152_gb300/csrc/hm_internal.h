@@ -1,0 +1,250 @@
+// Internal declarations shared by the host orchestration and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hm.h"
+
+namespace hm {
+
+// ------------------------------------------------------------ errors ------
+void set_error(const std::string& msg);
+const char* get_error();
+void clear_error();
+
+#define HM_CUDA_TRY(expr)                                                        \
+  do {                                                                           \
+    cudaError_t _e = (expr);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      ::hm::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));       \
+      return HM_ECUDA;                                                           \
+    }                                                                            \
+  } while (0)
+
+#define HM_TRY(expr)                    \
+  do {                                  \
+    hm_status _s = (expr);              \
+    if (_s != HM_OK) return _s;         \
+  } while (0)
+
+hm_status check_launch(const char* what);
+
+// Row chunk of one tree node: rows [r0, r1) of node `node`.
+struct Chunk {
+  int32_t node;
+  int32_t pad;
+  int64_t r0;
+  int64_t r1;
+};
+
+// TSQR task: Householder QR of up to two stacked sources.
+//  kind 0: rows [r0, r1) of the panel;  kind 1: an R slot (c x c, row-major).
+struct TsqrTask {
+  int32_t node;      // heap id (for bookkeeping)
+  int32_t nsrc;      // 1 or 2
+  int32_t kind[2];
+  int32_t out_slot;  // R slot written
+  int32_t slot[2];   // source slots for kind 1
+  int64_t r0[2];
+  int64_t r1[2];
+};
+
+// ------------------------------------------------------- launchers --------
+// All launchers enqueue on `st` and return cudaSuccess-style status via
+// check_launch; T is float (mixed) or double (FP64).
+
+template <typename T>
+void launch_gauss_fill(T* X, int64_t ldx, int64_t n, int r, int level, uint64_t seed,
+                       bool bf16, const int64_t* d_start, int L, cudaStream_t st);
+
+template <typename T>
+void launch_identity_probe(T* X, int64_t ldx, int64_t n, int nmax, const int64_t* d_start,
+                           int L, cudaStream_t st);
+
+template <typename T>
+void launch_dense_gemm(const T* A, int64_t lda, int trans, int64_t n, int64_t ncols,
+                       const T* X, int64_t ldx, T* Y, int64_t ldy, uint8_t* flags,
+                       cudaStream_t st);
+
+// Gram-like reduction: for every chunk, partial = A(rows, 0:ka)^T B(rows, 0:kb)
+// (column offsets chosen by node parity), then per node sum of its chunks:
+// out[node - node0] (ka x kb, column-major, ld ka) = sum.
+template <typename T>
+void launch_seg_tn(const Chunk* chunks, int nchunks, const int32_t* chunk_begin, int nnodes,
+                   int node0, const T* A, int64_t lda, int aoff_even, int aoff_odd, int ka,
+                   const T* B, int64_t ldb, int boff_even, int boff_odd, int kb,
+                   double* partial, T* out, cudaStream_t st);
+
+// Expansion: Y(rows, yoff(node) + 0:kout) = alpha * P(rows, poff(node) + 0:kin) *
+// C[(node ^ cflip) - node0] + beta * Y(...).  C is kin x kout column-major with
+// stride cstride per node.  P may alias Y (rows are staged before writing).
+template <typename T>
+void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int64_t ldp,
+                   int poff_even, int poff_odd, int kin, const T* C, int64_t cstride, int cld,
+                   int cflip, T* Y, int64_t ldy, int yoff_even, int yoff_odd, int kout, T alpha,
+                   T beta, cudaStream_t st);
+
+template <typename T>
+void launch_tsqr(const TsqrTask* tasks, int ntasks, int rows_max, const T* P, int64_t ldp,
+                 int c, T* R, cudaStream_t st);
+
+// One-sided Jacobi SVD of the final R of every node: W (c x c col-major, sorted
+// by descending sigma), sigma (c).  node_slot[i] = R slot of node node0 + i.
+template <typename T>
+void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W, T* sigma,
+                   cudaStream_t st);
+
+// Rank decision + T1 = W(:, :k) diag(1/sigma) (c x kcap, zero padded).
+// mode 0: numerical range (sigma > floor * sigma1), at most kcap.
+// mode 1: tolerance (sigma > eps_abs, with eps_abs computed at the first level
+//         from the largest sigma1 as eps_scale * tol * nu), at most kcap.
+// mode 2: fixed rank kfix (<= kcap).
+template <typename T>
+void launch_truncate(int nnodes, const T* W, const T* sigma, int c, int kcap, int mode,
+                     int kfix, double tol_scaled, double* eps_abs, int set_eps, double floor_rel,
+                     int32_t* rank, T* T1, int32_t* saturated, cudaStream_t st);
+
+// CholQR pass: from G (k x k per node, Gram of Q1) compute R2 = chol(G) with
+// dead-pivot guard, T2 = R2^{-1}; and M = T1-side coefficient W_k Sigma_k R2^T
+// (c x kcap) when want_m != 0.
+template <typename T>
+void launch_cholqr(int nnodes, const T* G, int kcap, const int32_t* rank, T* T2,
+                   const T* W, const T* sigma, int c, T* M, int want_m, cudaStream_t st);
+
+// X'(i, probe(node) + j) = U(i, j) for j < r; the other r columns zero.
+template <typename T>
+void launch_scatter_probe(const T* U, int64_t ldu, T* X, int64_t ldx, int64_t n, int r,
+                          int level_nodes, const int64_t* d_start, int L, cudaStream_t st);
+
+// P(i, j) = Y(i, sample(node) + j), j < r.
+template <typename T>
+void launch_gather_sample(const T* Y, int64_t ldy, T* P, int64_t ldp, int64_t n, int r,
+                          int level_nodes, const int64_t* d_start, int L, cudaStream_t st);
+
+// D_t = Y(I_t, 0:n_t) for every leaf (D: one nmax x nmax col-major block per leaf).
+template <typename T>
+void launch_extract_diag(const T* Y, int64_t ldy, T* D, int nmax, const int64_t* d_start,
+                         const int64_t* d_size, int L, cudaStream_t st);
+
+// Y(I_t, :) += op(D_t) X(I_t, :) for every leaf.
+template <typename T>
+void launch_blockdiag_apply(const T* D, int nmax, int trans, const T* X, int64_t ldx, T* Y,
+                            int64_t ldy, int64_t ncols, const int64_t* d_start,
+                            const int64_t* d_size, int L, cudaStream_t st);
+
+template <typename T>
+void launch_fill(T* p, int64_t count, T v, cudaStream_t st);
+
+template <typename T>
+void launch_copy_cols(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t rows,
+                      int64_t cols, cudaStream_t st);
+
+// Y(:, j) = e_{c0 + j} restricted to rows (identity columns), n x w.
+template <typename T>
+void launch_identity_cols(T* Y, int64_t ldy, int64_t n, int64_t c0, int64_t w, cudaStream_t st);
+
+// sum over tile of (A(i, c0 + j) - Ac(i, j))^2 and A^2 -> acc[0], acc[1] (atomic FP64)
+template <typename T>
+void launch_frob_tile(const T* A, int64_t lda, const T* Ac, int64_t ldc, int64_t n,
+                      int64_t c0, int64_t w, double* acc, cudaStream_t st);
+
+int32_t nonfinite_check_launch(const void* p, int64_t count, int is_double, int32_t* flag,
+                               cudaStream_t st);
+
+void launch_gen_log_kernel(float* A, int64_t n, int64_t lda, cudaStream_t st);
+
+struct FactChunk {
+  int32_t level;
+  int32_t node;
+  int64_t r0;
+  int64_t r1;
+};
+
+}  // namespace hm
+struct hm_tree;
+namespace hm {
+size_t factored_scratch_bytes(const hm_tree* t, int k);
+void launch_factored_apply(const hm_tree* t, int k, const float* U, const float* V,
+                           const float* D, int trans, const float* x, float* y, float* scratch,
+                           cudaStream_t st);
+void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const float* V,
+                             const float* D, const float* x, const float* res, float scale,
+                             float* gx, float* gU, float* gV, float* gD, float* scratch,
+                             cudaStream_t st);
+
+}  // namespace hm
+
+namespace hm {
+// Device work plan of one node level: row chunks for the segmented kernels and
+// the TSQR merge schedule (row blocks first, then pairwise R merges).
+struct LevelPlan {
+  int nnodes = 0, node0 = 0;
+  int n_tn = 0, n_nn = 0;
+  std::vector<std::vector<TsqrTask>> tsqr_rounds;
+  std::vector<int32_t> final_slot;
+  int nslots = 0;
+  std::vector<Chunk> tn, nn;
+  std::vector<int32_t> tn_begin;
+  void* dev = nullptr;
+  const Chunk* d_tn = nullptr;
+  const int32_t* d_tn_begin = nullptr;
+  const Chunk* d_nn = nullptr;
+  std::vector<const TsqrTask*> d_rounds;
+  const int32_t* d_final_slot = nullptr;
+};
+int64_t dense_flags_bytes(int64_t n, int64_t ncols, int is_double);
+}  // namespace hm
+
+// ----------------------------------------------------------- objects --------
+struct hm_tree {
+  int64_t n = 0;
+  int32_t leaf = 0;
+  int32_t L = 0;
+  std::vector<int64_t> start, size;  // indexed by heap id, length 2^(L+1)
+  int64_t* d_start = nullptr;        // device copies
+  int64_t* d_size = nullptr;
+  int64_t nmax = 0;
+  std::vector<hm::LevelPlan> plans;  // index = node level (1..L)
+  // 256-row chunks of every node of levels 1..L, level-major (heap-id order),
+  // and the first chunk of every heap id (fbegin[2^(L+1)] = n_fchunks)
+  std::vector<hm::FactChunk> fchunks;
+  std::vector<int32_t> fbegin;
+  void* fdev = nullptr;
+  const hm::FactChunk* d_fchunks = nullptr;
+  const int32_t* d_fbegin = nullptr;
+  int n_fchunks = 0;
+};
+
+struct hm_dense_ctx {
+  const void* A = nullptr;
+  int64_t n = 0, lda = 0;
+  int32_t dtype = 0;
+  uint8_t* flags = nullptr;  // zero-tile flags scratch
+  int64_t flags_bytes = 0;
+};
+
+struct hm_handle {
+  int32_t format = 0;
+  int32_t prec = 0;
+  int64_t n = 0;
+  int32_t L = 0;
+  int32_t r = 0;
+  hm_tree tree;  // own copy (device node table owned too)
+  // HODLR factors (element type by prec): level j in [1, L] at offset (j-1)*n*r
+  void* U = nullptr;  // U_j B_j (absorbed sibling matrix), n x r per level
+  void* V = nullptr;  // V_j, n x r per level
+  void* D = nullptr;  // leaves x nmax x nmax
+  std::vector<int32_t> rank;  // per heap id
+  // HBS-ID factors (host-built offsets into device arrays)
+  void* hbs_store = nullptr;
+  int64_t hbs_bytes = 0;
+  std::vector<int64_t> tin_off, tout_off, bsk_off;  // element offsets per heap id
+  std::vector<int32_t> kin, kout;                   // ranks per heap id
+  std::vector<int64_t> iin_off, iout_off;            // skeleton index offsets
+  int64_t* skel = nullptr;                           // device skeleton indices
+  hm_info_t info{};
+};

@@ -1,0 +1,216 @@
+// Factored HODLR apply y = H x (the O(k N log N) product of Sec. 2.8 with
+// sibling matrices B = I) and its hand-written adjoint (vector-Jacobian product
+// for x, U, V, D; with r = H x - b and scale 2, the gradients of ||H x - b||^2).
+//
+// Both are HBM-streaming: every factor byte is read once (and every gradient
+// byte written once).  Pass 1 reduces t_node = V(I_node)^T x(I_node) (and
+// s_node = U(I_node)^T res(I_node) for the adjoint) over 256-row chunks of all
+// levels; pass 2 reduces the chunk partials per node in a fixed order; pass 3
+// runs one block per leaf: every row of the leaf gathers the contributions of
+// its L ancestors' siblings (ancestor of leaf l on level j = l >> (L - j)) and
+// of the leaf block D, and, for the adjoint, writes the gradient rows.
+#include "hm_internal.h"
+
+namespace hm {
+namespace {
+
+constexpr int kMaxK = 64;
+
+// partial[chunk][0:k] = V_j(rows)^T x(rows); with second operand pair for the
+// adjoint: partial[chunk][k:2k] = U_j(rows)^T res(rows).
+__global__ __launch_bounds__(256) void k_fact_partial(const FactChunk* __restrict__ ch,
+                                                      int64_t n, int k,
+                                                      const float* __restrict__ A0,
+                                                      const float* __restrict__ v0,
+                                                      const float* __restrict__ A1,
+                                                      const float* __restrict__ v1,
+                                                      float* __restrict__ partial) {
+  __shared__ float red[8][2 * kMaxK];
+  const FactChunk c = ch[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t row = c.r0 + tid;
+  const bool live = row < c.r1;
+  const int npair = A1 ? 2 : 1;
+  for (int p = 0; p < npair; ++p) {
+    const float* A = (p == 0 ? A0 : A1) + (int64_t)(c.level - 1) * n * k;
+    const float xv = live ? (p == 0 ? v0 : v1)[row] : 0.f;
+    for (int col = 0; col < k; ++col) {
+      float v = live ? A[row + (int64_t)col * n] * xv : 0.f;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][p * k + col] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < npair * k; e += 256) {
+    float s = 0.f;
+    for (int w = 0; w < 8; ++w) s += red[w][e];
+    partial[(int64_t)blockIdx.x * npair * k + e] = s;
+  }
+}
+
+// out[node][e] = sum over the node's chunks (heap ids 2 .. 2^(L+1)-1).
+__global__ void k_fact_reduce(const float* __restrict__ partial, const int32_t* __restrict__ fbegin,
+                              int width, int nnodes_total, float* __restrict__ out) {
+  const int node = 2 + blockIdx.x;
+  if (node >= nnodes_total) return;
+  const int c0 = fbegin[node], c1 = fbegin[node + 1];
+  for (int e = threadIdx.x; e < width; e += blockDim.x) {
+    float s = 0.f;
+    for (int c = c0; c < c1; ++c) s += partial[(int64_t)c * width + e];
+    out[(int64_t)node * width + e] = s;
+  }
+}
+
+// y(I_leaf) = sum_j Uex_j(I_leaf) coef[sib(anc_j)] + op(D_leaf) x(I_leaf)
+__global__ __launch_bounds__(256) void k_fact_expand(const int64_t* __restrict__ start,
+                                                     const int64_t* __restrict__ size, int L,
+                                                     int64_t n, int k, int nmax, int width,
+                                                     const float* __restrict__ Uex,
+                                                     const float* __restrict__ coef,
+                                                     const float* __restrict__ D, int trans,
+                                                     const float* __restrict__ x,
+                                                     float* __restrict__ y) {
+  extern __shared__ float sm[];
+  float* cs = sm;                  // L * k coefficients
+  float* xs = sm + L * kMaxK;      // leaf slice of x
+  float* dt = xs + nmax;           // D^T x for the transposed product
+  const int leaf = (1 << L) + blockIdx.x;
+  const int64_t s0 = start[leaf];
+  const int ns = (int)size[leaf];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < L * k; e += blockDim.x) {
+    const int j = 1 + e / k, col = e % k;
+    const int anc = leaf >> (L - j);
+    cs[(j - 1) * kMaxK + col] = coef[(int64_t)(anc ^ 1) * width + col];
+  }
+  for (int m = tid; m < ns; m += blockDim.x) xs[m] = x[s0 + m];
+  __syncthreads();
+  const float* Dl = D + (int64_t)blockIdx.x * nmax * nmax;
+  if (trans) {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int i = warp; i < ns; i += blockDim.x >> 5) {
+      float v = 0.f;
+      for (int m = lane; m < ns; m += 32) v += Dl[m + (int64_t)i * nmax] * xs[m];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) dt[i] = v;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < ns; i += blockDim.x) {
+    const int64_t row = s0 + i;
+    float acc = 0.f;
+    for (int j = 1; j <= L; ++j) {
+      const float* Uj = Uex + (int64_t)(j - 1) * n * k;
+      for (int col = 0; col < k; ++col) acc = fmaf(Uj[row + (int64_t)col * n], cs[(j - 1) * kMaxK + col], acc);
+    }
+    if (trans) {
+      acc += dt[i];
+    } else {
+      for (int m = 0; m < ns; ++m) acc = fmaf(Dl[i + (int64_t)m * nmax], xs[m], acc);
+    }
+    y[row] = acc;
+  }
+}
+
+// Adjoint rows of one leaf.  coef holds [t | s] per node (width 2k):
+// t_node = V_j(I_node)^T x, s_node = U_j(I_node)^T res.
+__global__ __launch_bounds__(256) void k_fact_adjoint(
+    const int64_t* __restrict__ start, const int64_t* __restrict__ size, int L, int64_t n, int k,
+    int nmax, const float* __restrict__ U, const float* __restrict__ V,
+    const float* __restrict__ D, const float* __restrict__ coef, const float* __restrict__ x,
+    const float* __restrict__ res, float scale, float* __restrict__ gx, float* __restrict__ gU,
+    float* __restrict__ gV, float* __restrict__ gD) {
+  extern __shared__ float sm[];
+  float* ts = sm;                  // t of the sibling per level
+  float* ss = sm + L * kMaxK;      // s of the sibling per level
+  float* xs = ss + L * kMaxK;
+  float* rs = xs + nmax;
+  float* dt = rs + nmax;           // D^T res
+  const int leaf = (1 << L) + blockIdx.x;
+  const int64_t s0 = start[leaf];
+  const int ns = (int)size[leaf];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < L * k; e += blockDim.x) {
+    const int j = 1 + e / k, col = e % k;
+    const int sib = (leaf >> (L - j)) ^ 1;
+    ts[(j - 1) * kMaxK + col] = coef[(int64_t)sib * 2 * k + col];
+    ss[(j - 1) * kMaxK + col] = coef[(int64_t)sib * 2 * k + k + col];
+  }
+  for (int m = tid; m < ns; m += blockDim.x) {
+    xs[m] = x[s0 + m];
+    rs[m] = res[s0 + m];
+  }
+  __syncthreads();
+  const float* Dl = D + (int64_t)blockIdx.x * nmax * nmax;
+  if (gx) {
+    for (int i = warp; i < ns; i += blockDim.x >> 5) {
+      float v = 0.f;
+      for (int m = lane; m < ns; m += 32) v += Dl[m + (int64_t)i * nmax] * rs[m];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) dt[i] = v;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < ns; i += blockDim.x) {
+    const int64_t row = s0 + i;
+    const float xr = xs[i], rr = rs[i];
+    float acc = 0.f;
+    for (int j = 1; j <= L; ++j) {
+      const int64_t base = (int64_t)(j - 1) * n * k;
+      for (int col = 0; col < k; ++col) {
+        const int64_t off = base + row + (int64_t)col * n;
+        if (gx) acc = fmaf(V[off], ss[(j - 1) * kMaxK + col], acc);
+        if (gU) gU[off] = scale * rr * ts[(j - 1) * kMaxK + col];
+        if (gV) gV[off] = scale * xr * ss[(j - 1) * kMaxK + col];
+      }
+    }
+    if (gx) gx[row] = scale * (acc + dt[i]);
+    if (gD) {
+      float* gDl = gD + (int64_t)blockIdx.x * nmax * nmax;
+      for (int m = 0; m < nmax; ++m)
+        gDl[i + (int64_t)m * nmax] = (m < ns) ? scale * rr * xs[m] : 0.f;
+    }
+  }
+}
+
+}  // namespace
+
+size_t factored_scratch_bytes(const hm_tree* t, int k) {
+  const size_t nodes = (size_t)1 << (t->L + 1);
+  return sizeof(float) * ((size_t)t->n_fchunks * 2 * k + nodes * 2 * k) + 256;
+}
+
+void launch_factored_apply(const hm_tree* t, int k, const float* U, const float* V,
+                           const float* D, int trans, const float* x, float* y, float* scratch,
+                           cudaStream_t st) {
+  const int L = t->L;
+  const int nodes = 1 << (L + 1);
+  float* partial = scratch;
+  float* coef = scratch + (size_t)t->n_fchunks * k;
+  // t_node = Proj(I_node)^T x with Proj = V (H x) or U (H^T x)
+  k_fact_partial<<<t->n_fchunks, 256, 0, st>>>(t->d_fchunks, t->n, k, trans ? U : V, x, nullptr,
+                                                nullptr, partial);
+  k_fact_reduce<<<nodes - 2, 128, 0, st>>>(partial, t->d_fbegin, k, nodes, coef);
+  const int nmax = (int)t->nmax;
+  const size_t smem = sizeof(float) * (L * kMaxK + 2 * nmax);
+  k_fact_expand<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, k,
+                                           trans ? V : U, coef, D, trans, x, y);
+}
+
+void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const float* V,
+                             const float* D, const float* x, const float* res, float scale,
+                             float* gx, float* gU, float* gV, float* gD, float* scratch,
+                             cudaStream_t st) {
+  const int L = t->L;
+  const int nodes = 1 << (L + 1);
+  float* partial = scratch;
+  float* coef = scratch + (size_t)t->n_fchunks * 2 * k;
+  k_fact_partial<<<t->n_fchunks, 256, 0, st>>>(t->d_fchunks, t->n, k, V, x, U, res, partial);
+  k_fact_reduce<<<nodes - 2, 128, 0, st>>>(partial, t->d_fbegin, 2 * k, nodes, coef);
+  const int nmax = (int)t->nmax;
+  const size_t smem = sizeof(float) * (2 * L * kMaxK + 3 * nmax);
+  k_fact_adjoint<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, U, V, D,
+                                            coef, x, res, scale, gx, gU, gV, gD);
+}
+
+}  // namespace hm

@@ -1,0 +1,340 @@
+// Kernels of the HBS / HBS-ID path (Secs. 4.1-4.3):
+//  - parent spanning matrix  U_tau(J_alpha,:) diag(y_tau)  appended to a panel
+//    (Fig. "A storage efficient algorithm for compressing an HBS matrix"),
+//  - batched small GEMMs and per-node copies (short bases, sibling matrices,
+//    the upward / downward passes of Fig. "Application of A^(m) in the HBS
+//    framework"),
+//  - the interpolative decomposition of the HBS-ID sweep (Fig. "An algorithm
+//    for computing the HBS-ID representation"): column-pivoted Householder QR
+//    (Businger-Golub, largest remaining column norm, lowest index on ties) and
+//    T = R11^{-1} [R11 R12] in FP64, one block per node.
+#include "hm_internal.h"
+#include "hm_hbs.h"
+
+namespace hm {
+namespace {
+
+__device__ __forceinline__ int node_of_row_h(const int64_t* __restrict__ start, int lv,
+                                             int64_t row) {
+  const int64_t* s = start + (1 << lv);
+  int lo = 0, hi = (1 << lv) - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s[mid] <= row) lo = mid; else hi = mid - 1;
+  }
+  return (1 << lv) + lo;
+}
+
+// P(i, col0 + j) = U(i, j) * y[parent(node(i))][j]
+template <typename T>
+__global__ void k_gather_parent_scaled(const T* __restrict__ U, int64_t ldu, T* __restrict__ P,
+                                       int64_t ldp, int64_t n, int r, int lv,
+                                       const int64_t* __restrict__ start,
+                                       const T* __restrict__ y, int col0) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n) return;
+  const int node = node_of_row_h(start, lv, i);
+  P[i + (int64_t)(col0 + j) * ldp] = U[i + (int64_t)j * ldu] * y[(int64_t)(node >> 1) * r + j];
+}
+
+// C = alpha op(A) op(B) + beta C, one block per item; small sizes.
+template <typename T>
+__global__ void k_batched_gemm(const GemmItem* __restrict__ items, T alpha, T beta) {
+  const GemmItem it = items[blockIdx.x];
+  const T* A = (const T*)it.A;
+  const T* B = (const T*)it.B;
+  T* Cm = (T*)it.C;
+  const int mn = it.m * it.n;
+  for (int e = threadIdx.x; e < mn; e += blockDim.x) {
+    const int i = e % it.m, j = e / it.m;
+    T acc = 0;
+    for (int p = 0; p < it.k; ++p) {
+      const T a = it.ta ? A[p + (int64_t)i * it.lda] : A[i + (int64_t)p * it.lda];
+      const T b = it.tb ? B[j + (int64_t)p * it.ldb] : B[p + (int64_t)j * it.ldb];
+      acc = fma(a, b, acc);
+    }
+    T* c = Cm + i + (int64_t)j * it.ldc;
+    *c = (beta == (T)0) ? alpha * acc : alpha * acc + beta * (*c);
+  }
+}
+
+// dst[(node0 + i) ^ flip] (rows x cols, ld dld) = src[i] (ld sld); heap-indexed dst.
+template <typename TS, typename TD>
+__global__ void k_node_copy(int node0, const TS* __restrict__ src, int64_t sstride, int sld,
+                            TD* __restrict__ dst, int64_t dstride, int dld, int rows, int cols,
+                            int flip) {
+  const int i = blockIdx.x;
+  const int dnode = (node0 + i) ^ flip;
+  const TS* s = src + (int64_t)i * sstride;
+  TD* d = dst + (int64_t)dnode * dstride;
+  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+    const int rr = e % rows, cc = e / rows;
+    d[rr + (int64_t)cc * dld] = (TD)s[rr + (int64_t)cc * sld];
+  }
+}
+
+// Y_tmp^T of a leaf: Yt(i, j) = y[leaf][i] * U(s + j, i), i < r, j < n_leaf (FP64).
+template <typename T>
+__global__ void k_id_prep_leaf(const T* __restrict__ U, int64_t ldu,
+                               const int64_t* __restrict__ start, const int64_t* __restrict__ size,
+                               int L, const T* __restrict__ y, int r, double* __restrict__ Yt,
+                               int ncmax) {
+  const int leaf = (1 << L) + blockIdx.x;
+  const int64_t s = start[leaf];
+  const int ns = (int)size[leaf];
+  double* Y = Yt + (int64_t)blockIdx.x * r * ncmax;
+  for (int e = threadIdx.x; e < r * ncmax; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    Y[e] = (j < ns) ? (double)y[(int64_t)leaf * r + i] * (double)U[s + j + (int64_t)i * ldu] : 0.0;
+  }
+}
+
+// Y_tmp^T of a parent: Yt(i, j) = y[node][i] * Utmp(j, i), Utmp 2r x r per node.
+template <typename T>
+__global__ void k_id_prep_parent(int node0, const double* __restrict__ Utmp,
+                                 const T* __restrict__ y, int r, double* __restrict__ Yt) {
+  const int node = node0 + blockIdx.x;
+  const double* Ut = Utmp + (int64_t)blockIdx.x * 2 * r * r;
+  double* Y = Yt + (int64_t)blockIdx.x * r * 2 * r;
+  for (int e = threadIdx.x; e < r * 2 * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    Y[e] = (double)y[(int64_t)node * r + i] * Ut[j + (int64_t)i * 2 * r];
+  }
+}
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Column ID of the r x nc matrix Yt (per node) with tolerance eps (|R_jj| > eps)
+// and at most kcap terms.  Outputs k, J (kcap, -1 padded) and T (kcap x nc,
+// column-major, zero rows past k): Yt ~= Yt(:, J) T.
+__global__ __launch_bounds__(256) void k_pivqr_id(const double* __restrict__ Yt, int r, int nc,
+                                                  double eps, int kcap, int32_t* __restrict__ kout,
+                                                  int32_t* __restrict__ Jout,
+                                                  double* __restrict__ Tout) {
+  // layout stride of J and T rows is r (kcap <= r only caps the rank)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* M = reinterpret_cast<double*>(smem_raw);  // r x nc, column-major
+  double* nrm = M + r * nc;                          // nc
+  int* perm = reinterpret_cast<int*>(nrm + nc);      // nc
+  __shared__ double red[8];
+  __shared__ int redi[8];
+  __shared__ int sk;
+  const double* Y = Yt + (int64_t)blockIdx.x * r * nc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < r * nc; e += blockDim.x) M[e] = Y[e];
+  for (int j = tid; j < nc; j += blockDim.x) perm[j] = j;
+  __syncthreads();
+  const int steps = min(r, nc);
+  int k = 0;
+  for (int j = 0; j < steps; ++j) {
+    // norms of the remaining columns over rows j.. (recomputed: exact pivot rule)
+    for (int c = j + warp; c < nc; c += 8) {
+      double s = 0.0;
+      for (int i = j + lane; i < r; i += 32) s += M[i + c * r] * M[i + c * r];
+      s = wsum(s);
+      if (lane == 0) nrm[c] = s;
+    }
+    __syncthreads();
+    // argmax, first index on ties
+    double best = -1.0;
+    int bi = nc;
+    for (int c = j + tid; c < nc; c += blockDim.x)
+      if (nrm[c] > best || (nrm[c] == best && c < bi)) { best = nrm[c]; bi = c; }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red[warp] = best; redi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = red[0];
+      int i0 = redi[0];
+      for (int w = 1; w < 8; ++w)
+        if (red[w] > b || (red[w] == b && redi[w] < i0)) { b = red[w]; i0 = redi[w]; }
+      sk = (sqrt(b) > eps && j < kcap) ? i0 : -1;
+    }
+    __syncthreads();
+    const int p = sk;
+    if (p < 0) break;
+    if (p != j) {
+      for (int i = tid; i < r; i += blockDim.x) {
+        const double t = M[i + j * r];
+        M[i + j * r] = M[i + p * r];
+        M[i + p * r] = t;
+      }
+      if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+    }
+    __syncthreads();
+    // Householder on column j (rows j..r-1)
+    if (warp == 0) {
+      double s = 0.0;
+      for (int i = j + lane; i < r; i += 32) s += M[i + j * r] * M[i + j * r];
+      s = wsum(s);
+      if (lane == 0) {
+        const double x0 = M[j + j * r];
+        const double nx = sqrt(s);
+        const double alpha = (x0 > 0.0) ? -nx : nx;
+        const double v0 = x0 - alpha;
+        const double vtv = s - x0 * x0 + v0 * v0;
+        red[0] = alpha;
+        red[1] = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+        M[j + j * r] = v0;
+      }
+    }
+    __syncthreads();
+    const double beta = red[1];
+    for (int c = j + 1 + warp; c < nc; c += 8) {
+      double d = 0.0;
+      for (int i = j + lane; i < r; i += 32) d += M[i + j * r] * M[i + c * r];
+      d = wsum(d) * beta;
+      for (int i = j + lane; i < r; i += 32) M[i + c * r] -= d * M[i + j * r];
+    }
+    __syncthreads();
+    if (tid == 0) M[j + j * r] = red[0];
+    for (int i = j + 1 + tid; i < r; i += blockDim.x) M[i + j * r] = 0.0;
+    __syncthreads();
+    k = j + 1;
+  }
+  // T(:, perm) = [I, R11^{-1} R12]; solve column by column (back substitution)
+  double* T = Tout + (int64_t)blockIdx.x * r * nc;
+  for (int e = tid; e < r * nc; e += blockDim.x) T[e] = 0.0;
+  __syncthreads();
+  for (int c = tid; c < nc; c += blockDim.x) {
+    const int oc = perm[c];
+    if (c < k) {
+      T[c + (int64_t)oc * r] = 1.0;
+    } else {
+      for (int i = k - 1; i >= 0; --i) {
+        double s = M[i + c * r];
+        for (int q = i + 1; q < k; ++q) s -= M[i + q * r] * T[q + (int64_t)oc * r];
+        T[i + (int64_t)oc * r] = s / M[i + i * r];
+      }
+    }
+  }
+  int32_t* J = Jout + (int64_t)blockIdx.x * r;
+  for (int a = tid; a < r; a += blockDim.x) J[a] = (a < k) ? perm[a] : -1;
+  if (tid == 0) kout[blockIdx.x] = k;
+}
+
+// Usamp (r x r, row a = skeleton row a, zero rows past k) from a leaf basis.
+template <typename T>
+__global__ void k_usamp_leaf(const T* __restrict__ U, int64_t ldu, const int64_t* __restrict__ start,
+                             int L, const int32_t* __restrict__ J, int r,
+                             double* __restrict__ Us, int64_t* __restrict__ skel) {
+  const int leaf = (1 << L) + blockIdx.x;
+  const int64_t s = start[leaf];
+  const int32_t* Jl = J + (int64_t)blockIdx.x * r;
+  double* Ul = Us + (int64_t)leaf * r * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int a = e % r, c = e / r;
+    const int ja = Jl[a];
+    Ul[e] = (ja >= 0) ? (double)U[s + ja + (int64_t)c * ldu] : 0.0;
+  }
+  for (int a = threadIdx.x; a < r; a += blockDim.x)
+    skel[(int64_t)leaf * r + a] = (Jl[a] >= 0) ? s + Jl[a] : -1;
+}
+
+// Parent: Usamp = Utmp(J, :) and skeleton = children's skeletons at J.
+__global__ void k_usamp_parent(int node0, const double* __restrict__ Utmp,
+                               const int32_t* __restrict__ J, int r, double* __restrict__ Us,
+                               int64_t* __restrict__ skel) {
+  const int node = node0 + blockIdx.x;
+  const double* Ut = Utmp + (int64_t)blockIdx.x * 2 * r * r;
+  const int32_t* Jn = J + (int64_t)blockIdx.x * r;
+  double* Un = Us + (int64_t)node * r * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int a = e % r, c = e / r;
+    const int ja = Jn[a];
+    Un[e] = (ja >= 0) ? Ut[ja + (int64_t)c * 2 * r] : 0.0;
+  }
+  for (int a = threadIdx.x; a < r; a += blockDim.x) {
+    const int ja = Jn[a];
+    int64_t g = -1;
+    if (ja >= 0) g = (ja < r) ? skel[(int64_t)(2 * node) * r + ja] : skel[(int64_t)(2 * node + 1) * r + ja - r];
+    skel[(int64_t)node * r + a] = g;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_gather_parent_scaled(const T* U, int64_t ldu, T* P, int64_t ldp, int64_t n, int r,
+                                 int lv, const int64_t* d_start, const T* y, int col0,
+                                 cudaStream_t st) {
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)r);
+  k_gather_parent_scaled<T><<<grid, 256, 0, st>>>(U, ldu, P, ldp, n, r, lv, d_start, y, col0);
+}
+
+template <typename T>
+void launch_batched_gemm(const GemmItem* items, int count, T alpha, T beta, cudaStream_t st) {
+  if (count <= 0) return;
+  k_batched_gemm<T><<<count, 256, 0, st>>>(items, alpha, beta);
+}
+
+template <typename TS, typename TD>
+void launch_node_copy(int nnodes, int node0, const TS* src, int64_t sstride, int sld, TD* dst,
+                      int64_t dstride, int dld, int rows, int cols, int flip, cudaStream_t st) {
+  if (nnodes <= 0) return;
+  k_node_copy<TS, TD><<<nnodes, 256, 0, st>>>(node0, src, sstride, sld, dst, dstride, dld, rows,
+                                              cols, flip);
+}
+
+template <typename T>
+void launch_id_prep_leaf(const T* U, int64_t ldu, const int64_t* d_start, const int64_t* d_size,
+                         int L, const T* y, int r, double* Yt, int ncmax, cudaStream_t st) {
+  k_id_prep_leaf<T><<<1 << L, 256, 0, st>>>(U, ldu, d_start, d_size, L, y, r, Yt, ncmax);
+}
+
+template <typename T>
+void launch_id_prep_parent(int nnodes, int node0, const double* Utmp, const T* y, int r,
+                           double* Yt, cudaStream_t st) {
+  k_id_prep_parent<T><<<nnodes, 256, 0, st>>>(node0, Utmp, y, r, Yt);
+}
+
+void launch_pivqr_id(int nnodes, const double* Yt, int r, int nc, double eps, int kcap,
+                     int32_t* k, int32_t* J, double* T, cudaStream_t st) {
+  const size_t smem = sizeof(double) * ((size_t)r * nc + nc) + sizeof(int) * nc;
+  cudaFuncSetAttribute(k_pivqr_id, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_pivqr_id<<<nnodes, 256, smem, st>>>(Yt, r, nc, eps, kcap, k, J, T);
+}
+
+template <typename T>
+void launch_usamp_leaf(const T* U, int64_t ldu, const int64_t* d_start, int L, const int32_t* J,
+                       int r, double* Us, int64_t* skel, cudaStream_t st) {
+  k_usamp_leaf<T><<<1 << L, 128, 0, st>>>(U, ldu, d_start, L, J, r, Us, skel);
+}
+
+void launch_usamp_parent(int nnodes, int node0, const double* Utmp, const int32_t* J, int r,
+                         double* Us, int64_t* skel, cudaStream_t st) {
+  k_usamp_parent<<<nnodes, 128, 0, st>>>(node0, Utmp, J, r, Us, skel);
+}
+
+#define HM_INST(T)                                                                             \
+  template void launch_gather_parent_scaled<T>(const T*, int64_t, T*, int64_t, int64_t, int,   \
+                                               int, const int64_t*, const T*, int,             \
+                                               cudaStream_t);                                  \
+  template void launch_batched_gemm<T>(const GemmItem*, int, T, T, cudaStream_t);              \
+  template void launch_id_prep_leaf<T>(const T*, int64_t, const int64_t*, const int64_t*, int, \
+                                       const T*, int, double*, int, cudaStream_t);             \
+  template void launch_id_prep_parent<T>(int, int, const double*, const T*, int, double*,      \
+                                         cudaStream_t);                                        \
+  template void launch_usamp_leaf<T>(const T*, int64_t, const int64_t*, int, const int32_t*,   \
+                                     int, double*, int64_t*, cudaStream_t);
+HM_INST(float)
+HM_INST(double)
+#undef HM_INST
+template void launch_node_copy<float, float>(int, int, const float*, int64_t, int, float*, int64_t,
+                                             int, int, int, int, cudaStream_t);
+template void launch_node_copy<double, double>(int, int, const double*, int64_t, int, double*,
+                                               int64_t, int, int, int, int, cudaStream_t);
+template void launch_node_copy<float, double>(int, int, const float*, int64_t, int, double*,
+                                              int64_t, int, int, int, int, cudaStream_t);
+template void launch_node_copy<double, float>(int, int, const double*, int64_t, int, float*,
+                                              int64_t, int, int, int, int, cudaStream_t);
+
+}  // namespace hm

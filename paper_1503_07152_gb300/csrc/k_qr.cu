@@ -1,0 +1,385 @@
+// Per-node orthonormalization and truncated SVD of sample panels, batched over
+// all nodes of a level (uneven sizes in one launch):
+//   1. TSQR: Householder QR of row blocks in shared memory, R factors merged
+//      pairwise in a tree (R only; the panel P = Q R is never formed via Q).
+//   2. One-sided (Hestenes) Jacobi SVD of each node's final R: R = W_L S W^T;
+//      right vectors W and singular values S, sorted descending.
+//   3. Truncation: the rank k of the node (mode 2 fixed k, or mode 3 tolerance,
+//      Sec. 2.6) and T1 = W(:, :k) S^{-1}, so that Q1 = P T1 has orthonormal
+//      columns in exact arithmetic (the left singular vectors of P).
+//   4. CholQR pass: Q = Q1 R2^{-1} with R2 = chol(Q1^T Q1) restores
+//      orthonormality lost to rounding; the coefficient M = W_k S_k R2^T gives
+//      P ~= Q M^T for the sibling matrices (Remark 4 / the svd steps of the
+//      HODLR and HBS figures).
+// These realize qr(.) and svd(., k | eps) of Secs. 2.2-2.3 / 2.6 for panels too
+// tall for one block.
+#include "hm_internal.h"
+
+namespace hm {
+namespace {
+
+template <typename T> struct Eps;
+template <> struct Eps<float> { static constexpr double v = 5.960464477539063e-08; };
+template <> struct Eps<double> { static constexpr double v = 1.1102230246251565e-16; };
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Householder QR of the stacked sources of one task; writes the c x c R
+// (row-major, upper triangle, zero rows past min(m, c)).
+template <typename T>
+__global__ __launch_bounds__(256) void k_tsqr(const TsqrTask* __restrict__ tasks,
+                                              const T* __restrict__ P, int64_t ldp, int c,
+                                              T* __restrict__ R, int ldm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* M = reinterpret_cast<T*>(smem_raw);  // column-major, ld = ldm
+  __shared__ double red[8];
+  __shared__ T sh_alpha, sh_beta;
+  const TsqrTask tk = tasks[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int m = 0;
+  for (int s = 0; s < tk.nsrc; ++s) {
+    if (tk.kind[s] == 0) {
+      const int rows = (int)(tk.r1[s] - tk.r0[s]);
+      for (int idx = tid; idx < rows * c; idx += 256) {
+        const int rr = idx % rows, col = idx / rows;
+        M[col * ldm + m + rr] = P[tk.r0[s] + rr + (int64_t)col * ldp];
+      }
+      m += rows;
+    } else {
+      const T* Rs = R + (int64_t)tk.slot[s] * c * c;
+      for (int idx = tid; idx < c * c; idx += 256) {
+        const int rr = idx / c, col = idx % c;
+        M[col * ldm + m + rr] = Rs[rr * c + col];
+      }
+      m += c;
+    }
+  }
+  __syncthreads();
+  const int steps = m < c ? m : c;
+  for (int j = 0; j < steps; ++j) {
+    T* mj = M + j * ldm;
+    T s = 0;
+    for (int i = j + tid; i < m; i += 256) s = fma(mj[i], mj[i], s);
+    s = warp_sum(s);
+    if (lane == 0) red[warp] = (double)s;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < 8; ++w) tot += red[w];
+      const double x0 = (double)mj[j];
+      const double nrm = sqrt(tot);
+      const double alpha = (x0 > 0.0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = tot - x0 * x0 + v0 * v0;
+      sh_alpha = (T)alpha;
+      sh_beta = (vtv > 0.0) ? (T)(2.0 / vtv) : (T)0;
+      mj[j] = (T)v0;
+    }
+    __syncthreads();
+    const T beta = sh_beta;
+    if (beta != (T)0) {
+      for (int k = j + 1 + warp; k < c; k += 8) {
+        T* mk = M + k * ldm;
+        T dot = 0;
+        for (int i = j + lane; i < m; i += 32) dot = fma(mj[i], mk[i], dot);
+        dot = warp_sum(dot);
+        const T f = beta * dot;
+        for (int i = j + lane; i < m; i += 32) mk[i] = fma(-f, mj[i], mk[i]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) mj[j] = sh_alpha;
+    __syncthreads();
+  }
+  T* Ro = R + (int64_t)tk.out_slot * c * c;
+  for (int idx = tid; idx < c * c; idx += 256) {
+    const int rr = idx / c, col = idx % c;
+    Ro[idx] = (rr <= col && rr < steps) ? M[col * ldm + rr] : (T)0;
+  }
+}
+
+// One-sided Jacobi SVD of R (c x c); round-robin pairing, one warp per pair.
+template <typename T>
+__global__ __launch_bounds__(512) void k_jacobi(const int32_t* __restrict__ node_slot,
+                                                const T* __restrict__ R, int c,
+                                                T* __restrict__ W, T* __restrict__ sigma) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Am = reinterpret_cast<T*>(smem_raw);  // column j at Am + j * c
+  T* Vm = Am + c * c;
+  __shared__ int rotated;
+  __shared__ double sv[128];
+  __shared__ int order[128];
+  const int node = blockIdx.x;
+  const T* Rs = R + (int64_t)node_slot[node] * c * c;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int idx = tid; idx < c * c; idx += blockDim.x) {
+    const int rr = idx / c, col = idx % c;
+    Am[col * c + rr] = Rs[idx];
+    Vm[col * c + rr] = (rr == col) ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  const int cp = (c + 1) & ~1;  // even number of slots; slot c (odd c) is a bye
+  // a pair is rotated while its correlation exceeds the rounding level of the
+  // length-c dot products that measure it
+  const T tol = (T)(4.0 * Eps<T>::v * sqrt((double)c));
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < cp - 1; ++step) {
+      for (int pi = warp; pi < cp / 2; pi += nwarps) {
+        // circle method: slot 0 fixed, the others rotate
+        const int a = pi, b = cp - 1 - pi;
+        const int p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
+        const int q = ((b - 1 + step) % (cp - 1)) + 1;
+        if (p >= c || q >= c) continue;
+        T* ap = Am + p * c;
+        T* aq = Am + q * c;
+        T alT = 0, beT = 0, gaT = 0;
+        for (int i = lane; i < c; i += 32) {
+          const T x = ap[i], y = aq[i];
+          alT = fma(x, x, alT); beT = fma(y, y, beT); gaT = fma(x, y, gaT);
+        }
+        const T al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
+        if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const T zeta = (be - al) / ((T)2 * ga);
+          const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+          const T tc = (T)1 / sqrt((T)1 + t * t), ts = tc * t;
+          for (int i = lane; i < c; i += 32) {
+            const T x = ap[i], y = aq[i];
+            ap[i] = tc * x - ts * y;
+            aq[i] = ts * x + tc * y;
+          }
+          T* vp = Vm + p * c;
+          T* vq = Vm + q * c;
+          for (int i = lane; i < c; i += 32) {
+            const T x = vp[i], y = vq[i];
+            vp[i] = tc * x - ts * y;
+            vq[i] = ts * x + tc * y;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  for (int j = warp; j < c; j += nwarps) {
+    T s = 0;
+    for (int i = lane; i < c; i += 32) s = fma(Am[j * c + i], Am[j * c + i], s);
+    s = warp_sum(s);
+    // a non-finite column sorts last (the samples' NaN/Inf flag reports it), so
+    // that the ranks below always form a permutation
+    if (lane == 0) sv[j] = isfinite((double)s) ? sqrt((double)s) : -1.0;
+  }
+  __syncthreads();
+  for (int j = tid; j < c; j += blockDim.x) {
+    int rk = 0;
+    for (int i = 0; i < c; ++i) rk += (sv[i] > sv[j]) || (sv[i] == sv[j] && i < j);
+    order[rk] = j;
+  }
+  __syncthreads();
+  T* Wn = W + (int64_t)node * c * c;
+  for (int idx = tid; idx < c * c; idx += blockDim.x) {
+    const int rr = idx % c, col = idx / c;
+    Wn[idx] = Vm[order[col] * c + rr];
+  }
+  for (int j = tid; j < c; j += blockDim.x) sigma[(int64_t)node * c + j] = (T)sv[order[j]];
+}
+
+template <typename T>
+__global__ void k_truncate(int nnodes, const T* __restrict__ W, const T* __restrict__ sigma,
+                           int c, int kcap, int mode, int kfix, double tol_scaled,
+                           double* __restrict__ eps_abs, int set_eps, double floor_rel,
+                           int32_t* __restrict__ rank, T* __restrict__ T1,
+                           int32_t* __restrict__ saturated) {
+  __shared__ int sk;
+  const int node = blockIdx.x;
+  const T* sg = sigma + (int64_t)node * c;
+  if (threadIdx.x == 0) {
+    const double s1 = (double)sg[0];
+    double thr = floor_rel * s1;
+    if (mode == 1) {
+      double eps;
+      if (set_eps) {
+        double nu = 0.0;
+        for (int i = 0; i < nnodes; ++i) nu = fmax(nu, (double)sigma[(int64_t)i * c]);
+        eps = tol_scaled * nu;
+        if (node == 0) *eps_abs = eps;
+      } else {
+        eps = *eps_abs;
+      }
+      thr = fmax(thr, eps);
+    }
+    int k = 0;
+    const int lim = c < kcap ? c : kcap;
+    while (k < lim && (double)sg[k] > thr) ++k;
+    if (mode == 2) {
+      int kk = kfix < lim ? kfix : lim;
+      while (kk > 0 && !((double)sg[kk - 1] > 0.0)) --kk;
+      k = kk;
+    }
+    if (mode == 1 && k == lim && lim < c && (double)sg[lim] > thr) atomicAdd(saturated, 1);
+    if (mode == 1 && k == lim && lim == c) atomicAdd(saturated, 1);
+    if (k < 1 && (double)sg[0] > 0.0) k = 1;
+    rank[node] = k;
+    sk = k;
+  }
+  __syncthreads();
+  const int k = sk;
+  const T* Wn = W + (int64_t)node * c * c;
+  T* Tn = T1 + (int64_t)node * c * kcap;
+  for (int idx = threadIdx.x; idx < c * kcap; idx += blockDim.x) {
+    const int rr = idx % c, col = idx / c;
+    Tn[idx] = (col < k) ? (T)((double)Wn[rr + col * c] / (double)sg[col]) : (T)0;
+  }
+}
+
+// CholQR: G (kcap x kcap) = Q1^T Q1 -> R2 = chol(G) (dead pivots dropped),
+// T2 = R2^{-1}; optionally M = W_k S_k R2^T (c x kcap).
+template <typename T>
+__global__ __launch_bounds__(256) void k_cholqr(const T* __restrict__ G, int kcap,
+                                                const int32_t* __restrict__ rank,
+                                                T* __restrict__ T2, const T* __restrict__ W,
+                                                const T* __restrict__ sigma, int c,
+                                                T* __restrict__ M, int want_m) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Rm = reinterpret_cast<T*>(smem_raw);  // kcap x kcap, row-major upper
+  T* Ti = Rm + kcap * kcap;                 // kcap x kcap inverse, row-major
+  __shared__ int dead[128];
+  const int node = blockIdx.x;
+  const int k = rank[node];
+  const T* Gn = G + (int64_t)node * kcap * kcap;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < kcap * kcap; idx += blockDim.x) {
+    const int i = idx / kcap, j = idx % kcap;
+    Rm[idx] = (i < k && j < k) ? Gn[i + j * kcap] : (T)0;
+    Ti[idx] = 0;
+  }
+  for (int j = tid; j < kcap; j += blockDim.x) dead[j] = (j >= k);
+  __syncthreads();
+  double dmax = 0.0;
+  for (int j = 0; j < k; ++j) dmax = fmax(dmax, (double)Rm[j * kcap + j]);
+  // right-looking Cholesky, upper factor in Rm; a pivot below 64 eps max(diag)
+  // marks a dependent column, which is dropped
+  __shared__ double piv;
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      const double d = (double)Rm[j * kcap + j];
+      if (dead[j] || !(d > 64.0 * Eps<T>::v * dmax)) {
+        dead[j] = 1;
+        piv = 0.0;
+      } else {
+        piv = sqrt(d);
+      }
+    }
+    __syncthreads();
+    const T pj = (T)piv;
+    if (pj == (T)0) {
+      for (int l = j + tid; l < kcap; l += blockDim.x) Rm[j * kcap + l] = (l == j) ? (T)1 : (T)0;
+      __syncthreads();
+      continue;
+    }
+    for (int l = j + tid; l < k; l += blockDim.x) Rm[j * kcap + l] /= pj;  // R(j,j) = sqrt(d)
+    __syncthreads();
+    // trailing update of the upper triangle: G(a,b) -= R(j,a) R(j,b), a <= b
+    const int rem = k - j - 1;
+    for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+      const int a = j + 1 + idx / rem, b = j + 1 + idx % rem;
+      if (a <= b) Rm[a * kcap + b] = fma(-Rm[j * kcap + a], Rm[j * kcap + b], Rm[a * kcap + b]);
+    }
+    __syncthreads();
+  }
+  // inverse of the upper-triangular R2, one column per thread; dead columns -> 0
+  for (int l = tid; l < kcap; l += blockDim.x) {
+    if (l >= k || dead[l]) continue;
+    Ti[l * kcap + l] = (T)1 / Rm[l * kcap + l];
+    for (int i = l - 1; i >= 0; --i) {
+      if (dead[i]) continue;
+      T s = 0;
+      for (int mm = i + 1; mm <= l; ++mm) s = fma(Rm[i * kcap + mm], Ti[mm * kcap + l], s);
+      Ti[i * kcap + l] = -s / Rm[i * kcap + i];
+    }
+  }
+  __syncthreads();
+  T* T2n = T2 + (int64_t)node * kcap * kcap;
+  for (int idx = tid; idx < kcap * kcap; idx += blockDim.x) {
+    const int i = idx % kcap, j = idx / kcap;  // column-major output
+    T2n[idx] = Ti[i * kcap + j];
+  }
+  if (want_m) {
+    // M(row, col) = sum_{m >= col} W(row, m) s_m R2(col, m), live columns only
+    const T* Wn = W + (int64_t)node * c * c;
+    const T* sg = sigma + (int64_t)node * c;
+    T* Mn = M + (int64_t)node * c * kcap;
+    for (int idx = tid; idx < c * kcap; idx += blockDim.x) {
+      const int row = idx % c, col = idx / c;
+      T s = 0;
+      if (col < k && !dead[col])
+        for (int mm = col; mm < k; ++mm)
+          if (!dead[mm]) s = fma(Wn[row + mm * c] * sg[mm], Rm[col * kcap + mm], s);
+      Mn[idx] = s;
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_tsqr(const TsqrTask* tasks, int ntasks, int rows_max, const T* P, int64_t ldp, int c,
+                 T* R, cudaStream_t st) {
+  const int ldm = rows_max;
+  const size_t smem = (size_t)ldm * c * sizeof(T);
+  cudaFuncSetAttribute(k_tsqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_tsqr<T><<<ntasks, 256, smem, st>>>(tasks, P, ldp, c, R, ldm);
+}
+
+template <typename T>
+void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W, T* sigma,
+                   cudaStream_t st) {
+  const size_t smem = (size_t)2 * c * c * sizeof(T);
+  cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int threads = ((c / 2 + 31) / 32) * 32 * 32;
+  if (threads > 512) threads = 512;
+  if (threads < 64) threads = 64;
+  k_jacobi<T><<<nnodes, threads, smem, st>>>(node_slot, R, c, W, sigma);
+}
+
+template <typename T>
+void launch_truncate(int nnodes, const T* W, const T* sigma, int c, int kcap, int mode, int kfix,
+                     double tol_scaled, double* eps_abs, int set_eps, double floor_rel,
+                     int32_t* rank, T* T1, int32_t* saturated, cudaStream_t st) {
+  k_truncate<T><<<nnodes, 128, 0, st>>>(nnodes, W, sigma, c, kcap, mode, kfix, tol_scaled,
+                                        eps_abs, set_eps, floor_rel, rank, T1, saturated);
+}
+
+template <typename T>
+void launch_cholqr(int nnodes, const T* G, int kcap, const int32_t* rank, T* T2, const T* W,
+                   const T* sigma, int c, T* M, int want_m, cudaStream_t st) {
+  const size_t smem = (size_t)2 * kcap * kcap * sizeof(T);
+  cudaFuncSetAttribute(k_cholqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_cholqr<T><<<nnodes, 256, smem, st>>>(G, kcap, rank, T2, W, sigma, c, M, want_m);
+}
+
+#define HM_INST(T)                                                                           \
+  template void launch_tsqr<T>(const TsqrTask*, int, int, const T*, int64_t, int, T*,        \
+                               cudaStream_t);                                                \
+  template void launch_jacobi<T>(const int32_t*, int, const T*, int, T*, T*, cudaStream_t);  \
+  template void launch_truncate<T>(int, const T*, const T*, int, int, int, int, double,      \
+                                   double*, int, double, int32_t*, T*, int32_t*,             \
+                                   cudaStream_t);                                            \
+  template void launch_cholqr<T>(int, const T*, int, const int32_t*, T*, const T*, const T*, \
+                                 int, T*, int, cudaStream_t);
+HM_INST(float)
+HM_INST(double)
+#undef HM_INST
+
+}  // namespace hm

@@ -1,0 +1,196 @@
+// Segmented (per tree node) tall-skinny products, the workhorses of the peel
+// and of the per-node linear algebra:
+//   seg_tn:  out[node] = A(I_node, :)^T B(I_node, :)   (projections V^T x of the
+//            HODLR product, Sec. 2.8; Gram matrices; the short-basis products
+//            U_alpha^* U_tau(J_alpha,:) of Fig. "A basic scheme for compressing an
+//            HBS matrix")
+//   seg_nn:  Y(I_node, :) = alpha P(I_node, :) C[node'] + beta Y(I_node, :)
+//            (expansions U t, basis updates U <- U \hat U, Q = P T).
+// A node's rows are split into chunks; uneven node sizes go into one launch.
+// Column offsets can depend on the node's parity (left child / right child), which
+// is how the packed test matrices [Omega_2 | Omega_1] are addressed.
+#include "hm_internal.h"
+
+namespace hm {
+namespace {
+
+constexpr int TN_ROWS = 32;   // rows staged per step
+constexpr int TN_MAX = 128;   // max ka, kb
+
+// Partial products of one chunk (<= 256 rows).  256 threads in a 16 x 16 grid,
+// 8 x 8 outputs each.
+template <typename T>
+__global__ __launch_bounds__(256) void k_seg_tn_partial(
+    const Chunk* __restrict__ chunks, const T* __restrict__ A, int64_t lda, int aoff_e,
+    int aoff_o, int ka, const T* __restrict__ B, int64_t ldb, int boff_e, int boff_o, int kb,
+    double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);          // [TN_ROWS][TN_MAX + 1]
+  T* Bs = As + TN_ROWS * (TN_MAX + 1);              // [TN_ROWS][TN_MAX + 1]
+  const Chunk ch = chunks[blockIdx.x];
+  const int aoff = (ch.node & 1) ? aoff_o : aoff_e;
+  const int boff = (ch.node & 1) ? boff_o : boff_e;
+  const int tid = threadIdx.x;
+  const int ti = tid >> 4, tj = tid & 15;
+  T acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0;
+  for (int64_t r0 = ch.r0; r0 < ch.r1; r0 += TN_ROWS) {
+    const int rows = (int)((ch.r1 - r0) < TN_ROWS ? (ch.r1 - r0) : TN_ROWS);
+    for (int idx = tid; idx < TN_ROWS * TN_MAX; idx += 256) {
+      const int rr = idx % TN_ROWS, c = idx / TN_ROWS;
+      As[rr * (TN_MAX + 1) + c] =
+          (rr < rows && c < ka) ? A[r0 + rr + (int64_t)(aoff + c) * lda] : (T)0;
+      Bs[rr * (TN_MAX + 1) + c] =
+          (rr < rows && c < kb) ? B[r0 + rr + (int64_t)(boff + c) * ldb] : (T)0;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < rows; ++rr) {
+      T a[8], b[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = As[rr * (TN_MAX + 1) + ti * 8 + i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b[j] = Bs[rr * (TN_MAX + 1) + tj * 8 + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* out = partial + (int64_t)blockIdx.x * ka * kb;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int ii = ti * 8 + i, jj = tj * 8 + j;
+      if (ii < ka && jj < kb) out[ii + jj * ka] = (double)acc[i][j];
+    }
+}
+
+// out[node] = sum of the node's chunk partials, in chunk order (deterministic).
+template <typename T>
+__global__ void k_seg_tn_reduce(const double* __restrict__ partial,
+                                const int32_t* __restrict__ chunk_begin, int ka, int kb,
+                                T* __restrict__ out) {
+  const int node = blockIdx.y;
+  const int c0 = chunk_begin[node], c1 = chunk_begin[node + 1];
+  const int m = ka * kb;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = c0; c < c1; ++c) s += partial[(int64_t)c * m + e];
+    out[(int64_t)node * m + e] = (T)s;
+  }
+}
+
+constexpr int NN_ROWS = 64;
+constexpr int NN_MAX = 128;
+
+// One chunk of <= 64 rows.  Warp w owns output columns [16w, 16w + 16); lane
+// owns rows lane and lane + 32.  P is staged before any write (in-place safe).
+template <typename T>
+__global__ __launch_bounds__(256) void k_seg_nn(
+    const Chunk* __restrict__ chunks, int node0, const T* P, int64_t ldp, int poff_e,
+    int poff_o, int kin, const T* __restrict__ C, int64_t cstride, int cld, int cflip, T* Y,
+    int64_t ldy, int yoff_e, int yoff_o, int kout, T alpha, T beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ps = reinterpret_cast<T*>(smem_raw);   // [NN_MAX][NN_ROWS]
+  T* Cs = Ps + NN_MAX * NN_ROWS;             // [NN_MAX][NN_MAX]
+  const Chunk ch = chunks[blockIdx.x];
+  const int rows = (int)(ch.r1 - ch.r0);
+  const int poff = (ch.node & 1) ? poff_o : poff_e;
+  const int yoff = (ch.node & 1) ? yoff_o : yoff_e;
+  const T* Cn = C + (int64_t)((ch.node ^ cflip) - node0) * cstride;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < kin * NN_ROWS; idx += 256) {
+    const int rr = idx % NN_ROWS, k = idx / NN_ROWS;
+    Ps[k * NN_ROWS + rr] = (rr < rows) ? P[ch.r0 + rr + (int64_t)(poff + k) * ldp] : (T)0;
+  }
+  for (int idx = tid; idx < kin * NN_MAX; idx += 256) {
+    const int j = idx % NN_MAX, k = idx / NN_MAX;
+    Cs[k * NN_MAX + j] = (j < kout) ? Cn[k + (int64_t)j * cld] : (T)0;
+  }
+  __syncthreads();
+  const int lane = tid & 31, w = tid >> 5;
+  T acc[2][16];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[i][j] = 0;
+  for (int k = 0; k < kin; ++k) {
+    const T a0 = Ps[k * NN_ROWS + lane], a1 = Ps[k * NN_ROWS + lane + 32];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const T c = Cs[k * NN_MAX + w * 16 + j];
+      acc[0][j] = fma(a0, c, acc[0][j]);
+      acc[1][j] = fma(a1, c, acc[1][j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int col = w * 16 + j;
+    if (col >= kout) continue;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int rr = lane + 32 * i;
+      if (rr >= rows) continue;
+      T* yp = Y + ch.r0 + rr + (int64_t)(yoff + col) * ldy;
+      *yp = (beta == (T)0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*yp);
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_seg_tn(const Chunk* chunks, int nchunks, const int32_t* chunk_begin, int nnodes,
+                   int node0, const T* A, int64_t lda, int aoff_even, int aoff_odd, int ka,
+                   const T* B, int64_t ldb, int boff_even, int boff_odd, int kb, double* partial,
+                   T* out, cudaStream_t st) {
+  (void)node0;
+  const size_t smem = 2 * TN_ROWS * (TN_MAX + 1) * sizeof(T);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_seg_tn_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    configured = true;
+  }
+  k_seg_tn_partial<T><<<nchunks, 256, smem, st>>>(chunks, A, lda, aoff_even, aoff_odd, ka, B,
+                                                  ldb, boff_even, boff_odd, kb, partial);
+  const int m = ka * kb;
+  dim3 grid((unsigned)((m + 255) / 256), (unsigned)nnodes);
+  k_seg_tn_reduce<T><<<grid, 256, 0, st>>>(partial, chunk_begin, ka, kb, out);
+}
+
+template <typename T>
+void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int64_t ldp,
+                   int poff_even, int poff_odd, int kin, const T* C, int64_t cstride, int cld,
+                   int cflip, T* Y, int64_t ldy, int yoff_even, int yoff_odd, int kout, T alpha,
+                   T beta, cudaStream_t st) {
+  const size_t smem = (size_t)(NN_MAX * NN_ROWS + NN_MAX * NN_MAX) * sizeof(T);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_seg_nn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = true;
+  }
+  k_seg_nn<T><<<nchunks, 256, smem, st>>>(chunks, node0, P, ldp, poff_even, poff_odd, kin, C,
+                                          cstride, cld, cflip, Y, ldy, yoff_even, yoff_odd, kout,
+                                          alpha, beta);
+}
+
+template void launch_seg_tn<float>(const Chunk*, int, const int32_t*, int, int, const float*,
+                                   int64_t, int, int, int, const float*, int64_t, int, int, int,
+                                   double*, float*, cudaStream_t);
+template void launch_seg_tn<double>(const Chunk*, int, const int32_t*, int, int, const double*,
+                                    int64_t, int, int, int, const double*, int64_t, int, int,
+                                    int, double*, double*, cudaStream_t);
+template void launch_seg_nn<float>(const Chunk*, int, int, const float*, int64_t, int, int, int,
+                                   const float*, int64_t, int, int, float*, int64_t, int, int,
+                                   int, float, float, cudaStream_t);
+template void launch_seg_nn<double>(const Chunk*, int, int, const double*, int64_t, int, int,
+                                    int, const double*, int64_t, int, int, double*, int64_t, int,
+                                    int, int, double, double, cudaStream_t);
+
+}  // namespace hm

@@ -1,0 +1,107 @@
+"""GPU parity of the HBS / HBS-ID path (Sec. 4) against the FP64 oracle,
+through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import hbs as ohbs
+from oracle import hodlr as ohodlr
+from oracle.tree import build_tree
+
+pytestmark = pytest.mark.gpu
+hm = pytest.importorskip("paper_1503_07152_gb300")
+DEV = "cuda:0"
+
+
+def synthetic_hbs(N, m, k, seed):
+    """Dense matrix with exact nested bases of rank k (definition of Sec. 2.9)."""
+    t = build_tree(N, m)
+    rng = np.random.default_rng(seed)
+    U, V = {}, {}
+    for tau in t.leaves():
+        U[tau] = rng.standard_normal((int(t.size[tau]), k))
+        V[tau] = rng.standard_normal((int(t.size[tau]), k))
+    for lev in range(t.L - 1, 0, -1):
+        for tau in t.level_nodes(lev):
+            a, b = 2 * tau, 2 * tau + 1
+            for Lb in (U, V):
+                S = rng.standard_normal((2 * k, k)) / np.sqrt(2 * k)
+                Lb[tau] = np.vstack([Lb[a] @ S[:k], Lb[b] @ S[k:]])
+    A = np.zeros((N, N))
+    for lev in range(1, t.L + 1):
+        for a in t.level_nodes(lev):
+            A[t.rows(a), t.rows(a ^ 1)] = U[a] @ rng.standard_normal((k, k)) @ V[a ^ 1].T
+    for tau in t.leaves():
+        n = int(t.size[tau])
+        A[t.rows(tau), t.rows(tau)] = rng.standard_normal((n, n))
+    return A
+
+
+def run_gpu(A, N, m, prec, **kw):
+    dtype = torch.float64 if prec == 0 else torch.float32
+    At = torch.from_numpy(np.ascontiguousarray(A)).to(DEV, dtype)
+    op = hm.hm_dense_operator_create(At)
+    h = hm.hm_compress_hbs(op, hm.Tree(N, m), prec=prec, hbs_id=1, **kw)
+    out = torch.empty((N, N), device=DEV, dtype=dtype)
+    hm.hm_reconstruct_block(h, 0, N, 0, N, out)
+    torch.cuda.synchronize()
+    return h, out.double().cpu().numpy().T, At
+
+
+@pytest.mark.parametrize("N,m,k", [(512, 32, 5), (700, 40, 4)])
+def test_hbsid_exact_rank_fp64(N, m, k):
+    A = synthetic_hbs(N, m, k, seed=21)
+    h, Ag, At = run_gpu(A, N, m, 0, tol=1e-12, r=k + 10, seed=3)
+    o = ohbs.compress(ohodlr.dense_apply_fn(A), build_tree(N, m), r=k + 10, seed=3)
+    g = ohbs.to_hbsid(o, tol=1e-12)
+    Ao = ohbs.hbsid_dense(g)
+    nA = np.linalg.norm(A)
+    assert np.linalg.norm(Ag - A) / nA < 1e-10
+    assert np.linalg.norm(Ag - Ao) / nA < 1e-10
+    assert h.info["max_rank"] == k
+    assert h.info["cols_A"] == 2 * (k + 10) * build_tree(N, m).L + build_tree(N, m).n_max
+
+
+def test_hbsid_fixed_rank_parity_fp64():
+    N, m, k = 1024, 64, 6
+    A = synthetic_hbs(N, m, k, seed=5)
+    h, Ag, At = run_gpu(A, N, m, 0, k=k, p=10, seed=4)
+    o = ohbs.compress(ohodlr.dense_apply_fn(A), build_tree(N, m), r=k + 10, seed=4)
+    Ao = ohbs.hbsid_dense(ohbs.to_hbsid(o, k=k))
+    nA = np.linalg.norm(A)
+    assert np.linalg.norm(Ag - Ao) / nA < 1e-12
+    assert np.linalg.norm(Ag - A) / nA < 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_hbsid_log_kernel(prec):
+    N, m, r = 2048, 128, 40
+    A = W.log_kernel(N)
+    A64 = A.astype(np.float64)
+    h, Ag, At = run_gpu(A if prec == 1 else A64, N, m, prec, tol=1e-7, r=r, seed=2)
+    o = ohbs.compress(ohodlr.dense_apply_fn(A64), build_tree(N, m), r=r, seed=2, mixed=(prec == 1))
+    Ao = ohbs.hbsid_dense(ohbs.to_hbsid(o, tol=1e-7))
+    nA = np.linalg.norm(A64)
+    e_gpu = np.linalg.norm(Ag - A64) / nA
+    e_par = np.linalg.norm(Ag - Ao) / nA
+    e_or = np.linalg.norm(Ao - A64) / nA
+    print(f"HBS-ID prec={prec}: GPU err {e_gpu:.3e}, vs oracle {e_par:.3e}, oracle err {e_or:.3e}, "
+          f"ranks {h.info['min_rank']}..{h.info['max_rank']}")
+    if prec == 0:
+        assert e_gpu < 1e-7 and e_par < 1e-7
+    else:
+        assert e_par < 1e-6 and e_gpu < 1e-6
+
+
+def test_hbsid_apply_transpose():
+    N, m = 1024, 64
+    A = W.log_kernel(N).astype(np.float64)
+    h, Ag, At = run_gpu(A, N, m, 0, tol=1e-9, r=40, seed=6)
+    X = np.random.default_rng(1).standard_normal((N, 3))
+    for trans in (0, 1):
+        Y = torch.empty((3, N), device=DEV, dtype=torch.float64)
+        hm.hm_apply(h, trans, torch.from_numpy(np.ascontiguousarray(X.T)).to(DEV), Y)
+        torch.cuda.synchronize()
+        want = (Ag.T if trans else Ag) @ X
+        assert np.linalg.norm(Y.cpu().numpy().T - want) <= 1e-12 * np.linalg.norm(want)

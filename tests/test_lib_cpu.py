@@ -1,0 +1,58 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point declared in include/hm.h, builds the tree bit-exactly like the
+oracle, and rejects bad arguments before touching a device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from oracle.tree import build_tree
+
+hm = pytest.importorskip("paper_1503_07152_gb300")
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hm_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(hm.lib, name), name
+        assert C.cast(getattr(hm.lib, name), C.c_void_p).value
+
+
+@pytest.mark.parametrize("N,m", [(1, 4), (7, 4), (400, 50), (1000, 64), (2112, 64), (65536, 256),
+                                 (262144, 256)])
+def test_tree_matches_oracle_bit_exact(N, m):
+    t = hm.Tree(N, m)
+    o = build_tree(N, m)
+    assert t.levels == o.L
+    for node in range(1, 2 ** (o.L + 1)):
+        assert t.node(node) == (int(o.start[node]), int(o.size[node]))
+
+
+def test_argument_errors_before_device_use():
+    with pytest.raises(hm.HmError) as e:
+        hm.Tree(0, 4)
+    assert e.value.status == 1
+    t = hm.Tree(100, 10)
+    with pytest.raises(hm.HmError):
+        t.node(0)
+    with pytest.raises(hm.HmError):
+        t.node(2 ** (t.levels + 1))
+    # compress with mismatched operator size fails in argument checking
+    op = hm.callback_operator(99, lambda *a: 0)
+    with pytest.raises(hm.HmError) as e:
+        hm.hm_compress_hodlr(op, t, k=4, p=2, stream=0)
+    assert e.value.status == 1
+    op = hm.callback_operator(100, lambda *a: 0)
+    with pytest.raises(hm.HmError):
+        hm.hm_compress_hodlr(op, t, tol=2.0, r=8, stream=0)
+    assert hm.hm_version().startswith("hm")
