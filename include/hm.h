@@ -289,6 +289,9 @@ hm_status hm_gen_log_kernel(float* A, int64_t n, int64_t lda, void* stream);
 const char* hm_last_error(void);
 /* Library version string. */
 const char* hm_version(void);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (black-box GEMMs of the dense operator included). */
+int64_t hm_launch_count(void);
 
 #ifdef __cplusplus
 }

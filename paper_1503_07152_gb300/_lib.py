@@ -70,6 +70,7 @@ _sig = {
                                 C.c_int),
     "hm_last_error": ([], C.c_char_p),
     "hm_version": ([], C.c_char_p),
+    "hm_launch_count": ([], C.c_int64),
 }
 for _name, (_args, _ret) in _sig.items():
     _f = getattr(lib, _name)
@@ -109,6 +110,10 @@ def _colmajor(t: torch.Tensor, n: int, name: str):
 
 def hm_version() -> str:
     return lib.hm_version().decode()
+
+
+def hm_launch_count() -> int:
+    return int(lib.hm_launch_count())
 
 
 class Tree:

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 #include "hm_api.h"
@@ -16,6 +17,9 @@ void set_error(const std::string& msg) {
 }
 const char* get_error() { return g_err.c_str(); }
 void clear_error() { g_err.clear(); }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 hm_status check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
@@ -277,6 +281,7 @@ extern "C" {
 
 const char* hm_last_error(void) { return get_error(); }
 const char* hm_version(void) { return "hm 0.1 (sm_103a)"; }
+int64_t hm_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 hm_status hm_tree_create(int64_t n, int32_t leaf_size, hm_tree** out) {
   clear_error();

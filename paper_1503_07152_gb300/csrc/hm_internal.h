@@ -32,6 +32,8 @@ void clear_error();
   } while (0)
 
 hm_status check_launch(const char* what);
+// Process-wide count of kernels launched by the library (all devices).
+void count_launches(int n);
 
 // Row chunk of one tree node: rows [r0, r1) of node `node`.
 struct Chunk {

@@ -255,6 +255,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 template <typename T>
 void launch_gauss_fill(T* X, int64_t ldx, int64_t n, int r, int level, uint64_t seed, bool bf16,
                        const int64_t* d_start, int L, cudaStream_t st) {
+  count_launches(1);
   (void)L;
   dim3 grid(blocks_for(n, 256), (unsigned)((r + 1) / 2));
   k_gauss_fill<T><<<grid, 256, 0, st>>>(X, ldx, n, r, level, (uint32_t)(seed & 0xffffffffu),
@@ -264,6 +265,7 @@ void launch_gauss_fill(T* X, int64_t ldx, int64_t n, int r, int level, uint64_t 
 template <typename T>
 void launch_identity_probe(T* X, int64_t ldx, int64_t n, int nmax, const int64_t* d_start, int L,
                            cudaStream_t st) {
+  count_launches(1);
   dim3 grid(blocks_for(n, 256), (unsigned)nmax);
   k_identity_probe<T><<<grid, 256, 0, st>>>(X, ldx, n, nmax, d_start, L);
 }
@@ -271,6 +273,7 @@ void launch_identity_probe(T* X, int64_t ldx, int64_t n, int nmax, const int64_t
 template <typename T>
 void launch_scatter_probe(const T* U, int64_t ldu, T* X, int64_t ldx, int64_t n, int r,
                           int level_nodes, const int64_t* d_start, int L, cudaStream_t st) {
+  count_launches(1);
   (void)L;
   dim3 grid(blocks_for(n, 256), (unsigned)r);
   k_scatter_probe<T><<<grid, 256, 0, st>>>(U, ldu, X, ldx, n, r, level_nodes, d_start);
@@ -279,6 +282,7 @@ void launch_scatter_probe(const T* U, int64_t ldu, T* X, int64_t ldx, int64_t n,
 template <typename T>
 void launch_gather_sample(const T* Y, int64_t ldy, T* P, int64_t ldp, int64_t n, int r,
                           int level_nodes, const int64_t* d_start, int L, cudaStream_t st) {
+  count_launches(1);
   (void)L;
   dim3 grid(blocks_for(n, 256), (unsigned)r);
   k_gather_sample<T><<<grid, 256, 0, st>>>(Y, ldy, P, ldp, n, r, level_nodes, d_start);
@@ -287,6 +291,7 @@ void launch_gather_sample(const T* Y, int64_t ldy, T* P, int64_t ldp, int64_t n,
 template <typename T>
 void launch_extract_diag(const T* Y, int64_t ldy, T* D, int nmax, const int64_t* d_start,
                          const int64_t* d_size, int L, cudaStream_t st) {
+  count_launches(1);
   dim3 grid(blocks_for((int64_t)nmax * nmax, 256) < 64 ? blocks_for((int64_t)nmax * nmax, 256)
                                                        : 64,
             1u << L);
@@ -297,6 +302,7 @@ template <typename T>
 void launch_blockdiag_apply(const T* D, int nmax, int trans, const T* X, int64_t ldx, T* Y,
                             int64_t ldy, int64_t ncols, const int64_t* d_start,
                             const int64_t* d_size, int L, cudaStream_t st) {
+  count_launches(1);
   dim3 grid(1u << L, (unsigned)ncols);
   k_blockdiag_apply<T><<<grid, 256, nmax * sizeof(T), st>>>(D, nmax, trans, X, ldx, Y, ldy,
                                                             d_start, d_size, L);
@@ -305,6 +311,7 @@ void launch_blockdiag_apply(const T* D, int nmax, int trans, const T* X, int64_t
 template <typename T>
 void launch_fill(T* p, int64_t count, T v, cudaStream_t st) {
   if (count <= 0) return;
+  count_launches(1);
   unsigned g = blocks_for(count, 256);
   k_fill<T><<<g > 4096 ? 4096 : g, 256, 0, st>>>(p, count, v);
 }
@@ -313,12 +320,14 @@ template <typename T>
 void launch_copy_cols(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t rows, int64_t cols,
                       cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return;
+  count_launches(1);
   dim3 grid(blocks_for(rows, 256), (unsigned)cols);
   k_copy_cols<T><<<grid, 256, 0, st>>>(src, lds, dst, ldd, rows);
 }
 
 template <typename T>
 void launch_identity_cols(T* Y, int64_t ldy, int64_t n, int64_t c0, int64_t w, cudaStream_t st) {
+  count_launches(1);
   dim3 grid(blocks_for(n, 256), (unsigned)w);
   k_identity_cols<T><<<grid, 256, 0, st>>>(Y, ldy, n, c0);
 }
@@ -326,6 +335,7 @@ void launch_identity_cols(T* Y, int64_t ldy, int64_t n, int64_t c0, int64_t w, c
 template <typename T>
 void launch_frob_tile(const T* A, int64_t lda, const T* Ac, int64_t ldc, int64_t n, int64_t c0,
                       int64_t w, double* acc, cudaStream_t st) {
+  count_launches(1);
   unsigned g = blocks_for(n * w, 256);
   k_frob_tile<T><<<g > 2048 ? 2048 : g, 256, 0, st>>>(A, lda, Ac, ldc, n, c0, w, acc);
 }
@@ -333,6 +343,7 @@ void launch_frob_tile(const T* A, int64_t lda, const T* Ac, int64_t ldc, int64_t
 int32_t nonfinite_check_launch(const void* p, int64_t count, int is_double, int32_t* flag,
                                cudaStream_t st) {
   if (count <= 0) return 0;
+  count_launches(1);
   unsigned g = blocks_for(count, 256);
   if (g > 2048) g = 2048;
   if (is_double) k_nonfinite<double><<<g, 256, 0, st>>>((const double*)p, count, flag);
@@ -341,6 +352,7 @@ int32_t nonfinite_check_launch(const void* p, int64_t count, int is_double, int3
 }
 
 void launch_gen_log_kernel(float* A, int64_t n, int64_t lda, cudaStream_t st) {
+  count_launches(1);
   unsigned gx = blocks_for(n, 256);
   if (gx > 64) gx = 64;
   dim3 grid(gx, (unsigned)(n < 32768 ? n : 32768));

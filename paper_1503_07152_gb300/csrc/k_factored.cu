@@ -183,6 +183,7 @@ size_t factored_scratch_bytes(const hm_tree* t, int k) {
 void launch_factored_apply(const hm_tree* t, int k, const float* U, const float* V,
                            const float* D, int trans, const float* x, float* y, float* scratch,
                            cudaStream_t st) {
+  count_launches(3);
   const int L = t->L;
   const int nodes = 1 << (L + 1);
   float* partial = scratch;
@@ -201,6 +202,7 @@ void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const floa
                              const float* D, const float* x, const float* res, float scale,
                              float* gx, float* gU, float* gV, float* gD, float* scratch,
                              cudaStream_t st) {
+  count_launches(3);
   const int L = t->L;
   const int nodes = 1 << (L + 1);
   float* partial = scratch;

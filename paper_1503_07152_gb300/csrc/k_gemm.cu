@@ -134,6 +134,7 @@ __global__ __launch_bounds__(256) void k_dense_gemm(const T* __restrict__ A, int
 template <typename T>
 void launch_dense_gemm(const T* A, int64_t lda, int trans, int64_t n, int64_t ncols, const T* X,
                        int64_t ldx, T* Y, int64_t ldy, uint8_t* flags, cudaStream_t st) {
+  count_launches(flags ? 2 : 1);
   constexpr int BK = KTile<T>::BK;
   const int nct = (int)((ncols + BN - 1) / BN);
   const int nkt = (int)((n + BK - 1) / BK);

@@ -266,6 +266,7 @@ template <typename T>
 void launch_gather_parent_scaled(const T* U, int64_t ldu, T* P, int64_t ldp, int64_t n, int r,
                                  int lv, const int64_t* d_start, const T* y, int col0,
                                  cudaStream_t st) {
+  count_launches(1);
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)r);
   k_gather_parent_scaled<T><<<grid, 256, 0, st>>>(U, ldu, P, ldp, n, r, lv, d_start, y, col0);
 }
@@ -273,6 +274,7 @@ void launch_gather_parent_scaled(const T* U, int64_t ldu, T* P, int64_t ldp, int
 template <typename T>
 void launch_batched_gemm(const GemmItem* items, int count, T alpha, T beta, cudaStream_t st) {
   if (count <= 0) return;
+  count_launches(1);
   k_batched_gemm<T><<<count, 256, 0, st>>>(items, alpha, beta);
 }
 
@@ -280,6 +282,7 @@ template <typename TS, typename TD>
 void launch_node_copy(int nnodes, int node0, const TS* src, int64_t sstride, int sld, TD* dst,
                       int64_t dstride, int dld, int rows, int cols, int flip, cudaStream_t st) {
   if (nnodes <= 0) return;
+  count_launches(1);
   k_node_copy<TS, TD><<<nnodes, 256, 0, st>>>(node0, src, sstride, sld, dst, dstride, dld, rows,
                                               cols, flip);
 }
@@ -287,17 +290,20 @@ void launch_node_copy(int nnodes, int node0, const TS* src, int64_t sstride, int
 template <typename T>
 void launch_id_prep_leaf(const T* U, int64_t ldu, const int64_t* d_start, const int64_t* d_size,
                          int L, const T* y, int r, double* Yt, int ncmax, cudaStream_t st) {
+  count_launches(1);
   k_id_prep_leaf<T><<<1 << L, 256, 0, st>>>(U, ldu, d_start, d_size, L, y, r, Yt, ncmax);
 }
 
 template <typename T>
 void launch_id_prep_parent(int nnodes, int node0, const double* Utmp, const T* y, int r,
                            double* Yt, cudaStream_t st) {
+  count_launches(1);
   k_id_prep_parent<T><<<nnodes, 256, 0, st>>>(node0, Utmp, y, r, Yt);
 }
 
 void launch_pivqr_id(int nnodes, const double* Yt, int r, int nc, double eps, int kcap,
                      int32_t* k, int32_t* J, double* T, cudaStream_t st) {
+  count_launches(1);
   const size_t smem = sizeof(double) * ((size_t)r * nc + nc) + sizeof(int) * nc;
   cudaFuncSetAttribute(k_pivqr_id, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_pivqr_id<<<nnodes, 256, smem, st>>>(Yt, r, nc, eps, kcap, k, J, T);
@@ -306,11 +312,13 @@ void launch_pivqr_id(int nnodes, const double* Yt, int r, int nc, double eps, in
 template <typename T>
 void launch_usamp_leaf(const T* U, int64_t ldu, const int64_t* d_start, int L, const int32_t* J,
                        int r, double* Us, int64_t* skel, cudaStream_t st) {
+  count_launches(1);
   k_usamp_leaf<T><<<1 << L, 128, 0, st>>>(U, ldu, d_start, L, J, r, Us, skel);
 }
 
 void launch_usamp_parent(int nnodes, int node0, const double* Utmp, const int32_t* J, int r,
                          double* Us, int64_t* skel, cudaStream_t st) {
+  count_launches(1);
   k_usamp_parent<<<nnodes, 128, 0, st>>>(node0, Utmp, J, r, Us, skel);
 }
 

@@ -336,6 +336,7 @@ __global__ __launch_bounds__(256) void k_cholqr(const T* __restrict__ G, int kca
 template <typename T>
 void launch_tsqr(const TsqrTask* tasks, int ntasks, int rows_max, const T* P, int64_t ldp, int c,
                  T* R, cudaStream_t st) {
+  count_launches(1);
   const int ldm = rows_max;
   const size_t smem = (size_t)ldm * c * sizeof(T);
   cudaFuncSetAttribute(k_tsqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -345,6 +346,7 @@ void launch_tsqr(const TsqrTask* tasks, int ntasks, int rows_max, const T* P, in
 template <typename T>
 void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W, T* sigma,
                    cudaStream_t st) {
+  count_launches(1);
   const size_t smem = (size_t)2 * c * c * sizeof(T);
   cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int threads = ((c / 2 + 31) / 32) * 32 * 32;
@@ -357,6 +359,7 @@ template <typename T>
 void launch_truncate(int nnodes, const T* W, const T* sigma, int c, int kcap, int mode, int kfix,
                      double tol_scaled, double* eps_abs, int set_eps, double floor_rel,
                      int32_t* rank, T* T1, int32_t* saturated, cudaStream_t st) {
+  count_launches(1);
   k_truncate<T><<<nnodes, 128, 0, st>>>(nnodes, W, sigma, c, kcap, mode, kfix, tol_scaled,
                                         eps_abs, set_eps, floor_rel, rank, T1, saturated);
 }
@@ -364,6 +367,7 @@ void launch_truncate(int nnodes, const T* W, const T* sigma, int c, int kcap, in
 template <typename T>
 void launch_cholqr(int nnodes, const T* G, int kcap, const int32_t* rank, T* T2, const T* W,
                    const T* sigma, int c, T* M, int want_m, cudaStream_t st) {
+  count_launches(1);
   const size_t smem = (size_t)2 * kcap * kcap * sizeof(T);
   cudaFuncSetAttribute(k_cholqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_cholqr<T><<<nnodes, 256, smem, st>>>(G, kcap, rank, T2, W, sigma, c, M, want_m);

@@ -149,6 +149,7 @@ void launch_seg_tn(const Chunk* chunks, int nchunks, const int32_t* chunk_begin,
                    int node0, const T* A, int64_t lda, int aoff_even, int aoff_odd, int ka,
                    const T* B, int64_t ldb, int boff_even, int boff_odd, int kb, double* partial,
                    T* out, cudaStream_t st) {
+  count_launches(2);
   (void)node0;
   const size_t smem = 2 * TN_ROWS * (TN_MAX + 1) * sizeof(T);
   static bool configured = false;
@@ -169,6 +170,7 @@ void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int6
                    int poff_even, int poff_odd, int kin, const T* C, int64_t cstride, int cld,
                    int cflip, T* Y, int64_t ldy, int yoff_even, int yoff_odd, int kout, T alpha,
                    T beta, cudaStream_t st) {
+  count_launches(1);
   const size_t smem = (size_t)(NN_MAX * NN_ROWS + NN_MAX * NN_MAX) * sizeof(T);
   static bool configured = false;
   if (!configured) {
