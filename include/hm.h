@@ -16,8 +16,8 @@
  *    element (i, j) is at A[i * lda + j].
  *  - "device pointer" means memory of the current CUDA device; "host pointer"
  *    means ordinary (pageable or pinned) host memory.
- *  - Element type follows the precision of the call: HM_FP64 -> double,
- *    HM_MIXED -> float.
+ *  - Element type follows the precision of the call: HM_FP64 and HM_A32 ->
+ *    double, HM_MIXED -> float.
  *  - Work is enqueued on the caller's stream (a cudaStream_t passed as void*;
  *    NULL = legacy default stream).  Unless stated otherwise a call returns
  *    after enqueueing (asynchronous); the compress calls synchronize the stream
@@ -48,14 +48,17 @@ typedef enum {
   HM_EUNSUPPORTED = 8      /* valid request outside what this build supports */
 } hm_status;
 
-typedef enum { HM_FP64 = 0, HM_MIXED = 1 } hm_precision;
+/* HM_FP64: FP64 operator and pipeline.  HM_MIXED: FP32 samples, bases and
+ * peeling (small solves of the ID in FP64).  HM_A32: FP32 operator applied in
+ * FP64 (the black box receives and returns double blocks), FP64 pipeline. */
+typedef enum { HM_FP64 = 0, HM_MIXED = 1, HM_A32 = 2 } hm_precision;
 typedef enum { HM_FORMAT_HODLR = 0, HM_FORMAT_HBS = 1, HM_FORMAT_HBSID = 2 } hm_format;
 
 /*
  * Black box (Sec. 1, T_mult; Fig. "Randomized compression of a HODLR matrix":
  * the products A*Omega and A^*Omega).  Computes Y(0:n, 0:ncols) = op(A) X with
  * op = A (trans = 0) or A^T (trans = 1).  X and Y are device pointers,
- * column-major, element type double (HM_FP64) or float (HM_MIXED).  The
+ * column-major, element type double (HM_FP64, HM_A32) or float (HM_MIXED).  The
  * callback must enqueue its work on `stream` (a cudaStream_t) and return 0; any
  * other value aborts the compression with HM_ECALLBACK.  X is read-only and is
  * not retained after the call returns.
@@ -133,11 +136,11 @@ hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* 
 /* --------------------------------------------------------- black boxes --- */
 
 /*
- * Dense test operator: wraps a row-major N x N device matrix A (lda >= N;
- * dtype 0 = double, 1 = float) as a black box whose apply is the library's
- * sampling GEMM.  The matrix is NOT copied or owned: it must outlive the
- * operator.  A float matrix serves HM_MIXED compressions (samples in float);
- * a double matrix serves HM_FP64.  The returned operator's ctx is released by
+ * Dense test operator: wraps a row-major N x N device matrix A (lda >= N) as a
+ * black box whose apply is the library's sampling GEMM.  dtype 0: double
+ * matrix, double blocks (HM_FP64); 1: float matrix, float blocks (HM_MIXED);
+ * 2: float matrix, double blocks with FP64 products and sums (HM_A32).  The
+ * matrix is NOT copied or owned: it must outlive the operator.  The returned operator's ctx is released by
  * hm_dense_operator_destroy.
  */
 hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,

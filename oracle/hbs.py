@@ -44,7 +44,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .hodlr import ApplyFn, gaussian_test_matrix, identity_test_matrix
-from .lowrank import interp_decomp
+from .lowrank import RANGE_FLOOR, interp_decomp
 from .tree import Tree
 
 EPS_SCALE = 0.01
@@ -119,13 +119,25 @@ def dense(h: HBS) -> np.ndarray:
     return apply(h, np.eye(h.tree.N))
 
 
-def _svd_r(M: np.ndarray, r: int):
+def _svd_r(M: np.ndarray, r: int, floor: bool = False):
+    """svd(M, r): the leading r singular triplets.  With floor, directions whose
+    singular value is below RANGE_FLOOR * sigma_1 are returned as zero columns
+    (significant-range reading, as for ``lowrank.range_basis``)."""
     U, s, Vt = np.linalg.svd(M, full_matrices=False)
-    return U[:, :r], s[:r], Vt[:r].T
+    U, s, V = U[:, :r].copy(), s[:r].copy(), Vt[:r].T.copy()
+    if floor and s.size:
+        dead = ~(s > RANGE_FLOOR * s[0])
+        U[:, dead] = 0.0
+        V[:, dead] = 0.0
+        s[dead] = 0.0
+    return U, s, V
 
 
-def compress(apply_A: ApplyFn, tree: Tree, r: int, seed: int = 2, mixed: bool = False) -> HBS:
-    """Fig. "A basic scheme for compressing an HBS matrix" (fixed rank r)."""
+def compress(apply_A: ApplyFn, tree: Tree, r: int, seed: int = 2, mixed: bool = False,
+             floor: bool = False) -> HBS:
+    """Fig. "A basic scheme for compressing an HBS matrix" (fixed rank r).
+
+    floor: read svd(., r) on the numerical range (see ``_svd_r``)."""
     h = HBS(tree=tree, r=r)
     t = tree
     if min(int(t.size[x]) for x in t.leaves()) < r:
@@ -145,8 +157,8 @@ def compress(apply_A: ApplyFn, tree: Tree, r: int, seed: int = 2, mixed: bool = 
                 Ybold = h.Ulong[tau] * h.y[tau][None, :]
                 Yloc_a = np.hstack([Y[t.rows(a), :r], Ybold[Ja]])
                 Yloc_b = np.hstack([Y[t.rows(b), r:], Ybold[Jb]])
-            h.Ulong[a], h.y[a], _ = _svd_r(Yloc_a, r)
-            h.Ulong[b], h.y[b], _ = _svd_r(Yloc_b, r)
+            h.Ulong[a], h.y[a], _ = _svd_r(Yloc_a, r, floor)
+            h.Ulong[b], h.y[b], _ = _svd_r(Yloc_b, r, floor)
             Xt[t.rows(a), r:] = h.Ulong[a]
             Xt[t.rows(b), :r] = h.Ulong[b]
             if tau != 1:
@@ -164,8 +176,8 @@ def compress(apply_A: ApplyFn, tree: Tree, r: int, seed: int = 2, mixed: bool = 
                 Zbold = h.Vlong[tau] * h.z[tau][None, :]
                 Zloc_a = np.hstack([Z[t.rows(a), :r], Zbold[Ja]])
                 Zloc_b = np.hstack([Z[t.rows(b), r:], Zbold[Jb]])
-            h.Vlong[a], b21, X1 = _svd_r(Zloc_a, r)
-            h.Vlong[b], b12, X2 = _svd_r(Zloc_b, r)
+            h.Vlong[a], b21, X1 = _svd_r(Zloc_a, r, floor)
+            h.Vlong[b], b12, X2 = _svd_r(Zloc_b, r, floor)
             h.z[a], h.z[b] = b21, b12
             h.B[b] = X1[:r] * b21[None, :]   # B_ba = X1(1:r,:) diag(b21)
             h.B[a] = X2[:r] * b12[None, :]   # B_ab = X2(1:r,:) diag(b12)

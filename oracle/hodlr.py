@@ -35,7 +35,7 @@ from typing import Callable
 
 import numpy as np
 
-from .lowrank import qr_basis, svd_trunc
+from .lowrank import qr_basis, range_basis, svd_trunc
 from .philox import level_field
 from .tree import Tree
 
@@ -111,8 +111,17 @@ def identity_test_matrix(tree: Tree) -> np.ndarray:
 
 
 def compress(apply_A: ApplyFn, tree: Tree, r: int, k: int | None = None,
-             tol: float | None = None, seed: int = 2, mixed: bool = False) -> HODLR:
-    """Fig. "Randomized compression of a HODLR matrix", level by level."""
+             tol: float | None = None, seed: int = 2, mixed: bool = False,
+             basis: str = "qr") -> HODLR:
+    """Fig. "Randomized compression of a HODLR matrix", level by level.
+
+    basis: how U_alpha = qr(Y1(I_alpha,:)) is read: "qr" is the Q factor of a
+    full Householder QR (r columns); "range" keeps only the numerical range
+    (``range_basis``).  The two agree on the range of the samples and differ in
+    the directions that are rounding noise, which pick up the coarser levels'
+    truncation error through the transpose peel.
+    """
+    orth = qr_basis if basis == "qr" else range_basis
     if (k is None) == (tol is None):
         raise ValueError("exactly one of k (fixed rank) or tol (adaptive) is required")
     h = HODLR(tree=tree)
@@ -126,8 +135,8 @@ def compress(apply_A: ApplyFn, tree: Tree, r: int, k: int | None = None,
         Ucur = {}
         for tau in tree.level_nodes(level):
             a, b = 2 * tau, 2 * tau + 1
-            Ucur[a] = qr_basis(Y[tree.rows(a), :r])
-            Ucur[b] = qr_basis(Y[tree.rows(b), r:])
+            Ucur[a] = orth(Y[tree.rows(a), :r])
+            Ucur[b] = orth(Y[tree.rows(b), r:])
             # Omega_1(I_alpha,:) = U_alpha, Omega_2(I_beta,:) = U_beta (a node with
             # fewer than r rows has a square basis; the remaining columns stay zero)
             Xt[tree.rows(a), r:r + Ucur[a].shape[1]] = Ucur[a]

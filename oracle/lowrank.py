@@ -31,6 +31,24 @@ def qr_basis(A: np.ndarray) -> np.ndarray:
     return Q
 
 
+RANGE_FLOOR = 1e-12
+
+
+def range_basis(A: np.ndarray, rel_floor: float = RANGE_FLOOR) -> np.ndarray:
+    """Orthonormal basis of the numerically significant range of A: the left
+    singular vectors whose singular values exceed rel_floor * sigma_1.  A reading
+    of "qr(Y)" for samples that are numerically rank deficient: it spans the
+    significant part of the range of a full QR's Q and has no columns for
+    directions at the rounding level, whose choice is arbitrary (they would pick
+    up an arbitrary share of the coarser levels' truncation error through the
+    transpose peel).  The default floor 1e-12 lies well above FP64 rounding and
+    far below any compression tolerance."""
+    U, s, _ = np.linalg.svd(A, full_matrices=False)
+    if s.size == 0 or s[0] == 0.0:
+        return U[:, :0]
+    return U[:, : int(np.count_nonzero(s > rel_floor * s[0]))]
+
+
 def svd_trunc(A: np.ndarray, k: int | None = None, eps: float | None = None):
     """[U, s, Vt] truncated per mode 2 (k) or mode 3 (eps); mode 1 if neither."""
     U, s, Vt = np.linalg.svd(A, full_matrices=False)

@@ -8,7 +8,7 @@ Importing this package loads ``libhm.so`` and fails loudly if it is missing:
 there is no CPU fallback.
 """
 from ._lib import (  # noqa: F401
-    HM_FP64, HM_MIXED, HM_FORMAT_HODLR, HM_FORMAT_HBS, HM_FORMAT_HBSID, HmError, Opts, Tree,
+    HM_FP64, HM_MIXED, HM_A32, HM_FORMAT_HODLR, HM_FORMAT_HBS, HM_FORMAT_HBSID, HmError, Opts, Tree,
     Operator, Handle, lib, library_path, hm_tree_create, hm_dense_operator_create,
     hm_dense_apply, hm_compress_hodlr, hm_compress_hbs, hm_apply, hm_apply_host,
     hm_reconstruct_block, hm_rel_frob_error, hm_info, hm_node_rank, hm_hodlr_factored_apply,

@@ -9,7 +9,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libhm.so")
 
-HM_FP64, HM_MIXED = 0, 1
+HM_FP64, HM_MIXED, HM_A32 = 0, 1, 2
 HM_FORMAT_HODLR, HM_FORMAT_HBS, HM_FORMAT_HBSID = 0, 1, 2
 _STATUS = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "HM_ECALLBACK",
            5: "HM_ERANK_SATURATED", 6: "HM_ENONFINITE", 7: "HM_ETIMEOUT", 8: "HM_EUNSUPPORTED"}
@@ -155,11 +155,16 @@ class Operator:
             lib.hm_dense_operator_destroy(C.byref(self.op))
 
 
-def hm_dense_operator_create(A: torch.Tensor) -> Operator:
-    """Dense test operator over a row-major (n, lda) CUDA tensor (float64 or float32)."""
+def hm_dense_operator_create(A: torch.Tensor, fp64_blocks: bool = False) -> Operator:
+    """Dense test operator over a row-major (n, lda) CUDA tensor.  float64 -> HM_FP64;
+    float32 -> HM_MIXED, or HM_A32 (float matrix, double blocks) with fp64_blocks=True."""
     if A.dim() != 2 or A.stride(1) != 1 or not A.is_cuda:
         raise ValueError("A must be a row-major 2-D CUDA tensor")
     dtype = {torch.float64: 0, torch.float32: 1}[A.dtype]
+    if fp64_blocks:
+        if dtype != 1:
+            raise ValueError("fp64_blocks needs a float32 matrix")
+        dtype = 2
     op = _Operator()
     _check(lib.hm_dense_operator_create(_ptr(A), A.shape[0], A.stride(0), dtype, C.byref(op)),
            "hm_dense_operator_create")

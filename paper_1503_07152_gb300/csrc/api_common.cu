@@ -333,6 +333,9 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
       launch_dense_gemm<double>((const double*)d->A, d->lda, trans, n, w,
                                 (const double*)X + c0 * ldx, ldx, (double*)Y + c0 * ldy, ldy,
                                 d->flags, st);
+    else if (d->dtype == 2)
+      launch_dense_gemm_a32((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
+                            ldx, (double*)Y + c0 * ldy, ldy, d->flags, st);
     else
       launch_dense_gemm<float>((const float*)d->A, d->lda, trans, n, w,
                                (const float*)X + c0 * ldx, ldx, (float*)Y + c0 * ldy, ldy,
@@ -344,8 +347,8 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
 hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,
                                    hm_operator* out) {
   clear_error();
-  if (!A || !out || n < 1 || lda < n || (dtype != 0 && dtype != 1)) {
-    set_error("hm_dense_operator_create: need A, out, n >= 1, lda >= n, dtype 0|1");
+  if (!A || !out || n < 1 || lda < n || dtype < 0 || dtype > 2) {
+    set_error("hm_dense_operator_create: need A, out, n >= 1, lda >= n, dtype 0|1|2");
     return HM_EINVAL;
   }
   hm_dense_ctx* d = new hm_dense_ctx();

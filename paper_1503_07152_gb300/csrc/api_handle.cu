@@ -3,7 +3,9 @@
 // dense operator (Sec. 5), info, ranks, destruction; and the factored HODLR
 // apply with its hand-written adjoint.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "hm_hodlr.h"
 
@@ -23,7 +25,7 @@ static hm_status apply_any(const hm_handle* h, int trans, int64_t ncols, const T
   return hbs_apply_t<T>(h, trans, ncols, X, ldx, Y, ldy, st);
 }
 
-static size_t elem(const hm_handle* h) { return h->prec == HM_FP64 ? 8 : 4; }
+static size_t elem(const hm_handle* h) { return h->prec == HM_MIXED ? 4 : 8; }
 
 extern "C" {
 
@@ -36,7 +38,7 @@ hm_status hm_apply(const hm_handle* h, int trans, int64_t ncols, const void* X, 
   }
   if (ncols == 0) return HM_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  if (h->prec == HM_FP64)
+  if (h->prec != HM_MIXED)
     return apply_any<double>(h, trans, ncols, (const double*)X, ldx, (double*)Y, ldy, st);
   return apply_any<float>(h, trans, ncols, (const float*)X, ldx, (float*)Y, ldy, st);
 }
@@ -101,8 +103,8 @@ static hm_status reconstruct_t(const hm_handle* h, int64_t r0, int64_t r1, int64
   return check_launch("hm_reconstruct_block");
 }
 
-template <typename T>
-static hm_status frob_t(const hm_handle* h, const T* A, int64_t lda, double* err, cudaStream_t st) {
+template <typename T, typename TA = T>
+static hm_status frob_t(const hm_handle* h, const TA* A, int64_t lda, double* err, cudaStream_t st) {
   const int64_t N = h->n;
   const int64_t cw = 256;
   T* X = nullptr;
@@ -117,7 +119,10 @@ static hm_status frob_t(const hm_handle* h, const T* A, int64_t lda, double* err
     const int64_t w = std::min(cw, N - c);
     launch_identity_cols<T>(X, N, N, c, w, st);
     s = apply_any<T>(h, 0, w, X, N, Y, N, st);
-    if (s == HM_OK) launch_frob_tile<T>(A, lda, Y, N, N, c, w, acc, st);
+    if (s == HM_OK) {
+      if constexpr (std::is_same<T, TA>::value) launch_frob_tile<T>(A, lda, Y, N, N, c, w, acc, st);
+      else launch_frob_tile_a32((const float*)A, lda, (const double*)Y, N, N, c, w, acc, st);
+    }
   }
   double hacc[2] = {0, 0};
   if (s == HM_OK) {
@@ -147,7 +152,7 @@ hm_status hm_reconstruct_block(const hm_handle* h, int64_t r0, int64_t r1, int64
   }
   if (r1 == r0 || c1 == c0) return HM_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  if (h->prec == HM_FP64) return reconstruct_t<double>(h, r0, r1, c0, c1, (double*)out, ld, st);
+  if (h->prec != HM_MIXED) return reconstruct_t<double>(h, r0, r1, c0, c1, (double*)out, ld, st);
   return reconstruct_t<float>(h, r0, r1, c0, c1, (float*)out, ld, st);
 }
 
@@ -155,11 +160,12 @@ hm_status hm_rel_frob_error(const hm_handle* h, const void* A, int64_t lda, int3
                             double* err, void* stream) {
   clear_error();
   if (!h || !A || !err || lda < h->n || dtype != (h->prec == HM_FP64 ? 0 : 1)) {
-    set_error("hm_rel_frob_error: need handle, A (dtype matching the handle), lda >= n, err");
+    set_error("hm_rel_frob_error: need handle, A (double for HM_FP64, float otherwise), lda >= n");
     return HM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (h->prec == HM_FP64) return frob_t<double>(h, (const double*)A, lda, err, st);
+  if (h->prec == HM_A32) return frob_t<double, float>(h, (const float*)A, lda, err, st);
   return frob_t<float>(h, (const float*)A, lda, err, st);
 }
 
@@ -241,15 +247,15 @@ extern "C" hm_status hm_gaussian_test_matrix(const hm_tree* tree, int32_t level,
                                             void* stream) {
   clear_error();
   if (!tree || !X || level < 0 || level >= tree->L || r < 1 || ldx < tree->n ||
-      (prec != HM_FP64 && prec != HM_MIXED)) {
+      (prec != HM_FP64 && prec != HM_MIXED && prec != HM_A32)) {
     set_error("hm_gaussian_test_matrix: need tree, X, 0 <= level < L, r >= 1, ldx >= n, prec");
     return HM_EINVAL;
   }
   HM_TRY(tree_device(const_cast<hm_tree*>(tree)));
   cudaStream_t st = (cudaStream_t)stream;
-  if (prec == HM_FP64)
-    launch_gauss_fill<double>((double*)X, ldx, tree->n, r, level, seed, false, tree->d_start,
-                              tree->L, st);
+  if (prec != HM_MIXED)
+    launch_gauss_fill<double>((double*)X, ldx, tree->n, r, level, seed, prec == HM_A32,
+                              tree->d_start, tree->L, st);
   else
     launch_gauss_fill<float>((float*)X, ldx, tree->n, r, level, seed, true, tree->d_start, tree->L,
                              st);
@@ -263,7 +269,7 @@ extern "C" hm_status hm_hodlr_export_level(const hm_handle* h, int32_t level, vo
     set_error("hm_hodlr_export_level: need a HODLR handle, 1 <= level <= L, U and V");
     return HM_EINVAL;
   }
-  const size_t es = h->prec == HM_FP64 ? 8 : 4;
+  const size_t es = h->prec == HM_MIXED ? 4 : 8;
   const size_t bytes = es * (size_t)h->n * h->r;
   const size_t off = bytes * (size_t)(level - 1);
   cudaStream_t st = (cudaStream_t)stream;

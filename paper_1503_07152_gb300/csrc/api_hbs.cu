@@ -128,7 +128,7 @@ hm_status compress_hbs_t(Ctx<T>& c, HbsState<T>& s, T* D) {
   const int r = c.r;
   const int L = c.tree->L;
   const int nmax = (int)c.tree->nmax;
-  const bool bf16 = (sizeof(T) == 4);
+  const bool bf16 = c.bf16;
   T* Unext = s.Ucur + N * r;  // two level buffers, swapped by pointer
   T* Vnext = s.Vcur + N * r;
   const int64_t rr = (int64_t)r * r;
@@ -468,6 +468,7 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
   c.mode_tol = o->mode_tol;
   c.kfix = o->k;
   c.tol = o->tol;
+  c.bf16 = (o->prec != HM_FP64);
   HbsState<T> hs;
   hs.N = N;
   hs.r = r;
@@ -574,7 +575,7 @@ extern "C" hm_status hm_compress_hbs(const hm_operator* op, const hm_tree* tree,
                                      void* stream, hm_handle** out) {
   clear_error();
   if (!op || !op->apply || !tree || !opts || !out || op->n != tree->n || tree->L < 1 ||
-      (opts->prec != HM_FP64 && opts->prec != HM_MIXED)) {
+      (opts->prec != HM_FP64 && opts->prec != HM_MIXED && opts->prec != HM_A32)) {
     set_error("hm_compress_hbs: need operator, tree (L >= 1, same n), opts, out");
     return HM_EINVAL;
   }
@@ -589,7 +590,7 @@ extern "C" hm_status hm_compress_hbs(const hm_operator* op, const hm_tree* tree,
   }
   *out = nullptr;
   hm_tree* t = const_cast<hm_tree*>(tree);
-  if (opts->prec == HM_FP64)
+  if (opts->prec != HM_MIXED)
     return compress_hbs_entry<double>(op, t, opts, (cudaStream_t)stream, out);
   return compress_hbs_entry<float>(op, t, opts, (cudaStream_t)stream, out);
 }

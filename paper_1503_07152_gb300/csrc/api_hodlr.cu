@@ -84,9 +84,15 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
     launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rows_max, P, N, pc, c.Rw,
                    c.st);
   launch_jacobi<T>(lp.d_final_slot, lp.nnodes, c.Rw, pc, c.W, c.sig, c.st);
-  // directions below one unit roundoff of the panel's largest singular value are
-  // rounding noise of the working precision
-  const double floor_rel = (sizeof(T) == 4 ? 5.960464477539063e-08 : 1.1102230246251565e-16);
+  // Directions of the sample range below floor_rel * sigma_1 are dropped.  In
+  // FP64 the floor sits well above rounding noise (1e-12): directions near the
+  // noise level are arbitrary functions of the rounding and would capture an
+  // arbitrary share of the coarser levels' truncation error through the
+  // transpose peel; what they represent lies far below any tolerance.  In FP32
+  // the floor is the unit roundoff.  The tolerance threshold (mode 1) is applied
+  // on top.
+  const double floor_rel = (sizeof(T) == 4 ? 5.960464477539063e-08
+                                           : (mode == 1 ? 1.1102230246251565e-16 : 1e-12));
   launch_truncate<T>(lp.nnodes, c.W, c.sig, pc, r, mode, kfix, kEpsScale * c.tol, c.eps_dev,
                      set_eps ? 1 : 0, floor_rel, rank_lv, c.T1, c.flags_dev + 1, c.st);
   launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, P, N, 0, 0, pc, c.T1, (int64_t)pc * r, pc, 0, Q,
@@ -164,7 +170,7 @@ hm_status compress_hodlr_t(Ctx<T>& c, hm_handle* h) {
   const int nmax = (int)c.tree->nmax;
   T* U = (T*)h->U;
   T* V = (T*)h->V;
-  const bool bf16 = (sizeof(T) == 4);
+  const bool bf16 = c.bf16;
   for (int level = 0; level < L; ++level) {
     const int lv = level + 1;
     T* Ulv = U + (int64_t)(lv - 1) * N * r;
@@ -272,7 +278,7 @@ static hm_status check_opts(const hm_operator* op, const hm_tree* tree, const hm
     set_error("compress: operator size differs from the tree size");
     return HM_EINVAL;
   }
-  if (o->prec != HM_FP64 && o->prec != HM_MIXED) {
+  if (o->prec != HM_FP64 && o->prec != HM_MIXED && o->prec != HM_A32) {
     set_error("compress: prec must be HM_FP64 or HM_MIXED");
     return HM_EINVAL;
   }
@@ -326,6 +332,7 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
   c.mode_tol = o->mode_tol;
   c.kfix = o->k;
   c.tol = o->tol;
+  c.bf16 = (o->prec != HM_FP64);
   int32_t* rank_block = nullptr;
   if (s == HM_OK) s = device_alloc((void**)&rank_block, sizeof(int32_t) * 2 * ((size_t)1 << (tree->L + 1)));
   c.rank_dev = rank_block;
@@ -409,7 +416,7 @@ extern "C" hm_status hm_compress_hodlr(const hm_operator* op, const hm_tree* tre
   HM_TRY(check_opts(op, tree, opts, out));
   *out = nullptr;
   hm_tree* t = const_cast<hm_tree*>(tree);
-  if (opts->prec == HM_FP64)
+  if (opts->prec != HM_MIXED)
     return compress_hodlr_entry<double>(op, t, opts, (cudaStream_t)stream, out);
   return compress_hodlr_entry<float>(op, t, opts, (cudaStream_t)stream, out);
 }

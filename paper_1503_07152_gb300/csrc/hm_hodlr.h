@@ -17,6 +17,7 @@ struct Ctx {
   int r = 0;
   uint64_t seed = 0;
   int mode_tol = 0, kfix = 0;
+  bool bf16 = false;  // test matrices rounded to BF16 values (HM_MIXED, HM_A32)
   double tol = 0.0;
   void* block = nullptr;
   T *X = nullptr, *S = nullptr, *P = nullptr, *Rw = nullptr, *W = nullptr, *sig = nullptr;

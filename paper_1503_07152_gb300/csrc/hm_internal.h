@@ -72,6 +72,10 @@ void launch_dense_gemm(const T* A, int64_t lda, int trans, int64_t n, int64_t nc
                        const T* X, int64_t ldx, T* Y, int64_t ldy, uint8_t* flags,
                        cudaStream_t st);
 
+void launch_dense_gemm_a32(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
+                           const double* X, int64_t ldx, double* Y, int64_t ldy, uint8_t* flags,
+                           cudaStream_t st);
+
 // Gram-like reduction: for every chunk, partial = A(rows, 0:ka)^T B(rows, 0:kb)
 // (column offsets chosen by node parity), then per node sum of its chunks:
 // out[node - node0] (ka x kb, column-major, ld ka) = sum.
@@ -153,6 +157,9 @@ void launch_identity_cols(T* Y, int64_t ldy, int64_t n, int64_t c0, int64_t w, c
 template <typename T>
 void launch_frob_tile(const T* A, int64_t lda, const T* Ac, int64_t ldc, int64_t n,
                       int64_t c0, int64_t w, double* acc, cudaStream_t st);
+
+void launch_frob_tile_a32(const float* A, int64_t lda, const double* Ac, int64_t ldc, int64_t n,
+                          int64_t c0, int64_t w, double* acc, cudaStream_t st);
 
 int32_t nonfinite_check_launch(const void* p, int64_t count, int is_double, int32_t* flag,
                                cudaStream_t st);

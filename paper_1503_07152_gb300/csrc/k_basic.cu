@@ -191,8 +191,8 @@ __global__ void k_identity_cols(T* __restrict__ Y, int64_t ldy, int64_t n, int64
 }
 
 // A row-major, Ac column-major (n x w); accumulates sum (A - Ac)^2 and sum A^2.
-template <typename T>
-__global__ void k_frob_tile(const T* __restrict__ A, int64_t lda, const T* __restrict__ Ac,
+template <typename T, typename TC>
+__global__ void k_frob_tile(const T* __restrict__ A, int64_t lda, const TC* __restrict__ Ac,
                             int64_t ldc, int64_t n, int64_t c0, int64_t w,
                             double* __restrict__ acc) {
   __shared__ double red[2][32];
@@ -337,7 +337,14 @@ void launch_frob_tile(const T* A, int64_t lda, const T* Ac, int64_t ldc, int64_t
                       int64_t w, double* acc, cudaStream_t st) {
   count_launches(1);
   unsigned g = blocks_for(n * w, 256);
-  k_frob_tile<T><<<g > 2048 ? 2048 : g, 256, 0, st>>>(A, lda, Ac, ldc, n, c0, w, acc);
+  k_frob_tile<T, T><<<g > 2048 ? 2048 : g, 256, 0, st>>>(A, lda, Ac, ldc, n, c0, w, acc);
+}
+
+void launch_frob_tile_a32(const float* A, int64_t lda, const double* Ac, int64_t ldc, int64_t n,
+                          int64_t c0, int64_t w, double* acc, cudaStream_t st) {
+  count_launches(1);
+  unsigned g = blocks_for(n * w, 256);
+  k_frob_tile<float, double><<<g > 2048 ? 2048 : g, 256, 0, st>>>(A, lda, Ac, ldc, n, c0, w, acc);
 }
 
 int32_t nonfinite_check_launch(const void* p, int64_t count, int is_double, int32_t* flag,

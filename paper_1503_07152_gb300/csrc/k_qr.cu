@@ -128,7 +128,7 @@ __global__ __launch_bounds__(512) void k_jacobi(const int32_t* __restrict__ node
   const int cp = (c + 1) & ~1;  // even number of slots; slot c (odd c) is a bye
   // a pair is rotated while its correlation exceeds the rounding level of the
   // length-c dot products that measure it
-  const T tol = (T)(4.0 * Eps<T>::v * sqrt((double)c));
+  const T tol = (T)(Eps<T>::v * sqrt((double)c));
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (tid == 0) rotated = 0;
     __syncthreads();

@@ -32,11 +32,14 @@ __global__ __launch_bounds__(256) void k_seg_tn_partial(
   const int boff = (ch.node & 1) ? boff_o : boff_e;
   const int tid = threadIdx.x;
   const int ti = tid >> 4, tj = tid & 15;
-  T acc[8][8];
+  // products summed in T over at most 16 rows, then added into FP64 sums: the
+  // projections of the peel are differences of large sums, so a long FP32 sum
+  // would cost far more than its unit roundoff
+  double acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0;
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
   for (int64_t r0 = ch.r0; r0 < ch.r1; r0 += TN_ROWS) {
     const int rows = (int)((ch.r1 - r0) < TN_ROWS ? (ch.r1 - r0) : TN_ROWS);
     for (int idx = tid; idx < TN_ROWS * TN_MAX; idx += 256) {
@@ -47,16 +50,28 @@ __global__ __launch_bounds__(256) void k_seg_tn_partial(
           (rr < rows && c < kb) ? B[r0 + rr + (int64_t)(boff + c) * ldb] : (T)0;
     }
     __syncthreads();
-    for (int rr = 0; rr < rows; ++rr) {
-      T a[8], b[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = As[rr * (TN_MAX + 1) + ti * 8 + i];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) b[j] = Bs[rr * (TN_MAX + 1) + tj * 8 + j];
+    for (int q0 = 0; q0 < rows; q0 += 16) {
+      const int q1 = (q0 + 16 < rows) ? q0 + 16 : rows;
+      T tmp[8][8];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) tmp[i][j] = 0;
+      for (int rr = q0; rr < q1; ++rr) {
+        T a[8], b[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = As[rr * (TN_MAX + 1) + ti * 8 + i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] = Bs[rr * (TN_MAX + 1) + tj * 8 + j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tmp[i][j] = fma(a[i], b[j], tmp[i][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] += (double)tmp[i][j];
     }
     __syncthreads();
   }
@@ -66,7 +81,7 @@ __global__ __launch_bounds__(256) void k_seg_tn_partial(
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int ii = ti * 8 + i, jj = tj * 8 + j;
-      if (ii < ka && jj < kb) out[ii + jj * ka] = (double)acc[i][j];
+      if (ii < ka && jj < kb) out[ii + jj * ka] = acc[i][j];
     }
 }
 
@@ -114,19 +129,31 @@ __global__ __launch_bounds__(256) void k_seg_nn(
   }
   __syncthreads();
   const int lane = tid & 31, w = tid >> 5;
-  T acc[2][16];
+  double acc[2][16];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[i][j] = 0;
-  for (int k = 0; k < kin; ++k) {
-    const T a0 = Ps[k * NN_ROWS + lane], a1 = Ps[k * NN_ROWS + lane + 32];
+    for (int j = 0; j < 16; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < kin; k0 += 16) {
+    const int k1 = (k0 + 16 < kin) ? k0 + 16 : kin;
+    T tmp[2][16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const T c = Cs[k * NN_MAX + w * 16 + j];
-      acc[0][j] = fma(a0, c, acc[0][j]);
-      acc[1][j] = fma(a1, c, acc[1][j]);
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) tmp[i][j] = 0;
+    for (int k = k0; k < k1; ++k) {
+      const T a0 = Ps[k * NN_ROWS + lane], a1 = Ps[k * NN_ROWS + lane + 32];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const T c = Cs[k * NN_MAX + w * 16 + j];
+        tmp[0][j] = fma(a0, c, tmp[0][j]);
+        tmp[1][j] = fma(a1, c, tmp[1][j]);
+      }
     }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[i][j] += (double)tmp[i][j];
   }
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
@@ -137,7 +164,8 @@ __global__ __launch_bounds__(256) void k_seg_nn(
       const int rr = lane + 32 * i;
       if (rr >= rows) continue;
       T* yp = Y + ch.r0 + rr + (int64_t)(yoff + col) * ldy;
-      *yp = (beta == (T)0) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*yp);
+      const double v = (double)alpha * acc[i][j];
+      *yp = (beta == (T)0) ? (T)v : (T)(v + (double)beta * (double)(*yp));
     }
   }
 }

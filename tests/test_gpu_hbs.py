@@ -41,9 +41,9 @@ def synthetic_hbs(N, m, k, seed):
 def run_gpu(A, N, m, prec, **kw):
     dtype = torch.float64 if prec == 0 else torch.float32
     At = torch.from_numpy(np.ascontiguousarray(A)).to(DEV, dtype)
-    op = hm.hm_dense_operator_create(At)
+    op = hm.hm_dense_operator_create(At, fp64_blocks=(prec == 2))
     h = hm.hm_compress_hbs(op, hm.Tree(N, m), prec=prec, hbs_id=1, **kw)
-    out = torch.empty((N, N), device=DEV, dtype=dtype)
+    out = torch.empty((N, N), device=DEV, dtype=torch.float64 if prec != 1 else dtype)
     hm.hm_reconstruct_block(h, 0, N, 0, N, out)
     torch.cuda.synchronize()
     return h, out.double().cpu().numpy().T, At
@@ -74,13 +74,14 @@ def test_hbsid_fixed_rank_parity_fp64():
     assert np.linalg.norm(Ag - A) / nA < 1e-12
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_hbsid_log_kernel(prec):
     N, m, r = 2048, 128, 40
     A = W.log_kernel(N)
     A64 = A.astype(np.float64)
-    h, Ag, At = run_gpu(A if prec == 1 else A64, N, m, prec, tol=1e-7, r=r, seed=2)
-    o = ohbs.compress(ohodlr.dense_apply_fn(A64), build_tree(N, m), r=r, seed=2, mixed=(prec == 1))
+    h, Ag, At = run_gpu(A64 if prec == 0 else A, N, m, prec, tol=1e-7, r=r, seed=2)
+    o = ohbs.compress(ohodlr.dense_apply_fn(A64), build_tree(N, m), r=r, seed=2, mixed=(prec != 0),
+                      floor=True)
     Ao = ohbs.hbsid_dense(ohbs.to_hbsid(o, tol=1e-7))
     nA = np.linalg.norm(A64)
     e_gpu = np.linalg.norm(Ag - A64) / nA
@@ -88,10 +89,11 @@ def test_hbsid_log_kernel(prec):
     e_or = np.linalg.norm(Ao - A64) / nA
     print(f"HBS-ID prec={prec}: GPU err {e_gpu:.3e}, vs oracle {e_par:.3e}, oracle err {e_or:.3e}, "
           f"ranks {h.info['min_rank']}..{h.info['max_rank']}")
-    if prec == 0:
-        assert e_gpu < 1e-7 and e_par < 1e-7
-    else:
+    if prec == 1:
         assert e_par < 1e-6 and e_gpu < 1e-6
+    else:
+        assert e_gpu < 1e-7
+        assert e_par < 1e-12
 
 
 def test_hbsid_apply_transpose():

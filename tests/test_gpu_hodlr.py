@@ -23,6 +23,8 @@ def colmajor(M: np.ndarray, dtype) -> torch.Tensor:
 
 
 def dense_from_handle(h, n, dtype):
+    if h.info["prec"] == 2:
+        dtype = torch.float64
     out = torch.empty((n, n), device=DEV, dtype=dtype)
     hm.hm_reconstruct_block(h, 0, n, 0, n, out)
     torch.cuda.synchronize()
@@ -71,7 +73,7 @@ def test_dense_apply(dtype, N, ncols):
 def _compress_dense(A, N, m, prec, **kw):
     dtype = torch.float64 if prec == 0 else torch.float32
     At = torch.from_numpy(np.ascontiguousarray(A)).to(DEV, dtype)
-    op = hm.hm_dense_operator_create(At)
+    op = hm.hm_dense_operator_create(At, fp64_blocks=(prec == 2))
     t = hm.Tree(N, m)
     h = hm.hm_compress_hodlr(op, t, prec=prec, **kw)
     return h, At, dtype
@@ -218,3 +220,46 @@ def test_autograd_function_matches_adjoint():
     dx, dU, dV, dD = ograd.gradients(f, x.detach().cpu().double().numpy(), b.cpu().double().numpy())
     assert np.linalg.norm(x.grad.cpu().numpy() - dx) <= 1e-5 * np.linalg.norm(dx)
     assert np.linalg.norm(U.grad[0].cpu().numpy().T - dU[1]) <= 1e-5 * np.linalg.norm(dU[1])
+
+
+@pytest.mark.parametrize("N,m", [(2048, 128), (3000, 100)])
+def test_hodlr_a32_log_kernel_parity(N, m):
+    """FP32 operator applied in FP64 with an FP64 pipeline: the oracle's own arithmetic."""
+    A = W.log_kernel(N)
+    h, At, dtype = _compress_dense(A, N, m, 2, tol=1e-7, r=60, seed=2)
+    Ag = dense_from_handle(h, N, torch.float64)
+    # the GPU reads U = qr(Y) as an orthonormal basis of the numerical range of the
+    # samples; the oracle run with the same reading is the parity reference
+    o = ohodlr.compress(ohodlr.dense_apply_fn(A), build_tree(N, m), r=60, tol=1e-7, seed=2,
+                        mixed=True, basis="range")
+    Ao = ohodlr.dense(o)
+    oq = ohodlr.compress(ohodlr.dense_apply_fn(A), build_tree(N, m), r=60, tol=1e-7, seed=2,
+                         mixed=True)
+    Aq = ohodlr.dense(oq)
+    A64 = A.astype(np.float64)
+    nA = np.linalg.norm(A64)
+    e_gpu = np.linalg.norm(Ag - A64) / nA
+    e_par = np.linalg.norm(Ag - Ao) / nA
+    e_q = np.linalg.norm(Ag - Aq) / nA
+    print(f"A32 N={N}: GPU err vs A {e_gpu:.3e}, vs oracle (range) {e_par:.3e}, vs oracle (qr) {e_q:.3e}")
+    assert e_par < 1e-12
+    assert e_q < 2 * max(e_gpu, np.linalg.norm(Aq - A64) / nA)  # within the truncation error
+    assert e_gpu < 1e-7
+    assert abs(hm.hm_rel_frob_error(h, At) - e_gpu) < 1e-9
+
+
+def test_dense_apply_a32():
+    N, c = 1000, 45
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((N, N)).astype(np.float32)
+    X = rng.standard_normal((N, c))
+    At = torch.from_numpy(A).to(DEV)
+    op = hm.hm_dense_operator_create(At, fp64_blocks=True)
+    Xd = colmajor(X, torch.float64)
+    for trans in (0, 1):
+        Y = torch.empty((c, N), device=DEV, dtype=torch.float64)
+        hm.hm_dense_apply(op, trans, Xd, Y)
+        torch.cuda.synchronize()
+        A64 = A.astype(np.float64)
+        want = (A64.T if trans else A64) @ X
+        assert np.max(np.abs(Y.cpu().numpy().T - want)) <= 1e-13 * np.max(np.abs(want))

@@ -110,3 +110,19 @@ def test_mixed_test_matrix_is_bf16_exact():
     assert np.array_equal(X.astype(np.float32).astype(np.float64), X)
     # exactly r nonzeros per row (on the child's half)
     assert np.all(np.count_nonzero(X, axis=1) == 5)
+
+
+def test_range_basis_reading_same_accuracy():
+    """The numerical-range reading of qr(Y) reaches the same accuracy as the
+    Householder reading and recovers exact-rank matrices to rounding."""
+    f = W.synthetic_hodlr_factors(512, 32, 6, seed=11, shift=512.0)
+    A = W.dense_from_factors(f)
+    t = build_tree(512, 32)
+    h = hodlr.compress(hodlr.dense_apply_fn(A), t, r=16, k=6, seed=3, basis="range")
+    assert np.linalg.norm(A - hodlr.dense(h)) / np.linalg.norm(A) < 1e-13
+    L = W.log_kernel(1024).astype(np.float64)
+    t = build_tree(1024, 64)
+    e = [np.linalg.norm(L - hodlr.dense(hodlr.compress(hodlr.dense_apply_fn(L), t, r=40, tol=1e-7,
+                                                         seed=2, basis=b))) / np.linalg.norm(L)
+         for b in ("qr", "range")]
+    assert max(e) < 1e-7 and abs(e[0] - e[1]) < 0.5 * max(e)

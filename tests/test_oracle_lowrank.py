@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle.lowrank import interp_decomp, pivoted_qr, qr_basis, svd_trunc
+from oracle.lowrank import interp_decomp, pivoted_qr, qr_basis, range_basis, svd_trunc
 
 
 def _lowrank(m, n, k, seed, decay=1e-3):
@@ -64,3 +64,19 @@ def test_interp_decomp_brute_force_tiny():
     J, T = interp_decomp(A, eps=1e-12)
     assert J.size == 2
     assert np.allclose(A[:, J] @ T, A, atol=1e-13)
+
+
+def test_range_basis_spans_numerical_range():
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((80, 6)) @ rng.standard_normal((6, 20))  # rank 6 up to rounding
+    Q = range_basis(A, rel_floor=1e-12)
+    assert Q.shape[1] == 6
+    assert np.allclose(Q.T @ Q, np.eye(6), atol=1e-14)
+    assert np.linalg.norm(A - Q @ (Q.T @ A)) < 1e-12 * np.linalg.norm(A)
+    Qf = qr_basis(A)
+    assert np.linalg.norm(Qf @ (Qf.T @ Q) - Q) < 1e-12   # inside the span of the full Q
+    Q0 = range_basis(A, rel_floor=1e-17)  # below rounding: noise directions are kept too
+    assert 6 <= Q0.shape[1] <= 20 and np.allclose(Q0.T @ Q0, np.eye(Q0.shape[1]), atol=1e-13)
+    assert range_basis(A).shape[1] == 6
+    Z = np.zeros((10, 4))
+    assert range_basis(Z).shape[1] == 0
