@@ -138,9 +138,12 @@ hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* 
 /*
  * Dense test operator: wraps a row-major N x N device matrix A (lda >= N) as a
  * black box whose apply is the library's sampling GEMM.  dtype 0: double
- * matrix, double blocks (HM_FP64); 1: float matrix, float blocks (HM_MIXED);
- * 2: float matrix, double blocks with FP64 products and sums (HM_A32).  The
- * matrix is NOT copied or owned: it must outlive the operator.  The returned operator's ctx is released by
+ * matrix, double blocks (HM_FP64); 1: float matrix, float blocks (HM_MIXED) on
+ * the tensor cores (three-way BF16 split, FP32 accumulation drained into
+ * compensated FP32 sums); 2: float matrix, double blocks with FP64 products and
+ * sums (HM_A32); 3: as 1 on the CUDA cores (FP32 FMA, compensated sums).  The
+ * matrix is NOT copied or owned: it must outlive the operator.  dtype 1 grows a
+ * device workspace (a BF16 split of X) on first use of a larger block.  The returned operator's ctx is released by
  * hm_dense_operator_destroy.
  */
 hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,

@@ -155,9 +155,11 @@ class Operator:
             lib.hm_dense_operator_destroy(C.byref(self.op))
 
 
-def hm_dense_operator_create(A: torch.Tensor, fp64_blocks: bool = False) -> Operator:
+def hm_dense_operator_create(A: torch.Tensor, fp64_blocks: bool = False,
+                             cuda_cores: bool = False) -> Operator:
     """Dense test operator over a row-major (n, lda) CUDA tensor.  float64 -> HM_FP64;
-    float32 -> HM_MIXED, or HM_A32 (float matrix, double blocks) with fp64_blocks=True."""
+    float32 -> HM_MIXED on the tensor-core engine (cuda_cores=True: the CUDA-core
+    engine), or HM_A32 (float matrix, double blocks) with fp64_blocks=True."""
     if A.dim() != 2 or A.stride(1) != 1 or not A.is_cuda:
         raise ValueError("A must be a row-major 2-D CUDA tensor")
     dtype = {torch.float64: 0, torch.float32: 1}[A.dtype]
@@ -165,6 +167,8 @@ def hm_dense_operator_create(A: torch.Tensor, fp64_blocks: bool = False) -> Oper
         if dtype != 1:
             raise ValueError("fp64_blocks needs a float32 matrix")
         dtype = 2
+    elif cuda_cores and dtype == 1:
+        dtype = 3
     op = _Operator()
     _check(lib.hm_dense_operator_create(_ptr(A), A.shape[0], A.stride(0), dtype, C.byref(op)),
            "hm_dense_operator_create")

@@ -336,7 +336,19 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
     else if (d->dtype == 2)
       launch_dense_gemm_a32((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
                             ldx, (double*)Y + c0 * ldy, ldy, d->flags, st);
-    else
+    else if (d->dtype == 1 && gemm_tc_supported((const float*)d->A, d->lda, n)) {
+      const int64_t need = 2 * gemm_tc_xs_elems(n, w);
+      if (need > d->xs_bytes) {
+        if (d->xs) cudaFree(d->xs);
+        d->xs = nullptr;
+        d->xs_bytes = 0;
+        if (cudaMalloc(&d->xs, (size_t)need) != cudaSuccess) return 3;
+        d->xs_bytes = need;
+      }
+      if (launch_gemm_tc((const float*)d->A, d->lda, trans, n, w, (const float*)X + c0 * ldx,
+                         ldx, (float*)Y + c0 * ldy, ldy, d->xs, d->flags, d->err, st) != 0)
+        return 2;
+    } else  // dtype 3, or a layout TMA cannot address: FP32 on the CUDA-core engine
       launch_dense_gemm<float>((const float*)d->A, d->lda, trans, n, w,
                                (const float*)X + c0 * ldx, ldx, (float*)Y + c0 * ldy, ldy,
                                d->flags, st);
@@ -347,8 +359,8 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
 hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,
                                    hm_operator* out) {
   clear_error();
-  if (!A || !out || n < 1 || lda < n || dtype < 0 || dtype > 2) {
-    set_error("hm_dense_operator_create: need A, out, n >= 1, lda >= n, dtype 0|1|2");
+  if (!A || !out || n < 1 || lda < n || dtype < 0 || dtype > 3) {
+    set_error("hm_dense_operator_create: need A, out, n >= 1, lda >= n, dtype 0..3");
     return HM_EINVAL;
   }
   hm_dense_ctx* d = new hm_dense_ctx();
@@ -358,7 +370,10 @@ hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_
   d->dtype = dtype;
   d->flags_bytes = dense_flags_bytes(n, 1024, dtype == 0);
   hm_status s = device_alloc((void**)&d->flags, (size_t)d->flags_bytes);
+  if (s == HM_OK) s = device_alloc((void**)&d->err, sizeof(int));
+  if (s == HM_OK && cudaMemset(d->err, 0, sizeof(int)) != cudaSuccess) s = HM_ECUDA;
   if (s != HM_OK) {
+    if (d->flags) cudaFree(d->flags);
     delete d;
     return s;
   }
@@ -372,6 +387,8 @@ void hm_dense_operator_destroy(hm_operator* op) {
   if (!op || !op->ctx) return;
   hm_dense_ctx* d = (hm_dense_ctx*)op->ctx;
   if (d->flags) cudaFree(d->flags);
+  if (d->xs) cudaFree(d->xs);
+  if (d->err) cudaFree(d->err);
   delete d;
   op->ctx = nullptr;
   op->apply = nullptr;

@@ -72,6 +72,14 @@ void launch_dense_gemm(const T* A, int64_t lda, int trans, int64_t n, int64_t nc
                        const T* X, int64_t ldx, T* Y, int64_t ldy, uint8_t* flags,
                        cudaStream_t st);
 
+size_t gemm_tc_smem_bytes();
+int64_t gemm_tc_xs_elems(int64_t n, int64_t ncols);
+bool gemm_tc_supported(const float* A, int64_t lda, int64_t n);
+// 0: launched; 1: layout not supported (see gemm_tc_supported); 2: TMA map failed
+int launch_gemm_tc(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
+                   const float* X, int64_t ldx, float* Y, int64_t ldy, void* xs_work,
+                   uint8_t* flags, int* err, cudaStream_t st);
+
 void launch_dense_gemm_a32(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
                            const double* X, int64_t ldx, double* Y, int64_t ldy, uint8_t* flags,
                            cudaStream_t st);
@@ -234,6 +242,9 @@ struct hm_dense_ctx {
   int32_t dtype = 0;
   uint8_t* flags = nullptr;  // zero-tile flags scratch
   int64_t flags_bytes = 0;
+  void* xs = nullptr;        // split copy of X for the tensor-core engine
+  int64_t xs_bytes = 0;
+  int* err = nullptr;        // device flag raised by a kernel that gave up waiting
 };
 
 struct hm_handle {
