@@ -266,6 +266,37 @@ hm_status hm_hodlr_factored_apply(const hm_tree* tree, int32_t k, const float* U
                                   float* y, void* stream);
 
 /*
+ * hm_hodlr_factored_apply without per-call device allocation (the paper has no
+ * counterpart: this is an interface for callers, not a step of the method).
+ * Same arguments, layouts and results as hm_hodlr_factored_apply, computed by
+ * the same kernels; only the scratch differs.  For callers that cannot let the
+ * library allocate device memory on each call: applications whose own
+ * allocator has reserved the device memory (a per-call allocation from the
+ * CUDA memory pool could then fail), or loops that must not touch the memory
+ * pool at all.
+ *  - Scratch: a fixed 8 MiB buffer compiled into the library (reserved on every
+ *    device where the library's device code is loaded).  A call needs
+ *    4 * k * (c + 2^(L+1)) bytes, c = the number of 256-row chunks over all
+ *    nodes of levels 1..L (about L * N / 256); larger requests return
+ *    HM_EINVAL naming the size, before anything is launched.
+ *  - Nothing in the scratch needs to start at zero: every element a call reads
+ *    is written earlier in the same call.
+ *  - All calls on one device share the one buffer: two calls whose work may
+ *    overlap (different streams, or different host threads, without ordering
+ *    between them) race on it and give wrong results.  Order them on one
+ *    stream or with events.
+ *  - The first call on a device looks up the buffer's address
+ *    (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *    first call before any stream capture.
+ *  - The tree's index tables must already be on the device (uploading them
+ *    allocates): one call of hm_hodlr_factored_apply with this tree, on the
+ *    same device, uploads them; otherwise HM_EINVAL.
+ */
+hm_status hm_hodlr_factored_apply_noalloc(const hm_tree* tree, int32_t k, const float* U,
+                                          const float* V, const float* D, int trans,
+                                          const float* x, float* y, void* stream);
+
+/*
  * Hand-written adjoint (vector-Jacobian product) of y = H x at the factors
  * above.  Given r (device, length N), writes
  *   gx = scale * H^T r,            gU_j(I_a) = scale * r(I_a) (V_j(I_b)^T x(I_b))^T,

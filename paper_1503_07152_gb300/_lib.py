@@ -62,6 +62,7 @@ _sig = {
     "hm_node_rank": ([_P, C.c_int64, C.POINTER(C.c_int32)], C.c_int),
     "hm_destroy": ([_P], None),
     "hm_hodlr_factored_apply": ([_P, C.c_int32, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
+    "hm_hodlr_factored_apply_noalloc": ([_P, C.c_int32, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
     "hm_hodlr_factored_adjoint": ([_P, C.c_int32, _P, _P, _P, _P, _P, C.c_float, _P, _P, _P, _P, _P],
                                   C.c_int),
     "hm_gen_log_kernel": ([_P, C.c_int64, C.c_int64, _P], C.c_int),
@@ -282,6 +283,13 @@ def hm_node_rank(h: Handle, node: int) -> int:
 def hm_hodlr_factored_apply(tree: Tree, k: int, U, V, D, x, y, trans: int = 0, stream=None) -> None:
     _check(lib.hm_hodlr_factored_apply(tree.ptr, k, _ptr(U), _ptr(V), _ptr(D), trans, _ptr(x), _ptr(y),
                                        C.c_void_p(_stream(stream))), "hm_hodlr_factored_apply")
+
+
+def hm_hodlr_factored_apply_noalloc(tree: Tree, k: int, U, V, D, x, y, trans: int = 0,
+                                    stream=None) -> None:
+    _check(lib.hm_hodlr_factored_apply_noalloc(tree.ptr, k, _ptr(U), _ptr(V), _ptr(D), trans, _ptr(x),
+                                               _ptr(y), C.c_void_p(_stream(stream))),
+           "hm_hodlr_factored_apply_noalloc")
 
 
 def hm_hodlr_factored_adjoint(tree: Tree, k: int, U, V, D, x, r, scale=1.0, gx=None, gU=None,
