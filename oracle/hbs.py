@@ -44,7 +44,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .hodlr import ApplyFn, gaussian_test_matrix, identity_test_matrix
-from .lowrank import RANGE_FLOOR, interp_decomp
+from .lowrank import RANGE_FLOOR, fix_signs, interp_decomp
 from .tree import Tree
 
 EPS_SCALE = 0.01
@@ -124,6 +124,7 @@ def _svd_r(M: np.ndarray, r: int, floor: bool = False):
     singular value is below RANGE_FLOOR * sigma_1 are returned as zero columns
     (significant-range reading, as for ``lowrank.range_basis``)."""
     U, s, Vt = np.linalg.svd(M, full_matrices=False)
+    U, Vt = fix_signs(U, Vt)
     U, s, V = U[:, :r].copy(), s[:r].copy(), Vt[:r].T.copy()
     if floor and s.size:
         dead = ~(s > RANGE_FLOOR * s[0])

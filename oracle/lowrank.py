@@ -9,6 +9,12 @@ Readings:
 * ``svd(A, eps)`` keeps the singular values sigma_j > eps (eps is an absolute
   bound on the spectral truncation error, Eckart-Young, Sec. 2.3), at least one
   term; ``svd(A, k)`` keeps min(k, rank-dim) terms.
+* The sign of each singular triplet (u_j, v_j) is free in the paper; it is
+  fixed here: the largest-magnitude entry of v_j is positive (the first such
+  entry on ties), see ``fix_signs``.  With packed test matrices the sample of
+  one node carries the peel residual of other nodes in the same columns, so the
+  result depends on these signs at the level of the truncation error; one
+  convention makes it reproducible.
 * ``id`` is computed from a column-pivoted Householder QR (Businger-Golub: at
   each step the remaining column of largest norm is moved to the front; on ties
   the lowest index wins), A(:, J) = Q R, rank k by |R_jj| > eps (mode 3) or k
@@ -31,6 +37,18 @@ def qr_basis(A: np.ndarray) -> np.ndarray:
     return Q
 
 
+def fix_signs(U: np.ndarray, Vt: np.ndarray):
+    """Sign convention for singular triplets: flip (u_j, v_j) so that the
+    largest-magnitude entry of the right singular vector v_j (row j of Vt) is
+    positive; on ties the first such entry decides."""
+    if Vt.shape[0] == 0:
+        return U, Vt
+    idx = np.argmax(np.abs(Vt), axis=1)  # argmax returns the first maximum
+    sg = np.sign(Vt[np.arange(Vt.shape[0]), idx])
+    sg[sg == 0] = 1.0
+    return U * sg[None, :], Vt * sg[:, None]
+
+
 RANGE_FLOOR = 1e-12
 
 
@@ -43,7 +61,8 @@ def range_basis(A: np.ndarray, rel_floor: float = RANGE_FLOOR) -> np.ndarray:
     up an arbitrary share of the coarser levels' truncation error through the
     transpose peel).  The default floor 1e-12 lies well above FP64 rounding and
     far below any compression tolerance."""
-    U, s, _ = np.linalg.svd(A, full_matrices=False)
+    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    U, Vt = fix_signs(U, Vt)
     if s.size == 0 or s[0] == 0.0:
         return U[:, :0]
     return U[:, : int(np.count_nonzero(s > rel_floor * s[0]))]
@@ -52,6 +71,7 @@ def range_basis(A: np.ndarray, rel_floor: float = RANGE_FLOOR) -> np.ndarray:
 def svd_trunc(A: np.ndarray, k: int | None = None, eps: float | None = None):
     """[U, s, Vt] truncated per mode 2 (k) or mode 3 (eps); mode 1 if neither."""
     U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    U, Vt = fix_signs(U, Vt)
     n = s.size
     if k is not None:
         n = min(int(k), s.size)

@@ -187,10 +187,29 @@ __global__ __launch_bounds__(512) void k_jacobi(const int32_t* __restrict__ node
     order[rk] = j;
   }
   __syncthreads();
+  // sign convention of the singular triplets: the largest-magnitude entry of
+  // each right singular vector is positive (the first such entry on ties)
+  __shared__ signed char sgn[128];
+  for (int j = warp; j < c; j += nwarps) {
+    const T* v = Vm + order[j] * c;
+    double best = -1.0;
+    int bi = c;
+    for (int i = lane; i < c; i += 32) {
+      const double a = fabs((double)v[i]);
+      if (a > best) { best = a; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) sgn[j] = (bi < c && v[bi] < (T)0) ? -1 : 1;
+  }
+  __syncthreads();
   T* Wn = W + (int64_t)node * c * c;
   for (int idx = tid; idx < c * c; idx += blockDim.x) {
     const int rr = idx % c, col = idx / c;
-    Wn[idx] = Vm[order[col] * c + rr];
+    Wn[idx] = sgn[col] < 0 ? -Vm[order[col] * c + rr] : Vm[order[col] * c + rr];
   }
   for (int j = tid; j < c; j += blockDim.x) sigma[(int64_t)node * c + j] = (T)sv[order[j]];
 }

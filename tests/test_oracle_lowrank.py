@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from oracle.lowrank import interp_decomp, pivoted_qr, qr_basis, range_basis, svd_trunc
+from oracle.lowrank import fix_signs, interp_decomp, pivoted_qr, qr_basis, range_basis, svd_trunc
 
 
 def _lowrank(m, n, k, seed, decay=1e-3):
@@ -80,3 +80,30 @@ def test_range_basis_spans_numerical_range():
     assert range_basis(A).shape[1] == 6
     Z = np.zeros((10, 4))
     assert range_basis(Z).shape[1] == 0
+
+
+def test_singular_vector_sign_convention_closed_form():
+    """A = U0 diag(s0) V0^T with known factors whose right vectors already obey the
+    convention: the oracle's svd must return U0 itself (not -U0 in any column),
+    and every returned right vector must have a positive largest entry."""
+    rng = np.random.default_rng(11)
+    m, n = 30, 6
+    U0, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V0, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    idx = np.argmax(np.abs(V0), axis=0)
+    V0 = V0 * np.sign(V0[idx, np.arange(n)])[None, :]
+    s0 = np.array([9.0, 5.0, 3.0, 2.0, 1.0, 0.5])
+    A = U0 @ np.diag(s0) @ V0.T
+    U, s, Vt = svd_trunc(A)
+    assert np.allclose(s, s0, rtol=1e-13)
+    assert np.allclose(U, U0, atol=1e-12)
+    assert np.allclose(Vt, V0.T, atol=1e-12)
+    Ur = range_basis(A)
+    assert np.allclose(Ur, U0, atol=1e-12)
+    # the convention itself, and that it keeps A = U S V^T
+    B = rng.standard_normal((8, 5))
+    Ub, sb, Vtb = np.linalg.svd(B, full_matrices=False)
+    Uf, Vtf = fix_signs(-Ub, -Vtb)
+    rows = np.arange(Vtf.shape[0])
+    assert np.all(Vtf[rows, np.argmax(np.abs(Vtf), axis=1)] > 0)
+    assert np.allclose(Uf @ np.diag(sb) @ Vtf, B, atol=1e-13)
