@@ -211,7 +211,7 @@ hm_status tree_plans(hm_tree* t) {
     lp.node0 = 1 << lv;
     build_chunks(t, lv, 256, lp.tn, &lp.tn_begin);
     build_chunks(t, lv, 64, lp.nn, nullptr);
-    build_tsqr(t, lv, 128, lp);
+    build_tsqr(t, lv, kTsqrRows, lp);
     lp.n_tn = (int)lp.tn.size();
     lp.n_nn = (int)lp.nn.size();
   }

@@ -75,14 +75,16 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
   const LevelPlan& lp = c.tree->plans[lv];
   const int64_t N = c.N;
   const int r = c.r;
-  const int rows_max = std::max(128, 2 * pc);
-  if ((size_t)rows_max * pc * sizeof(T) > 220 * 1024 || (size_t)2 * pc * pc * sizeof(T) > 220 * 1024) {
+  const size_t lim = 220 * 1024;
+  if (pc > 128 || (size_t)kTsqrRows * pc * sizeof(T) > lim ||
+      (size_t)pc * (pc + 1) * sizeof(T) > lim ||
+      (size_t)(sizeof(T) == 4 ? 2 : 1) * pc * pc * sizeof(T) > lim) {
     set_error("panel too wide for the shared-memory QR in this precision");
     return HM_EUNSUPPORTED;
   }
   for (size_t rd = 0; rd < lp.d_rounds.size(); ++rd)
-    launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rows_max, P, N, pc, c.Rw,
-                   c.st);
+    launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rd > 0 ? 1 : 0, P, N, pc,
+                   c.Rw, c.st);
   launch_jacobi<T>(lp.d_final_slot, lp.nnodes, c.Rw, pc, c.W, c.sig, c.st);
   // Directions of the sample range below floor_rel * sigma_1 are dropped.  In
   // FP64 the floor sits well above rounding noise (1e-12): directions near the

@@ -45,6 +45,9 @@ struct Chunk {
 
 // TSQR task: Householder QR of up to two stacked sources.
 //  kind 0: rows [r0, r1) of the panel;  kind 1: an R slot (c x c, row-major).
+// rows of one leaf block of the TSQR (and the shared-memory tile of its QR)
+constexpr int kTsqrRows = 128;
+
 struct TsqrTask {
   int32_t node;      // heap id (for bookkeeping)
   int32_t nsrc;      // 1 or 2
@@ -103,7 +106,7 @@ void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int6
                    T beta, cudaStream_t st);
 
 template <typename T>
-void launch_tsqr(const TsqrTask* tasks, int ntasks, int rows_max, const T* P, int64_t ldp,
+void launch_tsqr(const TsqrTask* tasks, int ntasks, int merge, const T* P, int64_t ldp,
                  int c, T* R, cudaStream_t st);
 
 // One-sided Jacobi SVD of the final R of every node: W (c x c col-major, sorted

@@ -1,9 +1,17 @@
 // Per-node orthonormalization and truncated SVD of sample panels, batched over
 // all nodes of a level (uneven sizes in one launch):
-//   1. TSQR: Householder QR of row blocks in shared memory, R factors merged
-//      pairwise in a tree (R only; the panel P = Q R is never formed via Q).
-//   2. One-sided (Hestenes) Jacobi SVD of each node's final R: R = W_L S W^T;
-//      right vectors W and singular values S, sorted descending.
+//   1. TSQR: Householder QR of row blocks of at most 128 rows in shared memory;
+//      the R factors are merged pairwise in a tree by a Householder QR of the
+//      stacked pair that keeps both triangles packed (R only; Q is never formed).
+//   2. SVD of each node's final R.  FP64: a column-pivoted QR R P = Q2 R2
+//      (Businger-Golub), then one-sided (Hestenes) Jacobi on X = R2^T.  The normalized
+//      rotated columns of X are its left singular vectors U_x, so the right
+//      singular vectors of R are W = P U_x and no rotation has to be
+//      accumulated; R2^T has graded columns, so the sweeps converge quickly and
+//      the small singular values keep their relative accuracy.  FP32: one-sided
+//      Jacobi on R with the rotations accumulated into W (orthonormal to
+//      working precision, which FP32 needs).  Sorted descending, with a fixed
+//      sign convention.
 //   3. Truncation: the rank k of the node (mode 2 fixed k, or mode 3 tolerance,
 //      Sec. 2.6) and T1 = W(:, :k) S^{-1}, so that Q1 = P T1 has orthonormal
 //      columns in exact arithmetic (the left singular vectors of P).
@@ -105,9 +113,266 @@ __global__ __launch_bounds__(256) void k_tsqr(const TsqrTask* __restrict__ tasks
   }
 }
 
-// One-sided Jacobi SVD of R (c x c); round-robin pairing, one warp per pair.
+// Merge of two c x c upper triangular factors: R = qr([R1; R2]).  The j-th
+// Householder vector touches row j of R1 and rows 0..j of R2 only, so both
+// triangles stay packed (column j holds rows 0..j at offset j (j + 1) / 2).
+template <typename T>
+__global__ __launch_bounds__(256) void k_tsqr_merge(const TsqrTask* __restrict__ tasks, int c,
+                                                    T* __restrict__ R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int pk = c * (c + 1) / 2;
+  T* A = reinterpret_cast<T*>(smem_raw);  // R1, packed upper
+  T* B = A + pk;                          // R2, packed upper
+  __shared__ double red[8];
+  __shared__ T sh_alpha, sh_beta, sh_v0;
+  const TsqrTask tk = tasks[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* R1 = R + (int64_t)tk.slot[0] * c * c;
+  const T* R2 = R + (int64_t)tk.slot[1] * c * c;
+  for (int idx = tid; idx < c * c; idx += 256) {
+    const int rr = idx / c, col = idx % c;
+    if (rr <= col) {
+      A[col * (col + 1) / 2 + rr] = R1[idx];
+      B[col * (col + 1) / 2 + rr] = R2[idx];
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < c; ++j) {
+    const T* bj = B + j * (j + 1) / 2;  // rows 0..j of column j of R2
+    T s = 0;
+    for (int i = tid; i <= j; i += 256) s = fma(bj[i], bj[i], s);
+    s = warp_sum(s);
+    if (lane == 0) red[warp] = (double)s;
+    __syncthreads();
+    if (tid == 0) {
+      double tail = 0.0;
+      for (int w = 0; w < 8; ++w) tail += red[w];
+      const double x0 = (double)A[j * (j + 1) / 2 + j];
+      const double nrm = sqrt(x0 * x0 + tail);
+      const double alpha = (x0 > 0.0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = v0 * v0 + tail;
+      sh_alpha = (T)alpha;
+      sh_v0 = (T)v0;
+      sh_beta = (vtv > 0.0) ? (T)(2.0 / vtv) : (T)0;
+    }
+    __syncthreads();
+    const T beta = sh_beta, v0 = sh_v0;
+    if (beta != (T)0) {
+      for (int k = j + 1 + warp; k < c; k += 8) {
+        T* ak = A + k * (k + 1) / 2;
+        T* bk = B + k * (k + 1) / 2;
+        T dot = 0;
+        for (int i = lane; i <= j; i += 32) dot = fma(bj[i], bk[i], dot);
+        dot = warp_sum(dot) + v0 * ak[j];
+        const T f = beta * dot;
+        for (int i = lane; i <= j; i += 32) bk[i] = fma(-f, bj[i], bk[i]);
+        if (lane == 0) ak[j] = fma(-f, v0, ak[j]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && beta != (T)0) A[j * (j + 1) / 2 + j] = sh_alpha;
+    __syncthreads();
+  }
+  T* Ro = R + (int64_t)tk.out_slot * c * c;
+  for (int idx = tid; idx < c * c; idx += 256) {
+    const int rr = idx / c, col = idx % c;
+    Ro[idx] = (rr <= col) ? A[col * (col + 1) / 2 + rr] : (T)0;
+  }
+}
+
+// SVD of R (c x c, c <= 128): pivoted QR preconditioning, then one-sided Jacobi
+// on R2^T with round-robin pairing (one warp per pair).  Writes W (c x c,
+// column-major, right singular vectors of R) and sigma, descending.
 template <typename T>
 __global__ __launch_bounds__(512) void k_jacobi(const int32_t* __restrict__ node_slot,
+                                                const T* __restrict__ R, int c,
+                                                T* __restrict__ W, T* __restrict__ sigma) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* M = reinterpret_cast<T*>(smem_raw);  // column j at M + j * c
+  __shared__ int rotated;
+  __shared__ double sv[128];
+  __shared__ double cn[128];
+  __shared__ int perm[128];
+  __shared__ int order[128];
+  __shared__ signed char sgn[128];
+  __shared__ double red_v[16];
+  __shared__ int red_i[16];
+  __shared__ T sh_alpha, sh_beta;
+  const int node = blockIdx.x;
+  const T* Rs = R + (int64_t)node_slot[node] * c * c;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int idx = tid; idx < c * c; idx += blockDim.x) {
+    const int rr = idx / c, col = idx % c;
+    M[col * c + rr] = Rs[idx];
+  }
+  for (int j = tid; j < c; j += blockDim.x) perm[j] = j;
+  __syncthreads();
+  // ---- column-pivoted Householder QR of M (norms recomputed every step)
+  for (int j = 0; j < c; ++j) {
+    for (int k = j + warp; k < c; k += nwarps) {
+      const T* mk = M + k * c;
+      T s = 0;
+      for (int i = j + lane; i < c; i += 32) s = fma(mk[i], mk[i], s);
+      s = warp_sum(s);
+      if (lane == 0) cn[k] = (double)s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = c;
+      for (int k = j + lane; k < c; k += 32)
+        if (cn[k] > best) { best = cn[k]; bi = k; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { red_i[0] = bi; red_v[0] = best; }
+    }
+    __syncthreads();
+    const int p = red_i[0];
+    if (p != j && p < c) {
+      for (int i = tid; i < c; i += blockDim.x) {
+        const T t = M[j * c + i];
+        M[j * c + i] = M[p * c + i];
+        M[p * c + i] = t;
+      }
+      if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+    }
+    __syncthreads();
+    T* mj = M + j * c;
+    if (tid == 0) {
+      const double tot = red_v[0] > 0.0 ? red_v[0] : 0.0;
+      const double x0 = (double)mj[j];
+      const double nrm = sqrt(tot);
+      const double alpha = (x0 > 0.0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = tot - x0 * x0 + v0 * v0;
+      sh_alpha = (T)alpha;
+      sh_beta = (vtv > 0.0) ? (T)(2.0 / vtv) : (T)0;
+      mj[j] = (T)v0;
+    }
+    __syncthreads();
+    const T beta = sh_beta;
+    if (beta != (T)0) {
+      for (int k = j + 1 + warp; k < c; k += nwarps) {
+        T* mk = M + k * c;
+        T dot = 0;
+        for (int i = j + lane; i < c; i += 32) dot = fma(mj[i], mk[i], dot);
+        dot = warp_sum(dot);
+        const T f = beta * dot;
+        for (int i = j + lane; i < c; i += 32) mk[i] = fma(-f, mj[i], mk[i]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) mj[j] = (beta != (T)0) ? sh_alpha : mj[j];
+    __syncthreads();
+  }
+  // ---- X = R2^T in place (column i of X is row i of R2); below the diagonal
+  // of X the Householder vectors are replaced by R2, above it by zeros
+  for (int idx = tid; idx < c * c; idx += blockDim.x) {
+    const int i = idx / c, j = idx % c;  // pairs with i < j
+    if (i < j) {
+      M[i * c + j] = M[j * c + i];
+      M[j * c + i] = (T)0;
+    }
+  }
+  __syncthreads();
+  const int cp = (c + 1) & ~1;  // even number of slots; slot c (odd c) is a bye
+  // a pair is rotated while its correlation exceeds the rounding level of the
+  // length-c dot products that measure it
+  const T tol = (T)(Eps<T>::v * sqrt((double)c));
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < cp - 1; ++step) {
+      for (int pi = warp; pi < cp / 2; pi += nwarps) {
+        // circle method: slot 0 fixed, the others rotate
+        const int a = pi, b = cp - 1 - pi;
+        const int p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
+        const int q = ((b - 1 + step) % (cp - 1)) + 1;
+        if (p >= c || q >= c) continue;
+        T* ap = M + p * c;
+        T* aq = M + q * c;
+        T alT = 0, beT = 0, gaT = 0;
+        for (int i = lane; i < c; i += 32) {
+          const T x = ap[i], y = aq[i];
+          alT = fma(x, x, alT); beT = fma(y, y, beT); gaT = fma(x, y, gaT);
+        }
+        const T al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
+        if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const T zeta = (be - al) / ((T)2 * ga);
+          const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+          const T tc = (T)1 / sqrt((T)1 + t * t), ts = tc * t;
+          for (int i = lane; i < c; i += 32) {
+            const T x = ap[i], y = aq[i];
+            ap[i] = tc * x - ts * y;
+            aq[i] = ts * x + tc * y;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  for (int j = warp; j < c; j += nwarps) {
+    T s = 0;
+    for (int i = lane; i < c; i += 32) s = fma(M[j * c + i], M[j * c + i], s);
+    s = warp_sum(s);
+    // a non-finite column sorts last (the samples' NaN/Inf flag reports it), so
+    // that the ranks below always form a permutation
+    if (lane == 0) sv[j] = isfinite((double)s) ? sqrt((double)s) : -1.0;
+  }
+  __syncthreads();
+  for (int j = tid; j < c; j += blockDim.x) {
+    int rk = 0;
+    for (int i = 0; i < c; ++i) rk += (sv[i] > sv[j]) || (sv[i] == sv[j] && i < j);
+    order[rk] = j;
+  }
+  __syncthreads();
+  // W(:, col) = P U_x(:, order[col]): row perm[i] of W is row i of U_x.  Sign
+  // convention of the singular triplets: the largest-magnitude entry of each
+  // right singular vector is positive (the first such entry, in W's row order,
+  // on ties).
+  for (int j = warp; j < c; j += nwarps) {
+    const T* x = M + order[j] * c;
+    double best = -1.0;
+    int bi = c;
+    T bv = 0;
+    for (int i = lane; i < c; i += 32) {
+      const double a = fabs((double)x[i]);
+      const int row = perm[i];
+      if (a > best || (a == best && row < bi)) { best = a; bi = row; bv = x[i]; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = ov; }
+    }
+    if (lane == 0) sgn[j] = (bv < (T)0) ? -1 : 1;
+  }
+  __syncthreads();
+  T* Wn = W + (int64_t)node * c * c;
+  for (int idx = tid; idx < c * c; idx += blockDim.x) {
+    const int i = idx % c, col = idx / c;
+    const int j = order[col];
+    const double s = sv[j];
+    const T u = (s > 0.0) ? (T)((double)M[j * c + i] / s) : (T)0;
+    Wn[perm[i] + col * c] = sgn[col] < 0 ? -u : u;
+  }
+  for (int j = tid; j < c; j += blockDim.x) sigma[(int64_t)node * c + j] = (T)(sv[order[j]] > 0.0 ? sv[order[j]] : 0.0);
+}
+
+// One-sided Jacobi SVD of R (c x c) with the rotations accumulated into W;
+// round-robin pairing, one warp per pair.  Used in FP32, where it keeps the
+// right singular vectors orthonormal to working precision.
+template <typename T>
+__global__ __launch_bounds__(512) void k_jacobi_acc(const int32_t* __restrict__ node_slot,
                                                 const T* __restrict__ R, int c,
                                                 T* __restrict__ W, T* __restrict__ sigma) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -353,25 +618,38 @@ __global__ __launch_bounds__(256) void k_cholqr(const T* __restrict__ G, int kca
 }  // namespace
 
 template <typename T>
-void launch_tsqr(const TsqrTask* tasks, int ntasks, int rows_max, const T* P, int64_t ldp, int c,
+void launch_tsqr(const TsqrTask* tasks, int ntasks, int merge, const T* P, int64_t ldp, int c,
                  T* R, cudaStream_t st) {
   count_launches(1);
-  const int ldm = rows_max;
-  const size_t smem = (size_t)ldm * c * sizeof(T);
-  cudaFuncSetAttribute(k_tsqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_tsqr<T><<<ntasks, 256, smem, st>>>(tasks, P, ldp, c, R, ldm);
+  if (!merge) {
+    const int ldm = kTsqrRows;
+    const size_t smem = (size_t)ldm * c * sizeof(T);
+    cudaFuncSetAttribute(k_tsqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tsqr<T><<<ntasks, 256, smem, st>>>(tasks, P, ldp, c, R, ldm);
+  } else {
+    const size_t smem = (size_t)c * (c + 1) * sizeof(T);
+    cudaFuncSetAttribute(k_tsqr_merge<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_tsqr_merge<T><<<ntasks, 256, smem, st>>>(tasks, c, R);
+  }
 }
 
 template <typename T>
 void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W, T* sigma,
                    cudaStream_t st) {
   count_launches(1);
-  const size_t smem = (size_t)2 * c * c * sizeof(T);
-  cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int threads = ((c / 2 + 31) / 32) * 32 * 32;
   if (threads > 512) threads = 512;
   if (threads < 64) threads = 64;
-  k_jacobi<T><<<nnodes, threads, smem, st>>>(node_slot, R, c, W, sigma);
+  if (sizeof(T) == 4) {
+    const size_t smem = (size_t)2 * c * c * sizeof(T);
+    cudaFuncSetAttribute(k_jacobi_acc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi_acc<T><<<nnodes, threads, smem, st>>>(node_slot, R, c, W, sigma);
+  } else {
+    const size_t smem = (size_t)c * c * sizeof(T);
+    cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi<T><<<nnodes, threads, smem, st>>>(node_slot, R, c, W, sigma);
+  }
 }
 
 template <typename T>
