@@ -4,7 +4,8 @@
 //      the R factors are merged pairwise in a tree by a Householder QR of the
 //      stacked pair that keeps both triangles packed (R only; Q is never formed).
 //   2. SVD of each node's final R.  FP64: a column-pivoted QR R P = Q2 R2
-//      (Businger-Golub), then one-sided (Hestenes) Jacobi on X = R2^T.  The normalized
+//      (Businger-Golub), then one-sided (Hestenes) Jacobi on X = R2^T, run in
+//      FP32 first and finished in FP64 (see k_jacobi_mp).  The normalized
 //      rotated columns of X are its left singular vectors U_x, so the right
 //      singular vectors of R are W = P U_x and no rotation has to be
 //      accumulated; R2^T has graded columns, so the sweeps converge quickly and
@@ -21,6 +22,8 @@
 //      HODLR and HBS figures).
 // These realize qr(.) and svd(., k | eps) of Secs. 2.2-2.3 / 2.6 for panels too
 // tall for one block.
+#include <algorithm>
+
 #include "hm_internal.h"
 
 namespace hm {
@@ -181,193 +184,6 @@ __global__ __launch_bounds__(256) void k_tsqr_merge(const TsqrTask* __restrict__
   }
 }
 
-// SVD of R (c x c, c <= 128): pivoted QR preconditioning, then one-sided Jacobi
-// on R2^T with round-robin pairing (one warp per pair).  Writes W (c x c,
-// column-major, right singular vectors of R) and sigma, descending.
-template <typename T>
-__global__ __launch_bounds__(512) void k_jacobi(const int32_t* __restrict__ node_slot,
-                                                const T* __restrict__ R, int c,
-                                                T* __restrict__ W, T* __restrict__ sigma) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* M = reinterpret_cast<T*>(smem_raw);  // column j at M + j * c
-  __shared__ int rotated;
-  __shared__ double sv[128];
-  __shared__ double cn[128];
-  __shared__ int perm[128];
-  __shared__ int order[128];
-  __shared__ signed char sgn[128];
-  __shared__ double red_v[16];
-  __shared__ int red_i[16];
-  __shared__ T sh_alpha, sh_beta;
-  const int node = blockIdx.x;
-  const T* Rs = R + (int64_t)node_slot[node] * c * c;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  for (int idx = tid; idx < c * c; idx += blockDim.x) {
-    const int rr = idx / c, col = idx % c;
-    M[col * c + rr] = Rs[idx];
-  }
-  for (int j = tid; j < c; j += blockDim.x) perm[j] = j;
-  __syncthreads();
-  // ---- column-pivoted Householder QR of M (norms recomputed every step)
-  for (int j = 0; j < c; ++j) {
-    for (int k = j + warp; k < c; k += nwarps) {
-      const T* mk = M + k * c;
-      T s = 0;
-      for (int i = j + lane; i < c; i += 32) s = fma(mk[i], mk[i], s);
-      s = warp_sum(s);
-      if (lane == 0) cn[k] = (double)s;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double best = -1.0;
-      int bi = c;
-      for (int k = j + lane; k < c; k += 32)
-        if (cn[k] > best) { best = cn[k]; bi = k; }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) { red_i[0] = bi; red_v[0] = best; }
-    }
-    __syncthreads();
-    const int p = red_i[0];
-    if (p != j && p < c) {
-      for (int i = tid; i < c; i += blockDim.x) {
-        const T t = M[j * c + i];
-        M[j * c + i] = M[p * c + i];
-        M[p * c + i] = t;
-      }
-      if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
-    }
-    __syncthreads();
-    T* mj = M + j * c;
-    if (tid == 0) {
-      const double tot = red_v[0] > 0.0 ? red_v[0] : 0.0;
-      const double x0 = (double)mj[j];
-      const double nrm = sqrt(tot);
-      const double alpha = (x0 > 0.0) ? -nrm : nrm;
-      const double v0 = x0 - alpha;
-      const double vtv = tot - x0 * x0 + v0 * v0;
-      sh_alpha = (T)alpha;
-      sh_beta = (vtv > 0.0) ? (T)(2.0 / vtv) : (T)0;
-      mj[j] = (T)v0;
-    }
-    __syncthreads();
-    const T beta = sh_beta;
-    if (beta != (T)0) {
-      for (int k = j + 1 + warp; k < c; k += nwarps) {
-        T* mk = M + k * c;
-        T dot = 0;
-        for (int i = j + lane; i < c; i += 32) dot = fma(mj[i], mk[i], dot);
-        dot = warp_sum(dot);
-        const T f = beta * dot;
-        for (int i = j + lane; i < c; i += 32) mk[i] = fma(-f, mj[i], mk[i]);
-      }
-    }
-    __syncthreads();
-    if (tid == 0) mj[j] = (beta != (T)0) ? sh_alpha : mj[j];
-    __syncthreads();
-  }
-  // ---- X = R2^T in place (column i of X is row i of R2); below the diagonal
-  // of X the Householder vectors are replaced by R2, above it by zeros
-  for (int idx = tid; idx < c * c; idx += blockDim.x) {
-    const int i = idx / c, j = idx % c;  // pairs with i < j
-    if (i < j) {
-      M[i * c + j] = M[j * c + i];
-      M[j * c + i] = (T)0;
-    }
-  }
-  __syncthreads();
-  const int cp = (c + 1) & ~1;  // even number of slots; slot c (odd c) is a bye
-  // a pair is rotated while its correlation exceeds the rounding level of the
-  // length-c dot products that measure it
-  const T tol = (T)(Eps<T>::v * sqrt((double)c));
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    for (int step = 0; step < cp - 1; ++step) {
-      for (int pi = warp; pi < cp / 2; pi += nwarps) {
-        // circle method: slot 0 fixed, the others rotate
-        const int a = pi, b = cp - 1 - pi;
-        const int p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
-        const int q = ((b - 1 + step) % (cp - 1)) + 1;
-        if (p >= c || q >= c) continue;
-        T* ap = M + p * c;
-        T* aq = M + q * c;
-        T alT = 0, beT = 0, gaT = 0;
-        for (int i = lane; i < c; i += 32) {
-          const T x = ap[i], y = aq[i];
-          alT = fma(x, x, alT); beT = fma(y, y, beT); gaT = fma(x, y, gaT);
-        }
-        const T al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
-        if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          const T zeta = (be - al) / ((T)2 * ga);
-          const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-          const T tc = (T)1 / sqrt((T)1 + t * t), ts = tc * t;
-          for (int i = lane; i < c; i += 32) {
-            const T x = ap[i], y = aq[i];
-            ap[i] = tc * x - ts * y;
-            aq[i] = ts * x + tc * y;
-          }
-          if (lane == 0) rotated = 1;
-        }
-      }
-      __syncthreads();
-    }
-    const int any = rotated;
-    __syncthreads();
-    if (!any) break;
-  }
-  for (int j = warp; j < c; j += nwarps) {
-    T s = 0;
-    for (int i = lane; i < c; i += 32) s = fma(M[j * c + i], M[j * c + i], s);
-    s = warp_sum(s);
-    // a non-finite column sorts last (the samples' NaN/Inf flag reports it), so
-    // that the ranks below always form a permutation
-    if (lane == 0) sv[j] = isfinite((double)s) ? sqrt((double)s) : -1.0;
-  }
-  __syncthreads();
-  for (int j = tid; j < c; j += blockDim.x) {
-    int rk = 0;
-    for (int i = 0; i < c; ++i) rk += (sv[i] > sv[j]) || (sv[i] == sv[j] && i < j);
-    order[rk] = j;
-  }
-  __syncthreads();
-  // W(:, col) = P U_x(:, order[col]): row perm[i] of W is row i of U_x.  Sign
-  // convention of the singular triplets: the largest-magnitude entry of each
-  // right singular vector is positive (the first such entry, in W's row order,
-  // on ties).
-  for (int j = warp; j < c; j += nwarps) {
-    const T* x = M + order[j] * c;
-    double best = -1.0;
-    int bi = c;
-    T bv = 0;
-    for (int i = lane; i < c; i += 32) {
-      const double a = fabs((double)x[i]);
-      const int row = perm[i];
-      if (a > best || (a == best && row < bi)) { best = a; bi = row; bv = x[i]; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = ov; }
-    }
-    if (lane == 0) sgn[j] = (bv < (T)0) ? -1 : 1;
-  }
-  __syncthreads();
-  T* Wn = W + (int64_t)node * c * c;
-  for (int idx = tid; idx < c * c; idx += blockDim.x) {
-    const int i = idx % c, col = idx / c;
-    const int j = order[col];
-    const double s = sv[j];
-    const T u = (s > 0.0) ? (T)((double)M[j * c + i] / s) : (T)0;
-    Wn[perm[i] + col * c] = sgn[col] < 0 ? -u : u;
-  }
-  for (int j = tid; j < c; j += blockDim.x) sigma[(int64_t)node * c + j] = (T)(sv[order[j]] > 0.0 ? sv[order[j]] : 0.0);
-}
-
 // One-sided Jacobi SVD of R (c x c) with the rotations accumulated into W;
 // round-robin pairing, one warp per pair.  Used in FP32, where it keeps the
 // right singular vectors orthonormal to working precision.
@@ -477,6 +293,304 @@ __global__ __launch_bounds__(512) void k_jacobi_acc(const int32_t* __restrict__ 
     Wn[idx] = sgn[col] < 0 ? -Vm[order[col] * c + rr] : Vm[order[col] * c + rr];
   }
   for (int j = tid; j < c; j += blockDim.x) sigma[(int64_t)node * c + j] = (T)sv[order[j]];
+}
+
+// FP64 SVD of R (c x c, c <= 128) with the bulk of the Jacobi work in FP32:
+//   A. column-pivoted Householder QR R P = Q2 R2 in FP64; X = R2^T (graded
+//      columns) is parked in the node's W slot in global memory;
+//   B. one-sided Jacobi on float(X) with the rotations accumulated into V32
+//      (FP32 arithmetic, FP32 convergence threshold);
+//   C. Q = CGS2 orthonormalization of V32 in FP64 (orthogonal to FP64
+//      rounding; it differs from the exact V only by the FP32 error of B);
+//   D. X1 = X Q in FP64: same left singular vectors as X, columns orthogonal
+//      to FP32 precision;
+//   E. one-sided Jacobi on X1 in FP64 until the FP64 threshold holds (one or
+//      two sweeps from an FP32-orthogonal start);
+//   F. sigma_j = |X1_j|, right singular vectors of R: W = P U_x, U_x = the
+//      normalized columns; sorted descending, sign convention as in k_jacobi_acc.
+__global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ node_slot,
+                                                   const double* __restrict__ R, int c,
+                                                   double* __restrict__ W,
+                                                   double* __restrict__ sigma) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* M = reinterpret_cast<double*>(smem_raw);  // phase A: c x c, column-major
+  float* V32 = reinterpret_cast<float*>(smem_raw);  // phases B-C: c x c
+  const size_t off_q = (((size_t)c * c * sizeof(float)) + 15) & ~(size_t)15;
+  float* X32 = reinterpret_cast<float*>(smem_raw + off_q);    // phase B
+  double* Q = reinterpret_cast<double*>(smem_raw + off_q);    // phases C-F (X1 after D)
+  __shared__ int rotated;
+  __shared__ double sv[128];
+  __shared__ double cn[128];
+  __shared__ double hb[128];
+  __shared__ int perm[128];
+  __shared__ int order[128];
+  __shared__ signed char sgn[128];
+  __shared__ double red_v[16];
+  __shared__ int red_i[16];
+  __shared__ double sh_alpha, sh_beta;
+  const int node = blockIdx.x;
+  const double* Rs = R + (int64_t)node_slot[node] * c * c;
+  double* Wn = W + (int64_t)node * c * c;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int nthr = blockDim.x;
+  // ---------------------------------------------------------------- A
+  for (int idx = tid; idx < c * c; idx += nthr) {
+    const int rr = idx / c, col = idx % c;
+    M[col * c + rr] = Rs[idx];
+  }
+  for (int j = tid; j < c; j += nthr) perm[j] = j;
+  __syncthreads();
+  for (int j = 0; j < c; ++j) {
+    for (int k = j + warp; k < c; k += nwarps) {
+      const double* mk = M + k * c;
+      double s = 0;
+      for (int i = j + lane; i < c; i += 32) s = fma(mk[i], mk[i], s);
+      s = warp_sum(s);
+      if (lane == 0) cn[k] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = c;
+      for (int k = j + lane; k < c; k += 32)
+        if (cn[k] > best) { best = cn[k]; bi = k; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { red_i[0] = bi; red_v[0] = best; }
+    }
+    __syncthreads();
+    const int p = red_i[0];
+    if (p != j && p < c) {
+      for (int i = tid; i < c; i += nthr) {
+        const double t = M[j * c + i];
+        M[j * c + i] = M[p * c + i];
+        M[p * c + i] = t;
+      }
+      if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+    }
+    __syncthreads();
+    double* mj = M + j * c;
+    if (tid == 0) {
+      const double tot = red_v[0] > 0.0 ? red_v[0] : 0.0;
+      const double x0 = mj[j];
+      const double nrm = sqrt(tot);
+      const double alpha = (x0 > 0.0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = tot - x0 * x0 + v0 * v0;
+      sh_alpha = alpha;
+      sh_beta = (vtv > 0.0) ? 2.0 / vtv : 0.0;
+      mj[j] = v0;
+    }
+    __syncthreads();
+    const double beta = sh_beta;
+    if (beta != 0.0) {
+      for (int k = j + 1 + warp; k < c; k += nwarps) {
+        double* mk = M + k * c;
+        double dot = 0;
+        for (int i = j + lane; i < c; i += 32) dot = fma(mj[i], mk[i], dot);
+        dot = warp_sum(dot);
+        const double f = beta * dot;
+        for (int i = j + lane; i < c; i += 32) mk[i] = fma(-f, mj[i], mk[i]);
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && beta != 0.0) mj[j] = sh_alpha;
+    __syncthreads();
+  }
+  // X = R2^T, column-major, parked in the W slot
+  for (int idx = tid; idx < c * c; idx += nthr) {
+    const int col = idx / c, row = idx % c;  // X(row, col) = R2(col, row), zero above
+    Wn[idx] = (row >= col) ? M[row * c + col] : 0.0;
+  }
+  __syncthreads();
+  // ---------------------------------------------------------------- B
+  for (int idx = tid; idx < c * c; idx += nthr) {
+    X32[idx] = (float)Wn[idx];
+    V32[idx] = (idx / c == idx % c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int cp = (c + 1) & ~1;
+  {
+    const float tol = (float)(Eps<float>::v * sqrt((double)c));
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      if (tid == 0) rotated = 0;
+      __syncthreads();
+      for (int step = 0; step < cp - 1; ++step) {
+        for (int pi = warp; pi < cp / 2; pi += nwarps) {
+          const int a = pi, b = cp - 1 - pi;
+          const int p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
+          const int q = ((b - 1 + step) % (cp - 1)) + 1;
+          if (p >= c || q >= c) continue;
+          float* ap = X32 + p * c;
+          float* aq = X32 + q * c;
+          float alT = 0, beT = 0, gaT = 0;
+          for (int i = lane; i < c; i += 32) {
+            const float x = ap[i], y = aq[i];
+            alT = fmaf(x, x, alT); beT = fmaf(y, y, beT); gaT = fmaf(x, y, gaT);
+          }
+          const float al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
+          if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+            const float zeta = (be - al) / (2.f * ga);
+            const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            const float tc = 1.f / sqrtf(1.f + t * t), ts = tc * t;
+            for (int i = lane; i < c; i += 32) {
+              const float x = ap[i], y = aq[i];
+              ap[i] = tc * x - ts * y;
+              aq[i] = ts * x + tc * y;
+            }
+            float* vp = V32 + p * c;
+            float* vq = V32 + q * c;
+            for (int i = lane; i < c; i += 32) {
+              const float x = vp[i], y = vq[i];
+              vp[i] = tc * x - ts * y;
+              vq[i] = ts * x + tc * y;
+            }
+            if (lane == 0) rotated = 1;
+          }
+        }
+        __syncthreads();
+      }
+      const int any = rotated;
+      __syncthreads();
+      if (!any) break;
+    }
+  }
+  // ---------------------------------------------------------------- C
+  // (X32 is dead; Q overlays it)
+  for (int j = 0; j < c; ++j) {
+    double* qj = Q + j * c;
+    for (int i = tid; i < c; i += nthr) qj[i] = (double)V32[j * c + i];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = warp; i < j; i += nwarps) {
+        const double* qi = Q + i * c;
+        double s = 0;
+        for (int e = lane; e < c; e += 32) s = fma(qi[e], qj[e], s);
+        s = warp_sum(s);
+        if (lane == 0) hb[i] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < c; e += nthr) {
+        double s = 0;
+        for (int i = 0; i < j; ++i) s = fma(hb[i], Q[i * c + e], s);
+        qj[e] -= s;
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      double s = 0;
+      for (int e = lane; e < c; e += 32) s = fma(qj[e], qj[e], s);
+      s = warp_sum(s);
+      if (lane == 0) hb[0] = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+    }
+    __syncthreads();
+    const double inv = hb[0];
+    for (int e = tid; e < c; e += nthr) qj[e] *= inv;
+    __syncthreads();
+  }
+  // ---------------------------------------------------------------- D
+  for (int j = warp; j < c; j += nwarps) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const double* qj = Q + j * c;
+    for (int k = 0; k < c; ++k) {
+      const double qk = qj[k];
+      const double* xk = Wn + (int64_t)k * c;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int row = lane + 32 * rr;
+        if (row < c) acc[rr] = fma(xk[row], qk, acc[rr]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int row = lane + 32 * rr;
+      if (row < c) Q[j * c + row] = acc[rr];
+    }
+  }
+  __syncthreads();
+  // ---------------------------------------------------------------- E
+  {
+    const double tol = Eps<double>::v * sqrt((double)c);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      if (tid == 0) rotated = 0;
+      __syncthreads();
+      for (int step = 0; step < cp - 1; ++step) {
+        for (int pi = warp; pi < cp / 2; pi += nwarps) {
+          const int a = pi, b = cp - 1 - pi;
+          const int p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
+          const int q = ((b - 1 + step) % (cp - 1)) + 1;
+          if (p >= c || q >= c) continue;
+          double* ap = Q + p * c;
+          double* aq = Q + q * c;
+          double alT = 0, beT = 0, gaT = 0;
+          for (int i = lane; i < c; i += 32) {
+            const double x = ap[i], y = aq[i];
+            alT = fma(x, x, alT); beT = fma(y, y, beT); gaT = fma(x, y, gaT);
+          }
+          const double al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
+          if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double tc = 1.0 / sqrt(1.0 + t * t), ts = tc * t;
+            for (int i = lane; i < c; i += 32) {
+              const double x = ap[i], y = aq[i];
+              ap[i] = tc * x - ts * y;
+              aq[i] = ts * x + tc * y;
+            }
+            if (lane == 0) rotated = 1;
+          }
+        }
+        __syncthreads();
+      }
+      const int any = rotated;
+      __syncthreads();
+      if (!any) break;
+    }
+  }
+  // ---------------------------------------------------------------- F
+  for (int j = warp; j < c; j += nwarps) {
+    double s = 0;
+    for (int i = lane; i < c; i += 32) s = fma(Q[j * c + i], Q[j * c + i], s);
+    s = warp_sum(s);
+    if (lane == 0) sv[j] = isfinite(s) ? sqrt(s) : -1.0;
+  }
+  __syncthreads();
+  for (int j = tid; j < c; j += nthr) {
+    int rk = 0;
+    for (int i = 0; i < c; ++i) rk += (sv[i] > sv[j]) || (sv[i] == sv[j] && i < j);
+    order[rk] = j;
+  }
+  __syncthreads();
+  for (int j = warp; j < c; j += nwarps) {
+    const double* x = Q + order[j] * c;
+    double best = -1.0, bv = 0.0;
+    int bi = c;
+    for (int i = lane; i < c; i += 32) {
+      const double a = fabs(x[i]);
+      const int row = perm[i];
+      if (a > best || (a == best && row < bi)) { best = a; bi = row; bv = x[i]; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = ov; }
+    }
+    if (lane == 0) sgn[j] = (bv < 0.0) ? -1 : 1;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < c * c; idx += nthr) {
+    const int i = idx % c, col = idx / c;
+    const int j = order[col];
+    const double s = sv[j];
+    const double u = (s > 0.0) ? Q[j * c + i] / s : 0.0;
+    Wn[perm[i] + col * c] = sgn[col] < 0 ? -u : u;
+  }
+  for (int j = tid; j < c; j += nthr) sigma[(int64_t)node * c + j] = sv[order[j]] > 0.0 ? sv[order[j]] : 0.0;
 }
 
 template <typename T>
@@ -646,9 +760,11 @@ void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W
     cudaFuncSetAttribute(k_jacobi_acc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_jacobi_acc<T><<<nnodes, threads, smem, st>>>(node_slot, R, c, W, sigma);
   } else {
-    const size_t smem = (size_t)c * c * sizeof(T);
-    cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_jacobi<T><<<nnodes, threads, smem, st>>>(node_slot, R, c, W, sigma);
+    const size_t off_q = (((size_t)c * c * sizeof(float)) + 15) & ~(size_t)15;
+    const size_t smem = std::max((size_t)c * c * sizeof(double), off_q + (size_t)c * c * sizeof(double));
+    cudaFuncSetAttribute(k_jacobi_mp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi_mp<<<nnodes, threads, smem, st>>>(node_slot, (const double*)R, c, (double*)W,
+                                               (double*)sigma);
   }
 }
 
