@@ -141,9 +141,17 @@ hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* 
  * matrix, double blocks (HM_FP64); 1: float matrix, float blocks (HM_MIXED) on
  * the tensor cores (three-way BF16 split, FP32 accumulation drained into
  * compensated FP32 sums); 2: float matrix, double blocks with FP64 products and
- * sums (HM_A32); 3: as 1 on the CUDA cores (FP32 FMA, compensated sums).  The
- * matrix is NOT copied or owned: it must outlive the operator.  dtype 1 grows a
- * device workspace (a BF16 split of X) on first use of a larger block.  The returned operator's ctx is released by
+ * sums (HM_A32); 3: as 1 on the CUDA cores (FP32 FMA, compensated sums); 4: as 2
+ * on the tensor cores: per 64-wide K tile, rows of A and columns of X are cut
+ * into four 8-bit integer BF16 slices under a power-of-two scale, the products
+ * of each order are summed exactly in FP32 accumulators, orders above 5 are
+ * dropped (relative weight <= 2^-32), and the tile sums are added in FP32
+ * double-float; results whose magnitude exceeds the FP32 range are not
+ * representable (use 2).  The
+ * matrix is NOT copied or owned: it must outlive the operator.  dtypes 1 and 4
+ * grow a device workspace (the BF16 split of X) on first use of a larger block
+ * and need a 16-byte aligned A with lda % 4 == 0 and n >= 128 (TMA); other
+ * layouts run on the CUDA cores (dtype 3, resp. 2).  The returned operator's ctx is released by
  * hm_dense_operator_destroy.
  */
 hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,

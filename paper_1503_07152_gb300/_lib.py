@@ -157,17 +157,19 @@ class Operator:
 
 
 def hm_dense_operator_create(A: torch.Tensor, fp64_blocks: bool = False,
-                             cuda_cores: bool = False) -> Operator:
-    """Dense test operator over a row-major (n, lda) CUDA tensor.  float64 -> HM_FP64;
-    float32 -> HM_MIXED on the tensor-core engine (cuda_cores=True: the CUDA-core
-    engine), or HM_A32 (float matrix, double blocks) with fp64_blocks=True."""
+                             cuda_cores: bool = False, tensor_cores: bool | None = None) -> Operator:
+    """Dense test operator over a row-major (n, lda) CUDA tensor.  float64 -> HM_FP64.
+    float32 -> HM_MIXED (tensor-core engine by default; cuda_cores=True: CUDA-core
+    engine), or with fp64_blocks=True HM_A32 (float matrix, double blocks: exact FP64
+    products on the CUDA cores by default; tensor_cores=True: the exact-accumulation
+    split on the tensor cores)."""
     if A.dim() != 2 or A.stride(1) != 1 or not A.is_cuda:
         raise ValueError("A must be a row-major 2-D CUDA tensor")
     dtype = {torch.float64: 0, torch.float32: 1}[A.dtype]
     if fp64_blocks:
         if dtype != 1:
             raise ValueError("fp64_blocks needs a float32 matrix")
-        dtype = 2
+        dtype = 4 if tensor_cores else 2
     elif cuda_cores and dtype == 1:
         dtype = 3
     op = _Operator()

@@ -333,7 +333,19 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
       launch_dense_gemm<double>((const double*)d->A, d->lda, trans, n, w,
                                 (const double*)X + c0 * ldx, ldx, (double*)Y + c0 * ldy, ldy,
                                 d->flags, st);
-    else if (d->dtype == 2)
+    else if (d->dtype == 4 && gemm_tc_supported((const float*)d->A, d->lda, n)) {
+      const int64_t need = gemm_esg_work_bytes(n, w);
+      if (need > d->xs_bytes) {
+        if (d->xs) cudaFree(d->xs);
+        d->xs = nullptr;
+        d->xs_bytes = 0;
+        if (cudaMalloc(&d->xs, (size_t)need) != cudaSuccess) return 3;
+        d->xs_bytes = need;
+      }
+      if (launch_gemm_esg((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
+                          ldx, (double*)Y + c0 * ldy, ldy, d->xs, d->flags, d->err, st) != 0)
+        return 2;
+    } else if (d->dtype == 2 || d->dtype == 4)
       launch_dense_gemm_a32((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
                             ldx, (double*)Y + c0 * ldy, ldy, d->flags, st);
     else if (d->dtype == 1 && gemm_tc_supported((const float*)d->A, d->lda, n)) {
@@ -359,8 +371,8 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
 hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,
                                    hm_operator* out) {
   clear_error();
-  if (!A || !out || n < 1 || lda < n || dtype < 0 || dtype > 3) {
-    set_error("hm_dense_operator_create: need A, out, n >= 1, lda >= n, dtype 0..3");
+  if (!A || !out || n < 1 || lda < n || dtype < 0 || dtype > 4) {
+    set_error("hm_dense_operator_create: need A, out, n >= 1, lda >= n, dtype 0..4");
     return HM_EINVAL;
   }
   hm_dense_ctx* d = new hm_dense_ctx();

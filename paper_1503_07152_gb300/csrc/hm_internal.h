@@ -78,6 +78,12 @@ void launch_dense_gemm(const T* A, int64_t lda, int trans, int64_t n, int64_t nc
 size_t gemm_tc_smem_bytes();
 int64_t gemm_tc_xs_elems(int64_t n, int64_t ncols);
 bool gemm_tc_supported(const float* A, int64_t lda, int64_t n);
+// FP32 operator x FP64 block on the tensor cores with exact integer accumulation
+size_t gemm_esg_smem_bytes();
+int64_t gemm_esg_work_bytes(int64_t n, int64_t ncols);
+int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
+                    const double* X, int64_t ldx, double* Y, int64_t ldy, void* work,
+                    uint8_t* flags, int* err, cudaStream_t st);
 // 0: launched; 1: layout not supported (see gemm_tc_supported); 2: TMA map failed
 int launch_gemm_tc(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
                    const float* X, int64_t ldx, float* Y, int64_t ldy, void* xs_work,

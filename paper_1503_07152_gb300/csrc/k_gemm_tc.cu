@@ -33,14 +33,12 @@
 // in flight and leaves through the common exit path.  TMEM is released unless
 // the wait for the block's own MMAs itself timed out (freeing it under running
 // MMAs would be worse than leaking it).
-#include <cuda.h>
-#include <cudaTypedefs.h>
-#include <cuda_bf16.h>
-
-#include "hm_internal.h"
+#include "tc_util.cuh"
 
 namespace hm {
 namespace {
+
+using namespace tc;
 
 constexpr int TM = 128, TN = 64, TK = 64;
 constexpr int A_SLICE = TM * TK * 2;    // bytes of one BF16 slice tile of A
@@ -53,114 +51,6 @@ constexpr int LAYOUT_BYTES = 3 * RAW_BYTES + SSTAGES * (3 * A_SLICE + B_SLICE);
 static_assert(LAYOUT_BYTES == 2 * RAW_BYTES + SSTAGES * (3 * A_SLICE + 3 * B_SLICE), "layout");
 constexpr int NCONV = 128, NTHREADS = 320;
 constexpr uint32_t TMEM_COLS = 4 * TN;  // two (leading, correction) pairs
-constexpr long long kMaxPolls = 1ll << 25;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t n) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: false on timeout (or when another role already gave up)
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
-  for (long long i = 0; i < kMaxPolls; ++i) {
-    if (mbar_try(a, parity)) return true;
-    if ((i & 1023) == 1023 && *abort) return false;
-  }
-  *abort = 1;
-  return false;
-}
-// bounded wait that ignores the abort flag: used on the way out, to let the
-// block's own TMA copies land before its shared memory is given up
-__device__ __forceinline__ void mbar_wait_drain(uint32_t a, uint32_t parity) {
-  for (long long i = 0; i < kMaxPolls; ++i)
-    if (mbar_try(a, parity)) return;
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-// 2-D tiled TMA load into shared memory, completion counted on an mbarrier
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
-      "{%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart; start address and offsets in 16-byte units.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset between 8-row groups
-  d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: BF16 x BF16 -> FP32, A and B K-major, M = 128, N = 64.
-__device__ __forceinline__ uint32_t idesc_bf16_f32() {
-  uint32_t d = 0;
-  d |= 1u << 4;                   // D format FP32
-  d |= 1u << 7;                   // A format BF16
-  d |= 1u << 10;                  // B format BF16
-  d |= (uint32_t)(TN >> 3) << 17;  // N / 8
-  d |= (uint32_t)(TM >> 4) << 24;  // M / 16
-  return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t id,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(id), "r"(accum)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Three-way BF16 split of an FP32 value.
 __device__ __forceinline__ void split3(float a, __nv_bfloat16& h, __nv_bfloat16& m,
@@ -183,11 +73,6 @@ __device__ __forceinline__ void split3x2(float a, float b, uint32_t& h, uint32_t
   h = *reinterpret_cast<const uint32_t*>(&hh);
   m = *reinterpret_cast<const uint32_t*>(&mm);
   l = *reinterpret_cast<const uint32_t*>(&ll);
-}
-
-// byte offset of 16-byte chunk q (0..7) of row m in a 128-byte-swizzled K-major tile
-__device__ __forceinline__ uint32_t sw_off(int m, int q) {
-  return (uint32_t)(m * 128 + ((q ^ (m & 7)) << 4));
 }
 
 // X (FP32, column-major n x ncols) -> three BF16 slices, layout
@@ -491,8 +376,7 @@ bool gemm_tc_supported(const float* A, int64_t lda, int64_t n) {
          (((uintptr_t)A) & 15) == 0;
 }
 
-namespace {
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+PFN_cuTensorMapEncodeTiled_v12000 tc::encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -504,12 +388,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   }();
   return fn;
 }
-}  // namespace
 
 int launch_gemm_tc(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
                    const float* X, int64_t ldx, float* Y, int64_t ldy, void* xs_work,
                    uint8_t* flags, int* err, cudaStream_t st) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tc::encode_fn();
   if (!enc || !gemm_tc_supported(A, lda, n)) return 1;
   const int64_t kpad = ((n + TK - 1) / TK) * TK;
   const int nct = (int)((ncols + TN - 1) / TN);

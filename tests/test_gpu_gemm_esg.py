@@ -1,0 +1,93 @@
+"""The exact-accumulation split GEMM (FP32 operator x FP64 block on the tensor
+cores, dense operator dtype 4) against FP64 products, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import hbs as ohbs, hodlr as ohodlr
+from oracle.tree import build_tree
+
+pytestmark = pytest.mark.gpu
+hm = pytest.importorskip("paper_1503_07152_gb300")
+DEV = "cuda:0"
+
+
+def run(A32, X, trans, tensor_cores=True):
+    N, c = X.shape
+    op = hm.hm_dense_operator_create(torch.from_numpy(A32).to(DEV), fp64_blocks=True,
+                                     tensor_cores=tensor_cores)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.T)).to(DEV)
+    Y = torch.full((c, N), float("nan"), device=DEV, dtype=torch.float64)
+    hm.hm_dense_apply(op, trans, Xd, Y)
+    torch.cuda.synchronize()
+    return Y.cpu().numpy().T
+
+
+def rel_err(got, want):
+    scale = np.sqrt(np.sum(want ** 2, axis=0, keepdims=True) / want.shape[0])
+    return (np.abs(got - want) / scale).max()
+
+
+@pytest.mark.parametrize("N,c", [(1000, 37), (512, 64), (1536, 60), (776, 130)])
+@pytest.mark.parametrize("trans", [0, 1])
+@pytest.mark.parametrize("kind", ["bf16half", "orthonormal"])
+def test_esg_matches_fp64_product(N, c, trans, kind):
+    rng = np.random.default_rng(N + 3 * c + trans)
+    A = rng.standard_normal((N, N)).astype(np.float32)
+    A[rng.random((N, N)) < 0.05] *= 1e-3  # entries well below their row's maximum
+    if kind == "bf16half":
+        X = torch.from_numpy(rng.standard_normal((N, c))).to(torch.bfloat16).double().numpy()
+        X[: N // 2] = 0.0
+    else:
+        X, _ = np.linalg.qr(rng.standard_normal((N, c)))
+    got = run(A, X, trans)
+    want = (A.astype(np.float64).T if trans else A.astype(np.float64)) @ X
+    assert np.all(np.isfinite(got))
+    e = rel_err(got, want)
+    print(f"N={N} c={c} trans={trans} {kind}: {e:.2e}")
+    # orders s + t >= 6 are not formed: each product keeps ~2^-32 (max slice)^2
+    # relative error, ~1e-9 per product term and ~1e-8 at worst per entry
+    assert e < 3e-8
+
+
+def test_esg_zero_block_and_scales():
+    N = 640
+    rng = np.random.default_rng(5)
+    A = (rng.standard_normal((N, N)) * np.logspace(-20, 20, N)[:, None]).astype(np.float32)
+    X = np.zeros((N, 64))
+    assert np.all(run(A, X, 0) == 0.0)
+    X = rng.standard_normal((N, 64)) * 1e-3
+    for trans in (0, 1):
+        got = run(A, X, trans)
+        want = (A.astype(np.float64).T if trans else A.astype(np.float64)) @ X
+        # rows of very different scale: compare row by row
+        rel = np.abs(got - want) / np.maximum(np.abs(want).max(axis=1, keepdims=True), 1e-300)
+        assert rel.max() < 3e-8
+
+
+def test_esg_hbsid_compression_matches_oracle():
+    """A32 HBS-ID on the log kernel with the tensor-core products.  The products
+    carry ~2e-9 relative error instead of FP64 rounding, which moves the
+    near-threshold directions the way a different valid sample would: the
+    result meets the tolerance, its error matches the oracle's A32 reading, and
+    the two approximations differ by no more than their own truncation error.
+    (Element-wise A32 parity is tested on the exact CUDA-core products.)"""
+    N, m, r = 2048, 128, 40
+    A = W.log_kernel(N)
+    op = hm.hm_dense_operator_create(torch.from_numpy(A).to(DEV), fp64_blocks=True, tensor_cores=True)
+    h = hm.hm_compress_hbs(op, hm.Tree(N, m), prec=hm.HM_A32, hbs_id=1, tol=1e-7, r=r, seed=2)
+    out = torch.empty((N, N), device=DEV, dtype=torch.float64)
+    hm.hm_reconstruct_block(h, 0, N, 0, N, out)
+    torch.cuda.synchronize()
+    Ag = out.cpu().numpy().T
+    A64 = A.astype(np.float64)
+    o = ohbs.compress(ohodlr.dense_apply_fn(A64), build_tree(N, m), r=r, seed=2, mixed=True, floor=True)
+    Ao = ohbs.hbsid_dense(ohbs.to_hbsid(o, tol=1e-7))
+    nA = np.linalg.norm(A64)
+    e_gpu, e_par = np.linalg.norm(Ag - A64) / nA, np.linalg.norm(Ag - Ao) / nA
+    e_or = np.linalg.norm(Ao - A64) / nA
+    print(f"A32 tensor-core HBS-ID: err {e_gpu:.3e}, vs oracle {e_par:.3e}, oracle err {e_or:.3e}")
+    assert e_gpu < 1e-7
+    assert abs(e_gpu - e_or) < 0.1 * e_or
+    assert e_par < max(e_gpu, e_or)
