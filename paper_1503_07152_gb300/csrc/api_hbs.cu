@@ -23,7 +23,7 @@ using namespace hm;
 
 namespace hm {
 
-constexpr double kEpsScaleId = 0.01;  // ID threshold = 0.01 * tol * max(y | z on level 1)
+constexpr double kEpsScaleId = 0.005;  // ID threshold = 0.005 * tol * max(y | z on level 1)
 
 // Host-built list of small GEMMs launched in one kernel.
 template <typename T>
