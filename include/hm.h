@@ -142,12 +142,16 @@ hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* 
  * the tensor cores (three-way BF16 split, FP32 accumulation drained into
  * compensated FP32 sums); 2: float matrix, double blocks with FP64 products and
  * sums (HM_A32); 3: as 1 on the CUDA cores (FP32 FMA, compensated sums); 4: as 2
- * on the tensor cores: per 64-wide K tile, rows of A and columns of X are cut
- * into four 8-bit integer BF16 slices under a power-of-two scale, the products
- * of each order are summed exactly in FP32 accumulators, orders above 5 are
- * dropped (relative weight <= 2^-32), and the tile sums are added in FP32
+ * on the tensor cores: rows of A (whole rows) and columns of X (per 256-row
+ * window) are cut into four 8-bit integer BF16 slices under a power-of-two
+ * scale, the products of each order are summed exactly in FP32 accumulators
+ * over 256-wide K windows, orders above 5 are
+ * dropped (relative weight <= 2^-32), and the window sums are added in FP32
  * double-float; results whose magnitude exceeds the FP32 range are not
- * representable (use 2).  The
+ * representable (use 2).  The row and column scales of A are read once, at the
+ * first dtype-4 apply (one extra pass over A); if A's entries later grow past
+ * them, the affected outputs come back NaN (create a new operator after
+ * changing A).  The
  * matrix is NOT copied or owned: it must outlive the operator.  dtypes 1 and 4
  * grow a device workspace (the BF16 split of X) on first use of a larger block
  * and need a 16-byte aligned A with lda % 4 == 0 and n >= 128 (TMA); other

@@ -342,8 +342,13 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
         if (cudaMalloc(&d->xs, (size_t)need) != cudaSuccess) return 3;
         d->xs_bytes = need;
       }
+      if (!d->aexp) {
+        if (cudaMalloc(&d->aexp, sizeof(int) * 2 * (size_t)n) != cudaSuccess) return 3;
+        launch_esg_scales((const float*)d->A, d->lda, n, d->aexp, st);
+      }
       if (launch_gemm_esg((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
-                          ldx, (double*)Y + c0 * ldy, ldy, d->xs, d->flags, d->err, st) != 0)
+                          ldx, (double*)Y + c0 * ldy, ldy, d->xs, d->aexp, d->flags, d->err,
+                          st) != 0)
         return 2;
     } else if (d->dtype == 2 || d->dtype == 4)
       launch_dense_gemm_a32((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
@@ -401,6 +406,7 @@ void hm_dense_operator_destroy(hm_operator* op) {
   if (d->flags) cudaFree(d->flags);
   if (d->xs) cudaFree(d->xs);
   if (d->err) cudaFree(d->err);
+  if (d->aexp) cudaFree(d->aexp);
   delete d;
   op->ctx = nullptr;
   op->apply = nullptr;

@@ -81,9 +81,11 @@ bool gemm_tc_supported(const float* A, int64_t lda, int64_t n);
 // FP32 operator x FP64 block on the tensor cores with exact integer accumulation
 size_t gemm_esg_smem_bytes();
 int64_t gemm_esg_work_bytes(int64_t n, int64_t ncols);
+// row exponents then column exponents of A (2 n ints), taken once per operator
+void launch_esg_scales(const float* A, int64_t lda, int64_t n, int* aexp, cudaStream_t st);
 int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
                     const double* X, int64_t ldx, double* Y, int64_t ldy, void* work,
-                    uint8_t* flags, int* err, cudaStream_t st);
+                    const int* aexp, uint8_t* flags, int* err, cudaStream_t st);
 // 0: launched; 1: layout not supported (see gemm_tc_supported); 2: TMA map failed
 int launch_gemm_tc(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
                    const float* X, int64_t ldx, float* Y, int64_t ldy, void* xs_work,
@@ -254,6 +256,7 @@ struct hm_dense_ctx {
   void* xs = nullptr;        // split copy of X for the tensor-core engine
   int64_t xs_bytes = 0;
   int* err = nullptr;        // device flag raised by a kernel that gave up waiting
+  int* aexp = nullptr;       // dtype 4: row then column exponents of A (taken at first use)
 };
 
 struct hm_handle {

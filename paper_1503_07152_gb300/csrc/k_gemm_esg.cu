@@ -4,15 +4,16 @@
 // A Omega / A^* Omega of the compression figures, without FP64 arithmetic in
 // the contraction).
 //
-// Exact-accumulation split: inside one 64-wide K tile every row of op(A) and
-// every column of X is scaled by a power of two so that its largest entry lies
-// in [64, 128), and cut into four 8-bit integer slices (a = sum_s a_s 2^(-8(s-1))
-// up to the scale, |a_s| <= 128, each exact in BF16).  A BF16 x BF16 product of
-// slices is an integer below 2^14, and the products of one order d = s + t
-// (d = 2..5, the terms of relative weight >= 2^-24) summed over the tile stay
-// below 2^24, so the FP32 accumulators in TMEM hold them EXACTLY whatever the
-// tensor cores' rounding.  Orders above 5 (relative weight <= 2^-32) are not
-// formed.  Per tile and output element the drain adds
+// Exact-accumulation split: every row of op(A) (over all of K; the exponents
+// are recorded once per operator) and every column of X inside a window of
+// four 64-wide K tiles is scaled by a power of two so that its largest entry
+// lies in [64, 128), and cut into four 8-bit integer slices
+// (a = sum_s a_s 2^(-8(s-1)) up to the scale, |a_s| <= 128, each exact in BF16).
+// A BF16 x BF16 product of slices is an integer of magnitude <= 2^14, and the
+// products of one order d = s + t (d = 2..5, at most four of them) summed over
+// a window of 256 K values stay within 2^24, so the FP32 accumulators in TMEM
+// hold them EXACTLY whatever the tensor cores' rounding.  Orders above 5 are
+// not formed.  Per window and output element the drain adds
 //     2^(e_A + e_X - 14) (L + 2^-8 M + 2^-16 C + 2^-24 D)
 // (L, M, C, D: the exact sums of orders 2..5) into an FP32 double-float
 // (hi, lo): the leading term through an error-free TwoSum, the smaller ones
@@ -20,13 +21,15 @@
 //
 // Block: 128 rows of op(A) x 64 columns of X, eighteen warps:
 //   warp 17 (one lane): TMA loads of the FP32 tile of A into one raw stage;
-//   warps 0-7: move the raw tile to registers (releasing the stage), find the
-//     row scales, cut the slices into two operand stages (K-major, 128-byte
-//     swizzle); one lane loads the pre-cut X slices by TMA;
+//   warps 0-7: move the raw tile to registers (releasing the stage), scale and
+//     cut the slices into two operand stages (K-major, 128-byte swizzle); one
+//     lane loads the pre-cut X slices by TMA.  An entry that does not fit its
+//     recorded row scale (the operator changed after the scales were taken)
+//     aborts the block, whose outputs are then NaN;
 //   warp 8: allocates 512 TMEM columns; one lane issues the MMAs (up to ten
 //     products per 16-wide K step) into the four order accumulators;
-//   warps 9-16: drain (two warps per TMEM lane quarter, 32 columns each) and
-//     write Y.
+//   warps 9-16: drain once per window (two warps per TMEM lane quarter, 32
+//     columns each) and write Y.
 // All-zero K tiles of X are skipped.  Every mbarrier wait is bounded; on
 // timeout the block raises the error flag, writes NaN, lets its own TMA copies
 // land and leaves; TMEM is released unless the wait for its MMAs timed out.
@@ -48,7 +51,8 @@ constexpr int LAYOUT_BYTES = RAW_BYTES + SSTAGES * STAGE_BYTES;  // 224 KB
 constexpr int NCONV = 256, NDRAIN = 256, NTHREADS = 576;
 constexpr int W_MMA = 8, W_DRAIN0 = 9, W_TMA = 17;
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 4 orders x 64 columns
-constexpr int EXP_BIAS = 127;        // row exponents stored as uint8 e + 127, e in [-120, 128]
+constexpr int WIN_TILES = 4;         // K tiles per exact accumulation window
+constexpr int WIN_ROWS = WIN_TILES * TK;
 
 __device__ __forceinline__ float pow2f(int k) {  // 2^k for k in [-126, 127]
   return __int_as_float((k + 127) << 23);
@@ -78,27 +82,51 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// X (FP64, column-major n x ncols) -> per (K tile, column) exponents and four
+// Row exponents of A (e with max_j |A(i, j)| < 2^e, clamped to >= -120): one
+// warp per row.
+__global__ __launch_bounds__(256) void k_row_exp(const float* __restrict__ A, int64_t lda,
+                                                 int64_t n, int* __restrict__ e_row) {
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const float* a = A + row * lda;
+  float mx = 0.f;
+  for (int64_t j = lane; j < n; j += 32) mx = fmaxf(mx, fabsf(a[j]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) e_row[row] = max(exp_above(mx), -120);
+}
+
+// Column exponents of A: one thread per column, rows streamed.
+__global__ __launch_bounds__(256) void k_col_exp(const float* __restrict__ A, int64_t lda,
+                                                 int64_t n, int* __restrict__ e_col) {
+  const int64_t col = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (col >= n) return;
+  float mx = 0.f;
+#pragma unroll 8
+  for (int64_t i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(A[i * lda + col]));
+  e_col[col] = max(exp_above(mx), -120);
+}
+
+// X (FP64, column-major n x ncols) -> per (window, column) exponents and four
 // BF16 integer slices, layout Xs[((ct * 4 + t) * 64 + c) * kpad + k]; flags bit t
-// set when slice t of the (kt, ct) tile has a nonzero entry.
+// of (kt, ct) set when slice t of that K tile has a nonzero entry.  Block: one
+// window (four K tiles) x 64 columns; thread (c, q) covers K tile q of the window.
 __global__ __launch_bounds__(256) void k_split_x64(const double* __restrict__ X, int64_t ldx,
                                                    int64_t n, int64_t ncols, int64_t kpad,
                                                    int nct, __nv_bfloat16* __restrict__ Xs,
                                                    int* __restrict__ ex,
                                                    uint8_t* __restrict__ flags) {
-  const int kt = blockIdx.x, ct = blockIdx.y;
+  const int win = blockIdx.x, ct = blockIdx.y;
   const int tid = threadIdx.x;
-  const int c = tid >> 2, kq = tid & 3;  // column c, 16 rows k = kq*16 .. kq*16+15
+  const int c = tid >> 2, q = tid & 3;
   const int64_t col = (int64_t)ct * TN + c;
-  __shared__ int fl;
-  if (tid == 0) fl = 0;
-  double v[16];
+  const int64_t r0 = (int64_t)win * WIN_ROWS + q * TK;
+  __shared__ int fl[WIN_TILES];
+  if (tid < WIN_TILES) fl[tid] = 0;
   double mx = 0.0;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int64_t row = (int64_t)kt * TK + kq * 16 + i;
-    v[i] = (row < n && col < ncols) ? X[row + col * ldx] : 0.0;
-    mx = fmax(mx, fabs(v[i]));
+  for (int i = 0; i < TK; ++i) {
+    const int64_t row = r0 + i;
+    if (row < n && col < ncols) mx = fmax(mx, fabs(X[row + col * ldx]));
   }
   mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
   mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
@@ -107,25 +135,26 @@ __global__ __launch_bounds__(256) void k_split_x64(const double* __restrict__ X,
   __syncthreads();
   int bits = 0;
   const int64_t base = (int64_t)ct * NSL * TN;
+  if (r0 < kpad) {
+    for (int i = 0; i < TK; ++i) {
+      const int64_t row = r0 + i;
+      double r = (row < n && col < ncols) ? ldexp(X[row + col * ldx], 7 - e) : 0.0;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int64_t row = (int64_t)kt * TK + kq * 16 + i;
-    double r = ldexp(v[i], 7 - e);
-    double s[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      s[t] = rint(r);
-      r = (r - s[t]) * 256.0;
-      bits |= (s[t] != 0.0) ? (1 << t) : 0;
+      for (int t = 0; t < 4; ++t) {
+        const double st = rint(r);
+        r = (r - st) * 256.0;
+        bits |= (st != 0.0) ? (1 << t) : 0;
+        Xs[(base + t * TN + c) * kpad + row] = __float2bfloat16_rn((float)st);
+      }
     }
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      Xs[(base + t * TN + c) * kpad + row] = __float2bfloat16_rn((float)s[t]);
   }
-  if (bits) atomicOr(&fl, bits);
-  if (kq == 0) ex[((int64_t)kt * nct + ct) * TN + c] = e;
+  if (bits) atomicOr(&fl[q], bits);
+  if (q == 0) ex[((int64_t)win * nct + ct) * TN + c] = e;
   __syncthreads();
-  if (tid == 0) flags[(int64_t)kt * nct + ct] = (uint8_t)fl;
+  if (tid < WIN_TILES) {
+    const int64_t kt = (int64_t)win * WIN_TILES + tid;
+    if (kt * TK < kpad) flags[kt * nct + ct] = (uint8_t)fl[tid];
+  }
 }
 
 // instruction order of the products: every accumulator's first MMA (t = 1)
@@ -137,20 +166,18 @@ template <int TRANS>
 __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int64_t n,
     int64_t ncols, const uint8_t* __restrict__ flags, const int* __restrict__ ex,
-    double* __restrict__ Y, int64_t ldy, int* __restrict__ err) {
+    const int* __restrict__ e_rows, double* __restrict__ Y, int64_t ldy, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t raw_full, raw_empty, st_full[SSTAGES], x_full[SSTAGES],
-      st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final, exp_ready[4];
+      st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final;
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
-  // row exponents (+127) of the last four tiles; exp_ready[i] completes a phase
-  // when the cutters have written entry i (the drain reads it four tiles later
-  // at the latest, so a ring of four never overtakes it)
-  __shared__ uint8_t expa[4][TM];
+  __shared__ float srow[TM];  // 2^(7 - e), e the exponent of the row of op(A)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ct = blockIdx.x, mt = blockIdx.y, nct = gridDim.x;
   const int64_t m0 = (int64_t)mt * TM;
   const int nkt = (int)((n + TK - 1) / TK);
+  const int nwin = (nkt + WIN_TILES - 1) / WIN_TILES;
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sbase = smem_raw + (base - raw);
@@ -170,8 +197,11 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       mbar_init(smem_u32(&acc_empty[b]), NDRAIN);
     }
     mbar_init(smem_u32(&bar_final), 1);
-    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&exp_ready[i]), NCONV);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < TM) {
+    const int e = (m0 + tid < n) ? e_rows[m0 + tid] : 0;
+    srow[tid] = pow2f(7 - e);
   }
   if (warp == W_MMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -222,7 +252,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       if (!mbar_wait(smem_u32(&raw_full), it & 1, &abort_flag)) break;
       const unsigned char* rw = sbase;  // the raw stage sits at the aligned base
       unsigned char* sp = sbase + (st - base);
-      uint8_t* ea = expa[it & 3];
+      int bad = 0;
       if (!TRANS) {
         // raw [128 rows][64 k]; pass p: rows 16p .. 16p+15, 16 threads per row
         float4 v[8];
@@ -235,16 +265,14 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
           const int f = p * NCONV + tid, m = f >> 4, k4 = f & 15;
-          float mx = fmaxf(fmaxf(fabsf(v[p].x), fabsf(v[p].y)), fmaxf(fabsf(v[p].z), fabsf(v[p].w)));
-#pragma unroll
-          for (int o = 1; o < 16; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          const int e = max(exp_above(mx), -120);
-          if (k4 == 0) ea[m] = (uint8_t)(e + EXP_BIAS);
-          const float sc = pow2f(7 - e);
+          const float sc = srow[m];
           float a[4] = {v[p].x * sc, v[p].y * sc, v[p].z * sc, v[p].w * sc};
           float sl[4][4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) cut4(a[i], sl[0][i], sl[1][i], sl[2][i], sl[3][i]);
+          for (int i = 0; i < 4; ++i) {
+            bad |= !(fabsf(a[i]) < 128.f);
+            cut4(a[i], sl[0][i], sl[1][i], sl[2][i], sl[3][i]);
+          }
           const uint32_t off = sw_off(m, k4 >> 1) + (uint32_t)((k4 & 1) * 8);
 #pragma unroll
           for (int t = 0; t < NSL; ++t)
@@ -254,30 +282,21 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       } else {
         // raw [64 k][128 m]; thread (m, half) takes k = 32 half .. 32 half + 31
         const int m = tid & (TM - 1), h = tid >> 7;
-        // partial row maxima live in the last KB of this stage's slice 3 until the
-        // slices are written
-        float* pmax = reinterpret_cast<float*>(sp + 3 * A_SLICE + A_SLICE - 2 * TM * 4);
         float v[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i)
           v[i] = *reinterpret_cast<const float*>(rw + ((h * 32 + i) * TM + m) * 4);
         mbar_arrive(smem_u32(&raw_empty));
-        float mx = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[i]));
-        pmax[h * TM + m] = mx;
-        asm volatile("bar.sync 1, 256;" ::: "memory");
-        const float rmx = fmaxf(pmax[m], pmax[TM + m]);
-        asm volatile("bar.sync 1, 256;" ::: "memory");  // read before the slices overwrite it
-        const int e = max(exp_above(rmx), -120);
-        if (h == 0) ea[m] = (uint8_t)(e + EXP_BIAS);
-        const float sc = pow2f(7 - e);
+        const float sc = srow[m];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {  // 16-byte chunk q of this half: k = 32 h + 8 q ..
           float sl[4][8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            cut4(v[q * 8 + i] * sc, sl[0][i], sl[1][i], sl[2][i], sl[3][i]);
+          for (int i = 0; i < 8; ++i) {
+            const float a = v[q * 8 + i] * sc;
+            bad |= !(fabsf(a) < 128.f);
+            cut4(a, sl[0][i], sl[1][i], sl[2][i], sl[3][i]);
+          }
           const uint32_t off = sw_off(m, h * 4 + q);
 #pragma unroll
           for (int t = 0; t < NSL; ++t)
@@ -286,7 +305,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
                            pack_bf16(sl[t][4], sl[t][5]), pack_bf16(sl[t][6], sl[t][7]));
         }
       }
-      mbar_arrive(smem_u32(&exp_ready[it & 3]));
+      if (bad) abort_flag = 3;  // an entry outgrew its recorded row scale
       fence_proxy_async();
       mbar_arrive(smem_u32(&st_full[s]));
       ++it;
@@ -298,20 +317,30 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     // ---------------------------------------------------------- MMA issue
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16_f32();
-      int it = 0;
+      int it = 0, wc = 0, cur = -1;
+      uint32_t started = 0, dbase = 0;  // bit d: accumulator of order d + 2 written in this window
       bool ok = true;
       for (int kt = 0; kt < nkt && ok; ++kt) {
         const int fl = active(kt);
         if (!fl) continue;
-        const int b = it & 1, s = it % SSTAGES;
-        ok = mbar_wait(smem_u32(&acc_empty[b]), ((it >> 1) & 1) ^ 1, &abort_flag) &&
-             mbar_wait(smem_u32(&st_full[s]), (it / SSTAGES) & 1, &abort_flag) &&
+        const int w = kt / WIN_TILES;
+        if (w != cur) {
+          if (cur >= 0) {
+            mma_commit(smem_u32(&acc_full[wc & 1]));
+            ++wc;
+          }
+          cur = w;
+          ok = mbar_wait(smem_u32(&acc_empty[wc & 1]), ((wc >> 1) & 1) ^ 1, &abort_flag);
+          if (!ok) break;
+          dbase = tmem + (uint32_t)((wc & 1) * 4 * TN);
+          started = 0;
+        }
+        const int s = it % SSTAGES;
+        ok = mbar_wait(smem_u32(&st_full[s]), (it / SSTAGES) & 1, &abort_flag) &&
              mbar_wait(smem_u32(&x_full[s]), (it / SSTAGES) & 1, &abort_flag);
         if (!ok) break;
         tc_fence_after();
         const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
-        const uint32_t dbase = tmem + (uint32_t)(b * 4 * TN);
-        uint32_t started = 0;  // bit d: accumulator of order d + 2 already written
 #pragma unroll
         for (int kk = 0; kk < TK / 16; ++kk) {
 #pragma unroll
@@ -325,9 +354,9 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
           }
         }
         mma_commit(smem_u32(&st_empty[s]));
-        mma_commit(smem_u32(&acc_full[b]));
         ++it;
       }
+      if (ok && cur >= 0) mma_commit(smem_u32(&acc_full[wc & 1]));
       mma_commit(smem_u32(&bar_final));
       if (!mbar_wait(smem_u32(&bar_final), 0, &abort_flag)) abort_flag = 2;
     }
@@ -341,16 +370,16 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
 #pragma unroll
     for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
     const int64_t colbase = (int64_t)ct * TN + half * 32;
-    int it = 0;
-    for (int kt = 0; kt < nkt; ++kt) {
-      const int fl = active(kt);
-      if (!fl) continue;
-      const int b = it & 1;
-      const int exl = ex[((int64_t)kt * nct + ct) * TN + half * 32 + lane];  // column lane
-      if (!mbar_wait(smem_u32(&acc_full[b]), (it >> 1) & 1, &abort_flag)) break;
-      if (!mbar_wait(smem_u32(&exp_ready[it & 3]), (it >> 2) & 1, &abort_flag)) break;
+    const int ea = 7 - (((__float_as_int(srow[r]) >> 23) & 0xFF) - 127);  // row exponent
+    int wc = 0;
+    for (int w = 0; w < nwin; ++w) {
+      int any = 0;
+      for (int kt = w * WIN_TILES; kt < nkt && kt < (w + 1) * WIN_TILES; ++kt) any |= active(kt);
+      if (!any) continue;
+      const int b = wc & 1;
+      const int exl = ex[((int64_t)w * nct + ct) * TN + half * 32 + lane];  // column lane
+      if (!mbar_wait(smem_u32(&acc_full[b]), (wc >> 1) & 1, &abort_flag)) break;
       tc_fence_after();
-      const int ea = (int)expa[it & 3][r] - EXP_BIAS;
       const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 4 * TN + half * 32);
 #pragma unroll
       for (int g = 0; g < 2; ++g) {
@@ -386,7 +415,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&acc_empty[b]));
-      ++it;
+      ++wc;
     }
     const int64_t grow = m0 + r;
     const bool bad = abort_flag != 0;
@@ -416,7 +445,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
 size_t gemm_esg_smem_bytes() { return (size_t)LAYOUT_BYTES + 1024; }
 
 // bytes of the pre-cut X workspace: four BF16 slices per padded column tile,
-// then one int exponent per (K tile, column)
+// then one int exponent per (window, column) (sized per K tile, which is more)
 int64_t gemm_esg_work_bytes(int64_t n, int64_t ncols) {
   const int64_t kpad = ((n + TK - 1) / TK) * TK;
   const int64_t nct = (ncols + TN - 1) / TN;
@@ -424,9 +453,15 @@ int64_t gemm_esg_work_bytes(int64_t n, int64_t ncols) {
   return ((xs + 255) / 256) * 256 + (kpad / TK) * nct * TN * 4;
 }
 
+void launch_esg_scales(const float* A, int64_t lda, int64_t n, int* aexp, cudaStream_t st) {
+  count_launches(2);
+  k_row_exp<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(A, lda, n, aexp);
+  k_col_exp<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, n, aexp + n);
+}
+
 int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
                     const double* X, int64_t ldx, double* Y, int64_t ldy, void* work,
-                    uint8_t* flags, int* err, cudaStream_t st) {
+                    const int* aexp, uint8_t* flags, int* err, cudaStream_t st) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tc::encode_fn();
   if (!enc || !gemm_tc_supported(A, lda, n)) return 1;
   const int64_t kpad = ((n + TK - 1) / TK) * TK;
@@ -453,7 +488,9 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return 2;
   count_launches(2);
-  k_split_x64<<<dim3(nkt, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, ex, flags);
+  const int nwin = (nkt + WIN_TILES - 1) / WIN_TILES;
+  k_split_x64<<<dim3(nwin, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, ex, flags);
+  const int* e_rows = trans ? aexp + n : aexp;
   const size_t smem = gemm_esg_smem_bytes();
   static bool configured[2] = {false, false};
   dim3 grid((unsigned)nct, (unsigned)((n + TM - 1) / TM));
@@ -461,12 +498,14 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
     if (!configured[1])
       cudaFuncSetAttribute(k_gemm_esg<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured[1] = true;
-    k_gemm_esg<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, Y, ldy, err);
+    k_gemm_esg<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
+                                                err);
   } else {
     if (!configured[0])
       cudaFuncSetAttribute(k_gemm_esg<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     configured[0] = true;
-    k_gemm_esg<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, Y, ldy, err);
+    k_gemm_esg<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
+                                                err);
   }
   return 0;
 }

@@ -66,6 +66,24 @@ def test_esg_zero_block_and_scales():
         assert rel.max() < 3e-8
 
 
+def test_esg_operator_grown_after_first_use_gives_nan():
+    """The row scales are recorded at the first apply; entries that later outgrow
+    them must not give silently wrong products."""
+    N = 512
+    rng = np.random.default_rng(9)
+    At = torch.from_numpy(rng.standard_normal((N, N)).astype(np.float32)).to(DEV)
+    op = hm.hm_dense_operator_create(At, fp64_blocks=True, tensor_cores=True)
+    X = torch.from_numpy(rng.standard_normal((16, N))).to(DEV)
+    Y = torch.empty_like(X)
+    hm.hm_dense_apply(op, 0, X, Y)
+    torch.cuda.synchronize()
+    assert torch.isfinite(Y).all()
+    At.mul_(16.0)
+    hm.hm_dense_apply(op, 0, X, Y)
+    torch.cuda.synchronize()
+    assert torch.isnan(Y).all()
+
+
 def test_esg_hbsid_compression_matches_oracle():
     """A32 HBS-ID on the log kernel with the tensor-core products.  The products
     carry ~2e-9 relative error instead of FP64 rounding, which moves the
