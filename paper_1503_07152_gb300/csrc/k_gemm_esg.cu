@@ -16,8 +16,7 @@
 // not formed.  Per window and output element the drain adds
 //     2^(e_A + e_X - 14) (L + 2^-8 M + 2^-16 C + 2^-24 D)
 // (L, M, C, D: the exact sums of orders 2..5) into an FP32 double-float
-// (hi, lo): the leading term through an error-free TwoSum, the smaller ones
-// into lo.  Y = hi + lo in FP64.
+// (hi, lo), every term through an error-free TwoSum.  Y = hi + lo in FP64.
 //
 // Block: 128 rows of op(A) x 64 columns of X, eighteen warps:
 //   warp 17 (one lane): TMA loads of the FP32 tile of A into one raw stage;
@@ -389,29 +388,25 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
           const int e = ea + __shfl_sync(0xffffffffu, exl, g * 16 + j) - 14;
           sc[j] = (e >= -126 && e <= 127) ? pow2f(e) : ldexpf(1.f, e);
         }
-        // order 2: exact integer sums, added through TwoSum
-        tmem_ld16(tl + 0 * TN + g * 16, v);
+        // orders 2..5: exact integer sums times exact powers of two, each added
+        // into (hi, lo) through TwoSum, so that lo only gathers rounding residues
+        // (the lower orders are not small: their digits run up to 128 against a
+        // leading digit that may be much smaller)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int jj = g * 16 + j;
-          const float t = v[j] * sc[j];
-          const float sum = hi[jj] + t;
-          const float bp = sum - hi[jj];
-          lo[jj] += (hi[jj] - (sum - bp)) + (t - bp);
-          hi[jj] = sum;
+        for (int d = 0; d < 4; ++d) {
+          const float cd = d == 0 ? 1.f : (d == 1 ? 0.00390625f : (d == 2 ? 1.52587890625e-05f
+                                                                         : 5.9604644775390625e-08f));
+          tmem_ld16(tl + (uint32_t)(d * TN + g * 16), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int jj = g * 16 + j;
+            const float t = v[j] * (sc[j] * cd);
+            const float sum = hi[jj] + t;
+            const float bp = sum - hi[jj];
+            lo[jj] += (hi[jj] - (sum - bp)) + (t - bp);
+            hi[jj] = sum;
+          }
         }
-        // orders 3..5: 2^-8, 2^-16 and 2^-24 of the leading term, into lo
-        tmem_ld16(tl + 1 * TN + g * 16, v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) lo[g * 16 + j] = fmaf(v[j], sc[j] * 0.00390625f, lo[g * 16 + j]);
-        tmem_ld16(tl + 2 * TN + g * 16, v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          lo[g * 16 + j] = fmaf(v[j], sc[j] * 1.52587890625e-05f, lo[g * 16 + j]);
-        tmem_ld16(tl + 3 * TN + g * 16, v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          lo[g * 16 + j] = fmaf(v[j], sc[j] * 5.9604644775390625e-08f, lo[g * 16 + j]);
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&acc_empty[b]));
