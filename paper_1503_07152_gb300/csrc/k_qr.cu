@@ -194,7 +194,7 @@ __global__ __launch_bounds__(512) void k_jacobi_acc(const int32_t* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Am = reinterpret_cast<T*>(smem_raw);  // column j at Am + j * c
   T* Vm = Am + c * c;
-  __shared__ int rotated;
+  __shared__ int rotated, large;
   __shared__ double sv[128];
   __shared__ int order[128];
   const int node = blockIdx.x;
@@ -210,8 +210,9 @@ __global__ __launch_bounds__(512) void k_jacobi_acc(const int32_t* __restrict__ 
   // a pair is rotated while its correlation exceeds the rounding level of the
   // length-c dot products that measure it
   const T tol = (T)(Eps<T>::v * sqrt((double)c));
+  const T big2 = (T)(Eps<T>::v * sqrt((double)c));  // (sqrt(tol))^2
   for (int sweep = 0; sweep < 40; ++sweep) {
-    if (tid == 0) rotated = 0;
+    if (tid == 0) { rotated = 0; large = 0; }
     __syncthreads();
     for (int step = 0; step < cp - 1; ++step) {
       for (int pi = warp; pi < cp / 2; pi += nwarps) {
@@ -228,6 +229,9 @@ __global__ __launch_bounds__(512) void k_jacobi_acc(const int32_t* __restrict__ 
           alT = fma(x, x, alT); beT = fma(y, y, beT); gaT = fma(x, y, gaT);
         }
         const T al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
+        // a sweep whose largest correlation stays below sqrt(tol) leaves every
+        // pair below tol (quadratic convergence): no confirming sweep needed
+        if (lane == 0 && al > (T)0 && be > (T)0 && (ga / al) * (ga / be) > big2) large = 1;
         if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
           const T zeta = (be - al) / ((T)2 * ga);
           const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
@@ -249,7 +253,7 @@ __global__ __launch_bounds__(512) void k_jacobi_acc(const int32_t* __restrict__ 
       }
       __syncthreads();
     }
-    const int any = rotated;
+    const int any = rotated && large;
     __syncthreads();
     if (!any) break;
   }
@@ -318,7 +322,7 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
   const size_t off_q = (((size_t)c * c * sizeof(float)) + 15) & ~(size_t)15;
   float* X32 = reinterpret_cast<float*>(smem_raw + off_q);    // phase B
   double* Q = reinterpret_cast<double*>(smem_raw + off_q);    // phases C-F (X1 after D)
-  __shared__ int rotated;
+  __shared__ int rotated, large;
   __shared__ double sv[128];
   __shared__ double cn[128];
   __shared__ double hb[128];
@@ -415,8 +419,9 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
   const int cp = (c + 1) & ~1;
   {
     const float tol = (float)(Eps<float>::v * sqrt((double)c));
+    const float big2 = tol;  // (sqrt(tol))^2
     for (int sweep = 0; sweep < 40; ++sweep) {
-      if (tid == 0) rotated = 0;
+      if (tid == 0) { rotated = 0; large = 0; }
       __syncthreads();
       for (int step = 0; step < cp - 1; ++step) {
         for (int pi = warp; pi < cp / 2; pi += nwarps) {
@@ -432,6 +437,7 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
             alT = fmaf(x, x, alT); beT = fmaf(y, y, beT); gaT = fmaf(x, y, gaT);
           }
           const float al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
+          if (lane == 0 && al > 0.f && be > 0.f && (ga / al) * (ga / be) > big2) large = 1;
           if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
             const float zeta = (be - al) / (2.f * ga);
             const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
@@ -453,7 +459,7 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
         }
         __syncthreads();
       }
-      const int any = rotated;
+      const int any = rotated && large;
       __syncthreads();
       if (!any) break;
     }
@@ -515,8 +521,9 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
   // ---------------------------------------------------------------- E
   {
     const double tol = Eps<double>::v * sqrt((double)c);
+    const double tol2 = tol * tol, big2 = tol;  // squared thresholds
     for (int sweep = 0; sweep < 12; ++sweep) {
-      if (tid == 0) rotated = 0;
+      if (tid == 0) { rotated = 0; large = 0; }
       __syncthreads();
       for (int step = 0; step < cp - 1; ++step) {
         for (int pi = warp; pi < cp / 2; pi += nwarps) {
@@ -532,7 +539,9 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
             alT = fma(x, x, alT); beT = fma(y, y, beT); gaT = fma(x, y, gaT);
           }
           const double al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
-          if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const double g2 = ga * ga, ab = al * be;
+          if (lane == 0 && g2 > big2 * ab) large = 1;
+          if (ga != 0.0 && g2 > tol2 * ab) {
             const double zeta = (be - al) / (2.0 * ga);
             const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             const double tc = 1.0 / sqrt(1.0 + t * t), ts = tc * t;
@@ -546,7 +555,7 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
         }
         __syncthreads();
       }
-      const int any = rotated;
+      const int any = rotated && large;
       __syncthreads();
       if (!any) break;
     }
