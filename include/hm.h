@@ -204,6 +204,24 @@ hm_status hm_compress_hodlr(const hm_operator* op, const hm_tree* tree, const hm
 hm_status hm_compress_hbs(const hm_operator* op, const hm_tree* tree, const hm_opts* opts,
                           void* stream, hm_handle** out);
 
+/*
+ * Batched compression of nops independent operators of uneven size and rank
+ * (each the problem of Sec. 1 on its own): operator i with trees[i] and
+ * opts[i] is compressed exactly as hm_compress_hodlr (format HM_FORMAT_HODLR)
+ * or hm_compress_hbs (format HM_FORMAT_HBSID) would, and outs[i] receives its
+ * handle.  The operators run concurrently, each on an internal stream, from up
+ * to max_concurrency host threads (0: 8); their black boxes are therefore
+ * called from several threads at once and must allow it (the dense operators
+ * of this library do, one operator per entry).  The internal streams start
+ * after the work already queued on `stream`; all work is complete when the call
+ * returns.  Trees may be shared between operators.  On the first failure every
+ * handle of the call is destroyed, outs[] is set to NULL and the error names
+ * the operator.
+ */
+hm_status hm_compress_batched(int32_t nops, const hm_operator* ops, hm_tree* const* trees,
+                              const hm_opts* opts, int32_t format, int32_t max_concurrency,
+                              void* stream, hm_handle** outs);
+
 /* ---------------------------------------------------------- using it ----- */
 
 /*

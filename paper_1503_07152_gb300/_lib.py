@@ -54,6 +54,8 @@ _sig = {
     "hm_dense_apply": ([C.POINTER(_Operator), C.c_int, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
     "hm_compress_hodlr": ([C.POINTER(_Operator), _P, C.POINTER(Opts), _P, C.POINTER(_P)], C.c_int),
     "hm_compress_hbs": ([C.POINTER(_Operator), _P, C.POINTER(Opts), _P, C.POINTER(_P)], C.c_int),
+    "hm_compress_batched": ([C.c_int32, C.POINTER(_Operator), C.POINTER(_P), C.POINTER(Opts), C.c_int32,
+                             C.c_int32, _P, C.POINTER(_P)], C.c_int),
     "hm_apply": ([_P, C.c_int, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
     "hm_apply_host": ([_P, C.c_int, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
     "hm_reconstruct_block": ([_P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int64, _P], C.c_int),
@@ -235,6 +237,24 @@ def hm_compress_hbs(op: Operator, tree: Tree, stream=None, **kw) -> Handle:
     _check(lib.hm_compress_hbs(C.byref(op.op), tree.ptr, C.byref(o), C.c_void_p(_stream(stream)),
                                C.byref(h)), "hm_compress_hbs")
     return Handle(h, keep=(tree,))
+
+
+def hm_compress_batched(ops: list, trees: list, fmt: str = "hodlr", opts: list | None = None,
+                        max_concurrency: int = 0, stream=None) -> list:
+    """Compress independent operators in one call; opts: one dict of hm_compress_* keywords
+    per operator.  Returns one handle per operator."""
+    n = len(ops)
+    if len(trees) != n or (opts is not None and len(opts) != n):
+        raise ValueError("ops, trees and opts must have the same length")
+    opts = opts or [{} for _ in range(n)]
+    ops_arr = (_Operator * n)(*[o.op for o in ops])
+    trees_arr = (_P * n)(*[t.ptr for t in trees])
+    opts_arr = (Opts * n)(*[_opts(**kw) for kw in opts])
+    outs = (_P * n)()
+    fmt_id = {"hodlr": HM_FORMAT_HODLR, "hbsid": HM_FORMAT_HBSID}[fmt]
+    _check(lib.hm_compress_batched(n, ops_arr, trees_arr, opts_arr, fmt_id, max_concurrency,
+                                   C.c_void_p(_stream(stream)), outs), "hm_compress_batched")
+    return [Handle(C.c_void_p(outs[i]), keep=(trees[i], ops[i])) for i in range(n)]
 
 
 def hm_apply(h: Handle, trans: int, X: torch.Tensor, Y: torch.Tensor, stream=None) -> None:

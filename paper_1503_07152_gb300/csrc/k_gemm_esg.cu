@@ -32,6 +32,8 @@
 // All-zero K tiles of X are skipped.  Every mbarrier wait is bounded; on
 // timeout the block raises the error flag, writes NaN, lets its own TMA copies
 // land and leaves; TMEM is released unless the wait for its MMAs timed out.
+#include <atomic>
+
 #include "tc_util.cuh"
 
 namespace hm {
@@ -487,18 +489,20 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
   k_split_x64<<<dim3(nwin, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, ex, flags);
   const int* e_rows = trans ? aexp + n : aexp;
   const size_t smem = gemm_esg_smem_bytes();
-  static bool configured[2] = {false, false};
+  static std::atomic<bool> configured[2] = {{false}, {false}};  // several threads may launch
   dim3 grid((unsigned)nct, (unsigned)((n + TM - 1) / TM));
   if (trans) {
-    if (!configured[1])
+    if (!configured[1].load(std::memory_order_acquire)) {
       cudaFuncSetAttribute(k_gemm_esg<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured[1] = true;
+      configured[1].store(true, std::memory_order_release);
+    }
     k_gemm_esg<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
                                                 err);
   } else {
-    if (!configured[0])
+    if (!configured[0].load(std::memory_order_acquire)) {
       cudaFuncSetAttribute(k_gemm_esg<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured[0] = true;
+      configured[0].store(true, std::memory_order_release);
+    }
     k_gemm_esg<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
                                                 err);
   }

@@ -33,6 +33,8 @@
 // in flight and leaves through the common exit path.  TMEM is released unless
 // the wait for the block's own MMAs itself timed out (freeing it under running
 // MMAs would be worse than leaking it).
+#include <atomic>
+
 #include "tc_util.cuh"
 
 namespace hm {
@@ -420,18 +422,20 @@ int launch_gemm_tc(const float* A, int64_t lda, int trans, int64_t n, int64_t nc
   count_launches(2);
   k_split_x<<<dim3(nkt, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, flags);
   const size_t smem = gemm_tc_smem_bytes();
-  static bool configured[2] = {false, false};
+  static std::atomic<bool> configured[2] = {{false}, {false}};  // several threads may launch
   // column tiles of one row block run side by side, so A is read from HBM once
   dim3 grid((unsigned)nct, (unsigned)((n + TM - 1) / TM));
   if (trans) {
-    if (!configured[1])
+    if (!configured[1].load(std::memory_order_acquire)) {
       cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured[1] = true;
+      configured[1].store(true, std::memory_order_release);
+    }
     k_gemm_tc<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, Y, ldy, err);
   } else {
-    if (!configured[0])
+    if (!configured[0].load(std::memory_order_acquire)) {
       cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured[0] = true;
+      configured[0].store(true, std::memory_order_release);
+    }
     k_gemm_tc<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, Y, ldy, err);
   }
   return 0;

@@ -1,0 +1,77 @@
+"""hm_compress_batched: many independent operators of uneven size and rank in one
+call, through the C ABI, against one hm_compress_* call per operator (the same
+hot path) and against the operators themselves."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+hm = pytest.importorskip("paper_1503_07152_gb300")
+DEV = "cuda:0"
+
+
+def dense_of(h, N, dtype=torch.float64):
+    out = torch.empty((N, N), device=DEV, dtype=dtype)
+    hm.hm_reconstruct_block(h, 0, N, 0, N, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().T
+
+
+SPECS = [(640, 4), (1024, 10), (896, 6), (2048, 12), (1536, 8), (960, 5)]
+
+
+def _check_batched(fmt, mats, ops, trees, opts, err_bound, ranks=None):
+    hs = hm.hm_compress_batched(ops, trees, fmt, opts, max_concurrency=4)
+    assert len(hs) == len(mats)
+    for i, A in enumerate(mats):
+        N = A.shape[0]
+        one = (hm.hm_compress_hodlr if fmt == "hodlr" else hm.hm_compress_hbs)(ops[i], trees[i], **opts[i])
+        Ab, A1 = dense_of(hs[i], N), dense_of(one, N)
+        nA = np.linalg.norm(A)
+        assert np.linalg.norm(Ab - A1) / nA < 1e-14, i
+        assert np.linalg.norm(Ab - A) / nA < err_bound, i
+        if ranks is not None:
+            assert hs[i].info["max_rank"] == ranks[i]
+
+
+def test_batched_hodlr_matches_one_call_per_operator():
+    """Exact-rank synthetic HODLR operators of uneven size and rank (leaves of 64)."""
+    m = 64
+    mats, ops, trees, opts = [], [], [], []
+    for i, (N, k) in enumerate(SPECS):
+        A = W.dense_from_factors(W.synthetic_hodlr_factors(N, m, k, seed=1000 + i, shift=float(N)))
+        mats.append(A)
+        ops.append(hm.hm_dense_operator_create(torch.from_numpy(A).to(DEV)))
+        trees.append(hm.Tree(N, m))
+        opts.append(dict(k=k, p=10, seed=2000 + i, prec=hm.HM_FP64))
+    _check_batched("hodlr", mats, ops, trees, opts, 1e-10, ranks=[k for _, k in SPECS])
+
+
+def test_batched_hbsid_matches_one_call_per_operator():
+    """Log-kernel operators of uneven size, tolerance mode (HBS nested bases)."""
+    m = 128
+    mats, ops, trees, opts = [], [], [], []
+    for i, N in enumerate((1024, 1536, 2048, 1280)):
+        A = W.log_kernel(N).astype(np.float64)
+        mats.append(A)
+        ops.append(hm.hm_dense_operator_create(torch.from_numpy(A).to(DEV)))
+        trees.append(hm.Tree(N, m))
+        opts.append(dict(tol=1e-7, r=40, seed=2000 + i, prec=hm.HM_FP64))
+    _check_batched("hbsid", mats, ops, trees, opts, 1e-7)
+
+
+def test_batched_error_names_the_operator():
+    N, m = 512, 64
+    A = torch.eye(N, device=DEV, dtype=torch.float64)
+    good = hm.hm_dense_operator_create(A)
+    bad = hm.callback_operator(N, lambda *a: 7)
+    with pytest.raises(hm.HmError, match="operator 1") as e:
+        hm.hm_compress_batched([good, bad, good], [hm.Tree(N, m)] * 3, "hodlr",
+                               [dict(k=4, p=2, prec=hm.HM_FP64)] * 3)
+    assert e.value.status == 4
+
+
+def test_batched_empty():
+    assert hm.hm_compress_batched([], [], "hodlr") == []
