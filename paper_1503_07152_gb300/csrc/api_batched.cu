@@ -34,7 +34,7 @@ extern "C" hm_status hm_compress_batched(int32_t nops, const hm_operator* ops,
   HM_CUDA_TRY(cudaGetDevice(&dev));
   // upload every tree's tables here, once, so that the workers never race on a
   // tree shared between operators
-  for (int32_t i = 0; i < nops; ++i) HM_TRY(tree_device(trees[i]));
+  for (int32_t i = 0; i < nops; ++i) HM_TRY(tree_device(trees[i], (cudaStream_t)stream));
   // the workers' streams start after the work already queued on `stream`
   cudaEvent_t ready;
   HM_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));

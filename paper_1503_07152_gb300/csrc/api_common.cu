@@ -21,6 +21,23 @@ void clear_error() { g_err.clear(); }
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+void raise_smem_limit(const void* func, std::atomic<uint32_t>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 32) return;
+  const uint32_t bit = 1u << dev;
+  if (done.load(std::memory_order_acquire) & bit) return;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+          cudaSuccess ||
+      cudaFuncGetAttributes(&fa, func) != cudaSuccess)
+    return;  // the error stays set: the launch that follows reports it
+  // threads that race here all set the same value
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes) == cudaSuccess)
+    done.fetch_or(bit, std::memory_order_release);
+}
+
 hm_status check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -219,8 +236,13 @@ hm_status tree_plans(hm_tree* t) {
 }
 
 // Uploads the node table and the level plans on first use (needs a device).
-hm_status tree_device(hm_tree* t) {
+// The copies go on `st`, and the call waits for them: a plain cudaMemcpy from
+// pageable memory may return before its DMA lands, and it runs on the legacy
+// stream, which orders nothing on a non-blocking stream, so a kernel launched
+// next on such a stream could read a half-written plan.
+hm_status tree_device(hm_tree* t, cudaStream_t st) {
   if (t->d_start) return HM_OK;
+  std::vector<std::vector<unsigned char>> staged;  // alive until the copies end
   const int64_t nn = (int64_t)1 << (t->L + 1);
   HM_TRY(tree_plans(t));
   auto align = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -228,17 +250,20 @@ hm_status tree_device(hm_tree* t) {
   int64_t* dz = nullptr;
   HM_TRY(device_alloc((void**)&ds, nn * sizeof(int64_t)));
   HM_TRY(device_alloc((void**)&dz, nn * sizeof(int64_t)));
-  HM_CUDA_TRY(cudaMemcpy(ds, t->start.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice));
-  HM_CUDA_TRY(cudaMemcpy(dz, t->size.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice));
+  HM_CUDA_TRY(cudaMemcpyAsync(ds, t->start.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              st));
+  HM_CUDA_TRY(cudaMemcpyAsync(dz, t->size.data(), nn * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              st));
   t->d_size = dz;
   if (t->L >= 1) {
     const size_t b0 = align(t->fchunks.size() * sizeof(FactChunk));
     const size_t bytes = b0 + t->fbegin.size() * sizeof(int32_t);
     HM_TRY(device_alloc(&t->fdev, bytes));
-    HM_CUDA_TRY(cudaMemcpy(t->fdev, t->fchunks.data(), t->fchunks.size() * sizeof(FactChunk),
-                           cudaMemcpyHostToDevice));
-    HM_CUDA_TRY(cudaMemcpy((unsigned char*)t->fdev + b0, t->fbegin.data(),
-                           t->fbegin.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    HM_CUDA_TRY(cudaMemcpyAsync(t->fdev, t->fchunks.data(),
+                                t->fchunks.size() * sizeof(FactChunk), cudaMemcpyHostToDevice,
+                                st));
+    HM_CUDA_TRY(cudaMemcpyAsync((unsigned char*)t->fdev + b0, t->fbegin.data(),
+                                t->fbegin.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     t->d_fchunks = (const FactChunk*)t->fdev;
     t->d_fbegin = (const int32_t*)((unsigned char*)t->fdev + b0);
   }
@@ -255,7 +280,8 @@ hm_status tree_device(hm_tree* t) {
     }
     const size_t o_fs = bytes; bytes = align(bytes + lp.final_slot.size() * sizeof(int32_t));
     HM_TRY(device_alloc(&lp.dev, bytes));
-    std::vector<unsigned char> host(bytes, 0);
+    staged.emplace_back(bytes, 0);
+    std::vector<unsigned char>& host = staged.back();
     std::memcpy(host.data() + o_tn, lp.tn.data(), lp.tn.size() * sizeof(Chunk));
     std::memcpy(host.data() + o_tnb, lp.tn_begin.data(), lp.tn_begin.size() * sizeof(int32_t));
     std::memcpy(host.data() + o_nn, lp.nn.data(), lp.nn.size() * sizeof(Chunk));
@@ -263,7 +289,7 @@ hm_status tree_device(hm_tree* t) {
       std::memcpy(host.data() + o_rounds[i], lp.tsqr_rounds[i].data(),
                   lp.tsqr_rounds[i].size() * sizeof(TsqrTask));
     std::memcpy(host.data() + o_fs, lp.final_slot.data(), lp.final_slot.size() * sizeof(int32_t));
-    HM_CUDA_TRY(cudaMemcpy(lp.dev, host.data(), bytes, cudaMemcpyHostToDevice));
+    HM_CUDA_TRY(cudaMemcpyAsync(lp.dev, host.data(), bytes, cudaMemcpyHostToDevice, st));
     auto base = (unsigned char*)lp.dev;
     lp.d_tn = (const Chunk*)(base + o_tn);
     lp.d_tn_begin = (const int32_t*)(base + o_tnb);
@@ -273,6 +299,7 @@ hm_status tree_device(hm_tree* t) {
       lp.d_rounds.push_back((const TsqrTask*)(base + o_rounds[i]));
     lp.d_final_slot = (const int32_t*)(base + o_fs);
   }
+  HM_CUDA_TRY(cudaStreamSynchronize(st));
   t->d_start = ds;  // set last: marks the upload complete
   return HM_OK;
 }
@@ -388,7 +415,11 @@ hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_
   d->flags_bytes = dense_flags_bytes(n, 1024, dtype == 0);
   hm_status s = device_alloc((void**)&d->flags, (size_t)d->flags_bytes);
   if (s == HM_OK) s = device_alloc((void**)&d->err, sizeof(int));
-  if (s == HM_OK && cudaMemset(d->err, 0, sizeof(int)) != cudaSuccess) s = HM_ECUDA;
+  // the legacy-stream memset is waited for: the operator may next be applied on
+  // a non-blocking stream, which the legacy stream does not order
+  if (s == HM_OK && (cudaMemset(d->err, 0, sizeof(int)) != cudaSuccess ||
+                     cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess))
+    s = HM_ECUDA;
   if (s != HM_OK) {
     if (d->flags) cudaFree(d->flags);
     delete d;

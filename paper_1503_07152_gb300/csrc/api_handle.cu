@@ -212,7 +212,7 @@ hm_status hm_hodlr_factored_apply(const hm_tree* tree, int32_t k, const float* U
     return HM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  HM_TRY(tree_device(const_cast<hm_tree*>(tree)));
+  HM_TRY(tree_device(const_cast<hm_tree*>(tree), st));
   float* scratch = nullptr;
   const size_t sbytes = factored_scratch_bytes(tree, k);
   HM_CUDA_TRY(cudaMallocAsync((void**)&scratch, sbytes, st));
@@ -231,7 +231,7 @@ hm_status hm_hodlr_factored_adjoint(const hm_tree* tree, int32_t k, const float*
     return HM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  HM_TRY(tree_device(const_cast<hm_tree*>(tree)));
+  HM_TRY(tree_device(const_cast<hm_tree*>(tree), st));
   float* scratch = nullptr;
   const size_t sbytes = factored_scratch_bytes(tree, k);
   HM_CUDA_TRY(cudaMallocAsync((void**)&scratch, sbytes, st));
@@ -251,8 +251,8 @@ extern "C" hm_status hm_gaussian_test_matrix(const hm_tree* tree, int32_t level,
     set_error("hm_gaussian_test_matrix: need tree, X, 0 <= level < L, r >= 1, ldx >= n, prec");
     return HM_EINVAL;
   }
-  HM_TRY(tree_device(const_cast<hm_tree*>(tree)));
   cudaStream_t st = (cudaStream_t)stream;
+  HM_TRY(tree_device(const_cast<hm_tree*>(tree), st));
   if (prec != HM_MIXED)
     launch_gauss_fill<double>((double*)X, ldx, tree->n, r, level, seed, prec == HM_A32,
                               tree->d_start, tree->L, st);

@@ -453,7 +453,7 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
   h->r = r;
   hm_status s = tree_build(tree->n, tree->leaf, &h->tree);
   if (s == HM_OK) s = tree_plans(&h->tree);
-  if (s == HM_OK) s = tree_device(&h->tree);
+  if (s == HM_OK) s = tree_device(&h->tree, st);
   const int64_t N = tree->n;
   const int L = tree->L;
   const int nheap = 1 << (L + 1);

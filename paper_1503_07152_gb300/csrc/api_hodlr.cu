@@ -318,7 +318,7 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
   h->r = r;
   hm_status s = tree_build(tree->n, tree->leaf, &h->tree);
   if (s == HM_OK) s = tree_plans(&h->tree);
-  if (s == HM_OK) s = tree_device(&h->tree);
+  if (s == HM_OK) s = tree_device(&h->tree, st);
   const int64_t N = tree->n;
   if (s == HM_OK) s = device_alloc(&h->U, sizeof(T) * (size_t)tree->L * N * r);
   if (s == HM_OK) s = device_alloc(&h->V, sizeof(T) * (size_t)tree->L * N * r);

@@ -59,5 +59,5 @@ hm_status arena_alloc(void** block, F&& layout) {
 
 hm_status tree_build(int64_t n, int32_t leaf, hm_tree* t);
 hm_status tree_plans(hm_tree* t);
-hm_status tree_device(hm_tree* t);
+hm_status tree_device(hm_tree* t, cudaStream_t st);
 void tree_free(hm_tree* t);

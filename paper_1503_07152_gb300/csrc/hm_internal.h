@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -34,6 +35,13 @@ void clear_error();
 hm_status check_launch(const char* what);
 // Process-wide count of kernels launched by the library (all devices).
 void count_launches(int n);
+
+// Raises a kernel's dynamic shared-memory limit, once per device, to all that one
+// block may opt in to (`done` holds one bit per device).  The limit belongs to
+// the function and is shared by every host thread: set per launch to that
+// launch's own size, one thread could lower it between another thread's set and
+// that thread's launch.  Occupancy still follows the size each launch asks for.
+void raise_smem_limit(const void* func, std::atomic<uint32_t>& done);
 
 // Row chunk of one tree node: rows [r0, r1) of node `node`.
 struct Chunk {

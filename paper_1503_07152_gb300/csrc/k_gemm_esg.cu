@@ -489,20 +489,14 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
   k_split_x64<<<dim3(nwin, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, ex, flags);
   const int* e_rows = trans ? aexp + n : aexp;
   const size_t smem = gemm_esg_smem_bytes();
-  static std::atomic<bool> configured[2] = {{false}, {false}};  // several threads may launch
+  static std::atomic<uint32_t> done[2] = {{0}, {0}};
   dim3 grid((unsigned)nct, (unsigned)((n + TM - 1) / TM));
   if (trans) {
-    if (!configured[1].load(std::memory_order_acquire)) {
-      cudaFuncSetAttribute(k_gemm_esg<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      configured[1].store(true, std::memory_order_release);
-    }
+    raise_smem_limit((const void*)k_gemm_esg<1>, done[1]);
     k_gemm_esg<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
                                                 err);
   } else {
-    if (!configured[0].load(std::memory_order_acquire)) {
-      cudaFuncSetAttribute(k_gemm_esg<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      configured[0].store(true, std::memory_order_release);
-    }
+    raise_smem_limit((const void*)k_gemm_esg<0>, done[0]);
     k_gemm_esg<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
                                                 err);
   }

@@ -422,20 +422,14 @@ int launch_gemm_tc(const float* A, int64_t lda, int trans, int64_t n, int64_t nc
   count_launches(2);
   k_split_x<<<dim3(nkt, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, flags);
   const size_t smem = gemm_tc_smem_bytes();
-  static std::atomic<bool> configured[2] = {{false}, {false}};  // several threads may launch
+  static std::atomic<uint32_t> done[2] = {{0}, {0}};
   // column tiles of one row block run side by side, so A is read from HBM once
   dim3 grid((unsigned)nct, (unsigned)((n + TM - 1) / TM));
   if (trans) {
-    if (!configured[1].load(std::memory_order_acquire)) {
-      cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      configured[1].store(true, std::memory_order_release);
-    }
+    raise_smem_limit((const void*)k_gemm_tc<1>, done[1]);
     k_gemm_tc<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, Y, ldy, err);
   } else {
-    if (!configured[0].load(std::memory_order_acquire)) {
-      cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      configured[0].store(true, std::memory_order_release);
-    }
+    raise_smem_limit((const void*)k_gemm_tc<0>, done[0]);
     k_gemm_tc<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, Y, ldy, err);
   }
   return 0;

@@ -305,7 +305,8 @@ void launch_pivqr_id(int nnodes, const double* Yt, int r, int nc, double eps, in
                      int32_t* k, int32_t* J, double* T, cudaStream_t st) {
   count_launches(1);
   const size_t smem = sizeof(double) * ((size_t)r * nc + nc) + sizeof(int) * nc;
-  cudaFuncSetAttribute(k_pivqr_id, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<uint32_t> done{0};
+  raise_smem_limit((const void*)k_pivqr_id, done);
   k_pivqr_id<<<nnodes, 256, smem, st>>>(Yt, r, nc, eps, kcap, k, J, T);
 }
 

@@ -747,12 +747,13 @@ void launch_tsqr(const TsqrTask* tasks, int ntasks, int merge, const T* P, int64
   if (!merge) {
     const int ldm = kTsqrRows;
     const size_t smem = (size_t)ldm * c * sizeof(T);
-    cudaFuncSetAttribute(k_tsqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_tsqr<T>, done);
     k_tsqr<T><<<ntasks, 256, smem, st>>>(tasks, P, ldp, c, R, ldm);
   } else {
     const size_t smem = (size_t)c * (c + 1) * sizeof(T);
-    cudaFuncSetAttribute(k_tsqr_merge<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_tsqr_merge<T>, done);
     k_tsqr_merge<T><<<ntasks, 256, smem, st>>>(tasks, c, R);
   }
 }
@@ -766,12 +767,14 @@ void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W
   if (threads < 64) threads = 64;
   if (sizeof(T) == 4) {
     const size_t smem = (size_t)2 * c * c * sizeof(T);
-    cudaFuncSetAttribute(k_jacobi_acc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_jacobi_acc<T>, done);
     k_jacobi_acc<T><<<nnodes, threads, smem, st>>>(node_slot, R, c, W, sigma);
   } else {
     const size_t off_q = (((size_t)c * c * sizeof(float)) + 15) & ~(size_t)15;
     const size_t smem = std::max((size_t)c * c * sizeof(double), off_q + (size_t)c * c * sizeof(double));
-    cudaFuncSetAttribute(k_jacobi_mp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_jacobi_mp, done);
     k_jacobi_mp<<<nnodes, threads, smem, st>>>(node_slot, (const double*)R, c, (double*)W,
                                                (double*)sigma);
   }
@@ -791,7 +794,8 @@ void launch_cholqr(int nnodes, const T* G, int kcap, const int32_t* rank, T* T2,
                    const T* sigma, int c, T* M, int want_m, cudaStream_t st) {
   count_launches(1);
   const size_t smem = (size_t)2 * kcap * kcap * sizeof(T);
-  cudaFuncSetAttribute(k_cholqr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<uint32_t> done{0};
+  raise_smem_limit((const void*)k_cholqr<T>, done);
   k_cholqr<T><<<nnodes, 256, smem, st>>>(G, kcap, rank, T2, W, sigma, c, M, want_m);
 }
 

@@ -182,12 +182,8 @@ void launch_seg_tn(const Chunk* chunks, int nchunks, const int32_t* chunk_begin,
   count_launches(2);
   (void)node0;
   const size_t smem = 2 * TN_ROWS * (TN_MAX + 1) * sizeof(T);
-  static std::atomic<bool> configured{false};  // compressions may run in several threads
-  if (!configured.load(std::memory_order_acquire)) {
-    cudaFuncSetAttribute(k_seg_tn_partial<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    configured.store(true, std::memory_order_release);
-  }
+  static std::atomic<uint32_t> done{0};
+  raise_smem_limit((const void*)k_seg_tn_partial<T>, done);
   k_seg_tn_partial<T><<<nchunks, 256, smem, st>>>(chunks, A, lda, aoff_even, aoff_odd, ka, B,
                                                   ldb, boff_even, boff_odd, kb, partial);
   const int m = ka * kb;
@@ -202,11 +198,8 @@ void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int6
                    T beta, cudaStream_t st) {
   count_launches(1);
   const size_t smem = (size_t)(NN_MAX * NN_ROWS + NN_MAX * NN_MAX) * sizeof(T);
-  static std::atomic<bool> configured{false};
-  if (!configured.load(std::memory_order_acquire)) {
-    cudaFuncSetAttribute(k_seg_nn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured.store(true, std::memory_order_release);
-  }
+  static std::atomic<uint32_t> done{0};
+  raise_smem_limit((const void*)k_seg_nn<T>, done);
   k_seg_nn<T><<<nchunks, 256, smem, st>>>(chunks, node0, P, ldp, poff_even, poff_odd, kin, C,
                                           cstride, cld, cflip, Y, ldy, yoff_even, yoff_odd, kout,
                                           alpha, beta);

@@ -49,6 +49,36 @@ def test_batched_hodlr_matches_one_call_per_operator():
     _check_batched("hodlr", mats, ops, trees, opts, 1e-10, ranks=[k for _, k in SPECS])
 
 
+def test_batched_mixed_panel_widths_eight_threads():
+    """Sixteen operators whose panel widths k + p all differ, eight at a time: the
+    QR and Jacobi kernels size their shared memory by the panel width, so this is
+    where threads that configure one kernel for different widths would collide.
+    Every handle must equal the one-call result."""
+    m = 64
+    rng = np.random.default_rng(7)
+    mats, ops, trees, opts = [], [], [], []
+    for i in range(16):
+        N = int(64 * rng.integers(48, 97))
+        k = 6 + 2 * i
+        A = torch.from_numpy(W.dense_from_factors(
+            W.synthetic_hodlr_factors(N, m, k, seed=3000 + i, shift=float(N)))).to(DEV)
+        mats.append(A)
+        ops.append(hm.hm_dense_operator_create(A))
+        trees.append(hm.Tree(N, m))
+        opts.append(dict(k=k, p=10, seed=4000 + i, prec=hm.HM_FP64))
+    hs = hm.hm_compress_batched(ops, trees, "hodlr", opts, max_concurrency=8)
+    for i, A in enumerate(mats):
+        N = A.shape[0]
+        one = hm.hm_compress_hodlr(ops[i], trees[i], **opts[i])
+        Rb = torch.empty((N, N), device=DEV, dtype=torch.float64)
+        R1 = torch.empty_like(Rb)
+        hm.hm_reconstruct_block(hs[i], 0, N, 0, N, Rb)
+        hm.hm_reconstruct_block(one, 0, N, 0, N, R1)
+        nA = float(A.norm())
+        assert float((Rb - R1).norm()) / nA < 1e-14, i
+        assert float((Rb.T - A).norm()) / nA < 1e-10, i
+
+
 def test_batched_hbsid_matches_one_call_per_operator():
     """Log-kernel operators of uneven size, tolerance mode (HBS nested bases)."""
     m = 128
