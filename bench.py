@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-frob", action="store_true", help="skip the full Frobenius error check")
     ap.add_argument("--skip-mixed", action="store_true", help="skip the HM_MIXED comparison run")
+    ap.add_argument("--skip-batched", action="store_true", help="skip the batched many-operator run")
     return ap.parse_args()
 
 
@@ -181,6 +182,55 @@ def adjoint_bench(hm, torch, dev, steps, warmup):
     return {"value": round(1000.0 / ms, 2), "unit": "(forward + adjoint) applies/s",
             "ms_per_apply_pair": round(ms, 4), "config": {"n": n, "k": k, "leaf": m, "levels": L},
             "bytes_per_pair": moved, "achieved_GBs": round(moved / (ms * 1e-3) / 1e9, 1)}
+
+
+def batched_bench(hm, torch, dev, count=64):
+    """Batched workload: 64 independent synthetic HODLR operators (N log-uniform in [2048, 32768]
+    rounded to 64, k uniform in [8, 40], leaves of 64, r = k + 10), each formed densely in
+    FP32 on the device from its seeded factors, compressed by one hm_compress_batched call
+    in HM_A32 (FP64 pipeline, tensor-core products)."""
+    import numpy as np
+    import workloads as W
+    specs = W.batched_hodlr_specs(count)
+    mats, ops, trees, opts = [], [], [], []
+    for sp in specs:
+        N, k = sp["N"], sp["k"]
+        f = W.synthetic_hodlr_factors(N, 64, k, seed=sp["op_seed"], shift=float(N), dtype=np.float32)
+        A = torch.zeros((N, N), device=dev, dtype=torch.float32)
+        st, sz = f["start"], f["size"]
+        for j in range(1, f["L"] + 1):
+            Uj = torch.from_numpy(f["U"][j]).to(dev)
+            Vj = torch.from_numpy(f["V"][j]).to(dev)
+            for a in range(2 ** j, 2 ** (j + 1)):
+                b = a ^ 1
+                A[st[a]:st[a] + sz[a], st[b]:st[b] + sz[b]] = Uj[st[a]:st[a] + sz[a]] @ Vj[st[b]:st[b] + sz[b]].T
+        for i, t in enumerate(range(2 ** f["L"], 2 ** (f["L"] + 1))):
+            A[st[t]:st[t] + sz[t], st[t]:st[t] + sz[t]] = torch.from_numpy(f["D"][i]).to(dev)
+        mats.append(A)
+        ops.append(hm.hm_dense_operator_create(A, fp64_blocks=True, tensor_cores=True))
+        trees.append(hm.Tree(N, 64))
+        opts.append(dict(k=k, p=10, seed=sp["omega_seed"], prec=hm.HM_A32))
+    hs = hm.hm_compress_batched(ops, trees, "hodlr", opts)  # warm-up (operator scales, plans)
+    del hs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = hm.hm_compress_batched(ops, trees, "hodlr", opts)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    errs = []
+    g = torch.Generator(device=dev).manual_seed(12)
+    for A, h, op in zip(mats, hs, ops):
+        N = A.shape[0]
+        W4 = torch.randn((4, N), device=dev, dtype=torch.float64, generator=g)
+        Yt, Yc = torch.empty_like(W4), torch.empty_like(W4)
+        hm.hm_dense_apply(op, 0, W4, Yt)
+        hm.hm_apply(h, 0, W4, Yc)
+        errs.append(float(((Yt - Yc).norm(dim=1) / Yt.norm(dim=1)).max()))
+    ns = [sp["N"] for sp in specs]
+    return {"ops": count, "ms": round(ms, 2), "compressions_per_s": round(count / (ms * 1e-3), 2),
+            "n_range": [min(ns), max(ns)], "k_range": [min(sp["k"] for sp in specs), max(sp["k"] for sp in specs)],
+            "max_estimate_E": max(errs), "precision": "HM_A32",
+            "note": "host wall time of one hm_compress_batched call (all operators resident)"}
 
 
 def oracle_sample(n_sample: int):
@@ -346,6 +396,8 @@ def run_gpu(args):
                        "of one leaf block -> pinned host"}
         del A_host
     adj = None if args.skip_adjoint else adjoint_bench(hm, torch, dev, max(3, args.steps), 3)
+    del op
+    batched = None if args.skip_batched else batched_bench(hm, torch, dev)
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = cpu_baseline_line()
@@ -378,6 +430,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "e2e": e2e,
         "adjoint": adj,
+        "batched": batched,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
