@@ -132,6 +132,13 @@ def time_events(fn, reps, torch):
     return s.elapsed_time(e) / reps
 
 
+# DRAM traffic of one k_gemm_esg launch from an ncu capture of the same call (level-0
+# A Omega_2, 60 columns) at N = 16384: 541.9 MB read + 3.4 MB written for 552.6 MB of
+# algorithmic bytes.  Traffic grows with the units processed (rows x active K), so a
+# launch at another N moves this ratio times its own algorithmic bytes.
+ESG_TRAFFIC_PER_ALG_BYTE = (541.9e6 + 3.4e6) / (4.0 * 16384 * 8192 + 16.0 * 16384 * 60)
+
+
 def gemm_roofline(hm, torch, A, op, tree, n, peak_gbs, peak_kind):
     """Dominant HBM-bound kernel: one black-box call with a level-0 test matrix half
     (Y_1 = A Omega_2, Omega_2 nonzero on the right child's rows only), FP64 block."""
@@ -148,7 +155,9 @@ def gemm_roofline(hm, torch, A, op, tree, n, peak_gbs, peak_kind):
     alg_bytes = 4.0 * n * k_active + 8.0 * n * r * 2
     gbs = alg_bytes / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_gbs, "unit": "GB/s",
-            "frac": round(gbs / peak_gbs, 4), "traffic": None,
+            "frac": round(gbs / peak_gbs, 4), "traffic": round(alg_bytes * ESG_TRAFFIC_PER_ALG_BYTE),
+            "traffic_source": "ncu dram read+write of the same launch at N=16384, scaled by the "
+                              "algorithmic bytes (rows x active K)",
             "kernel": "k_gemm_esg (exact-accumulation split sampling GEMM, A Omega_2 at level 0)",
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": round(ms, 4),
             "peak_source": f"{peak_kind} HBM copy bandwidth",
