@@ -25,11 +25,21 @@
 //     lane loads the pre-cut X slices by TMA.  An entry that does not fit its
 //     recorded row scale (the operator changed after the scales were taken)
 //     aborts the block, whose outputs are then NaN;
-//   warp 8: allocates 512 TMEM columns; one lane issues the MMAs (up to ten
-//     products per 16-wide K step) into the four order accumulators;
+//   warp 8: allocates 512 TMEM columns; one lane issues the MMAs into the four
+//     order accumulators.  The four X slices of a stage lie one after the other
+//     as one 256-row K-major operand, so one MMA takes A slice s times X slices
+//     1 .. 5 - s (N = 64 (5 - s)) into the accumulators from column 64 (s - 1)
+//     on: product (s, t) lands in the accumulator of order s + t, and the ten
+//     products of orders 2..5 take four instructions per 16-wide K step.  MMAs
+//     are ordered back to back only for the same accumulator and shape, so the
+//     four K steps of one s form a chain, and before a chain of another shape
+//     the issuing lane waits for the previous one to complete (commit to a
+//     private mbarrier).  Successive tiles run the chains in alternate order,
+//     so that a tile's first chain has the shape of the previous tile's last;
 //   warps 9-16: drain once per window (two warps per TMEM lane quarter, 32
 //     columns each) and write Y.
-// All-zero K tiles of X are skipped.  Every mbarrier wait is bounded; on
+// All-zero K tiles of X are skipped; the four X slices of an active tile are
+// always loaded (a zero slice contributes zeros).  Every mbarrier wait is bounded; on
 // timeout the block raises the error flag, writes NaN, lets its own TMA copies
 // land and leaves; TMEM is released unless the wait for its MMAs timed out.
 #include <atomic>
@@ -158,11 +168,6 @@ __global__ __launch_bounds__(256) void k_split_x64(const double* __restrict__ X,
   }
 }
 
-// instruction order of the products: every accumulator's first MMA (t = 1)
-// comes first, so that it overwrites
-__constant__ int8_t kProdS[10] = {1, 2, 3, 4, 1, 2, 3, 1, 2, 1};
-__constant__ int8_t kProdT[10] = {1, 1, 1, 1, 2, 2, 2, 3, 3, 4};
-
 template <int TRANS>
 __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int64_t n,
@@ -170,7 +175,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     const int* __restrict__ e_rows, double* __restrict__ Y, int64_t ldy, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t raw_full, raw_empty, st_full[SSTAGES], x_full[SSTAGES],
-      st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final;
+      st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final, bar_chain;
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
   __shared__ float srow[TM];  // 2^(7 - e), e the exponent of the row of op(A)
@@ -198,6 +203,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       mbar_init(smem_u32(&acc_empty[b]), NDRAIN);
     }
     mbar_init(smem_u32(&bar_final), 1);
+    mbar_init(smem_u32(&bar_chain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < TM) {
@@ -243,11 +249,10 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag)) break;
       const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
       if (tid == 0) {
-        mbar_arrive_tx(smem_u32(&x_full[s]), (uint32_t)__popc(fl & 15) * B_SLICE);
+        mbar_arrive_tx(smem_u32(&x_full[s]), (uint32_t)(NSL * B_SLICE));
         for (int t = 0; t < NSL; ++t)
-          if (fl & (1 << t))
-            tma_load_2d(st + NSL * A_SLICE + t * B_SLICE, &tmX, kt * TK, (ct * NSL + t) * TN,
-                        smem_u32(&x_full[s]));
+          tma_load_2d(st + NSL * A_SLICE + t * B_SLICE, &tmX, kt * TK, (ct * NSL + t) * TN,
+                      smem_u32(&x_full[s]));
         xissued = it + 1;
       }
       if (!mbar_wait(smem_u32(&raw_full), it & 1, &abort_flag)) break;
@@ -262,6 +267,8 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
           const int f = p * NCONV + tid, m = f >> 4, k4 = f & 15;
           v[p] = *reinterpret_cast<const float4*>(rw + m * 256 + k4 * 16);
         }
+        // the next TMA write (async proxy) must follow these generic reads
+        fence_proxy_async();
         mbar_arrive(smem_u32(&raw_empty));  // the raw stage is free for the next tile
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
@@ -287,6 +294,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
 #pragma unroll
         for (int i = 0; i < 32; ++i)
           v[i] = *reinterpret_cast<const float*>(rw + ((h * 32 + i) * TM + m) * 4);
+        fence_proxy_async();
         mbar_arrive(smem_u32(&raw_empty));
         const float sc = srow[m];
 #pragma unroll
@@ -317,9 +325,8 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
   } else if (warp == W_MMA) {
     // ---------------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32();
-      int it = 0, wc = 0, cur = -1;
-      uint32_t started = 0, dbase = 0;  // bit d: accumulator of order d + 2 written in this window
+      int it = 0, wc = 0, cur = -1, pos = 0;  // pos: active tiles so far in the window
+      uint32_t started = 0, dbase = 0, chain_ph = 0;
       bool ok = true;
       for (int kt = 0; kt < nkt && ok; ++kt) {
         const int fl = active(kt);
@@ -335,6 +342,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
           if (!ok) break;
           dbase = tmem + (uint32_t)((wc & 1) * 4 * TN);
           started = 0;
+          pos = 0;
         }
         const int s = it % SSTAGES;
         ok = mbar_wait(smem_u32(&st_full[s]), (it / SSTAGES) & 1, &abort_flag) &&
@@ -342,18 +350,27 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
         if (!ok) break;
         tc_fence_after();
         const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
+        // chains s = 1..4 on even positions, 4..1 on odd ones: the window's first
+        // MMA (s = 1, N = 256) overwrites all four accumulators
+        for (int c = 0; c < NSL && ok; ++c) {
+          const int sa = (pos & 1) ? NSL - 1 - c : c;
+          if (c > 0) {  // the previous chain had another shape: let it complete
+            mma_commit(smem_u32(&bar_chain));
+            ok = mbar_wait(smem_u32(&bar_chain), chain_ph, &abort_flag);
+            chain_ph ^= 1;
+            if (!ok) break;
+          }
 #pragma unroll
-        for (int kk = 0; kk < TK / 16; ++kk) {
-#pragma unroll
-          for (int p = 0; p < 10; ++p) {
-            const int sa = kProdS[p] - 1, sb = kProdT[p] - 1, d = sa + sb;
-            if (!(fl & (1 << sb))) continue;
+          for (int kk = 0; kk < TK / 16; ++kk) {
             const uint64_t ad = sw128_desc(st + sa * A_SLICE + kk * 32);
-            const uint64_t bd = sw128_desc(st + NSL * A_SLICE + sb * B_SLICE + kk * 32);
-            mma_bf16(dbase + (uint32_t)(d * TN), ad, bd, idesc, (started >> d) & 1u);
-            started |= 1u << d;
+            const uint64_t bd = sw128_desc(st + NSL * A_SLICE + kk * 32);
+            // A slice sa + 1 times X slices 1 .. NSL - sa
+            mma_bf16(dbase + (uint32_t)(sa * TN), ad, bd, idesc_bf16_f32_n((NSL - sa) * TN),
+                     started);
+            started = 1;
           }
         }
+        ++pos;
         mma_commit(smem_u32(&st_empty[s]));
         ++it;
       }

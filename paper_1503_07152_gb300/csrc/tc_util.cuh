@@ -93,6 +93,11 @@ __device__ __forceinline__ uint32_t idesc_bf16_f32() {
   return d;
 }
 
+// The same with N = n (a multiple of 16 in [16, 256]).
+__device__ __forceinline__ uint32_t idesc_bf16_f32_n(int n) {
+  return (idesc_bf16_f32() & ~(0x3Fu << 17)) | ((uint32_t)(n >> 3) << 17);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t id,
                                          uint32_t accum) {
   asm volatile(
