@@ -344,13 +344,26 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
   }
   for (int j = tid; j < c; j += nthr) perm[j] = j;
   __syncthreads();
+  // squared norms of the trailing columns: computed once, downdated after every
+  // step (cn[k] -= M(j, k)^2) and recomputed where the downdate has cancelled
+  // below sqrt(eps) of the last computed value (hb[] keeps that value)
+  for (int k = warp; k < c; k += nwarps) {
+    const double* mk = M + k * c;
+    double s = 0;
+    for (int i = lane; i < c; i += 32) s = fma(mk[i], mk[i], s);
+    s = warp_sum(s);
+    if (lane == 0) { cn[k] = s; hb[k] = s; }
+  }
+  __syncthreads();
   for (int j = 0; j < c; ++j) {
     for (int k = j + warp; k < c; k += nwarps) {
-      const double* mk = M + k * c;
-      double s = 0;
-      for (int i = j + lane; i < c; i += 32) s = fma(mk[i], mk[i], s);
-      s = warp_sum(s);
-      if (lane == 0) cn[k] = s;
+      if (!(cn[k] > 1.4901161193847656e-08 * hb[k])) {
+        const double* mk = M + k * c;
+        double s = 0;
+        for (int i = j + lane; i < c; i += 32) s = fma(mk[i], mk[i], s);
+        s = warp_sum(s);
+        if (lane == 0) { cn[k] = s; hb[k] = s; }
+      }
     }
     __syncthreads();
     if (warp == 0) {
@@ -373,10 +386,21 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
         M[j * c + i] = M[p * c + i];
         M[p * c + i] = t;
       }
-      if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+      if (tid == 0) {
+        const int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+        double u = cn[j]; cn[j] = cn[p]; cn[p] = u;
+        u = hb[j]; hb[j] = hb[p]; hb[p] = u;
+      }
     }
     __syncthreads();
     double* mj = M + j * c;
+    if (warp == 0) {  // the reflector needs the pivot column's exact norm
+      double s = 0;
+      for (int i = j + lane; i < c; i += 32) s = fma(mj[i], mj[i], s);
+      s = warp_sum(s);
+      if (lane == 0) red_v[0] = s;
+    }
+    __syncthreads();
     if (tid == 0) {
       const double tot = red_v[0] > 0.0 ? red_v[0] : 0.0;
       const double x0 = mj[j];
@@ -402,6 +426,7 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
     }
     __syncthreads();
     if (tid == 0 && beta != 0.0) mj[j] = sh_alpha;
+    for (int k = j + 1 + tid; k < c; k += nthr) cn[k] -= M[k * c + j] * M[k * c + j];
     __syncthreads();
   }
   // X = R2^T, column-major, parked in the W slot
@@ -417,6 +442,15 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
   }
   __syncthreads();
   const int cp = (c + 1) & ~1;
+  // squared column norms of X32, updated by each rotation (hb[] as FP32 storage)
+  float* cn32 = reinterpret_cast<float*>(hb);
+  for (int j = warp; j < c; j += nwarps) {
+    float s2 = 0.f;
+    for (int i = lane; i < c; i += 32) s2 = fmaf(X32[j * c + i], X32[j * c + i], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) cn32[j] = s2;
+  }
+  __syncthreads();
   {
     const float tol = (float)(Eps<float>::v * sqrt((double)c));
     const float big2 = tol;  // (sqrt(tol))^2
@@ -431,12 +465,10 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
           if (p >= c || q >= c) continue;
           float* ap = X32 + p * c;
           float* aq = X32 + q * c;
-          float alT = 0, beT = 0, gaT = 0;
-          for (int i = lane; i < c; i += 32) {
-            const float x = ap[i], y = aq[i];
-            alT = fmaf(x, x, alT); beT = fmaf(y, y, beT); gaT = fmaf(x, y, gaT);
-          }
-          const float al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
+          float gaT = 0;
+          for (int i = lane; i < c; i += 32) gaT = fmaf(ap[i], aq[i], gaT);
+          const float ga = warp_sum(gaT);
+          const float al = cn32[p], be = cn32[q];
           if (lane == 0 && al > 0.f && be > 0.f && (ga / al) * (ga / be) > big2) large = 1;
           if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
             const float zeta = (be - al) / (2.f * ga);
@@ -454,7 +486,12 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
               vp[i] = tc * x - ts * y;
               vq[i] = ts * x + tc * y;
             }
-            if (lane == 0) rotated = 1;
+            if (lane == 0) {
+              const float cs2 = 2.f * tc * ts, c2 = tc * tc, s2 = ts * ts;
+              cn32[p] = fmaxf(fmaf(c2, al, fmaf(-cs2, ga, s2 * be)), 0.f);
+              cn32[q] = fmaxf(fmaf(s2, al, fmaf(cs2, ga, c2 * be)), 0.f);
+              rotated = 1;
+            }
           }
         }
         __syncthreads();
@@ -470,7 +507,9 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
     double* qj = Q + j * c;
     for (int i = tid; i < c; i += nthr) qj[i] = (double)V32[j * c + i];
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
+    // one classical Gram-Schmidt pass: V32 is orthogonal to FP32 precision, and
+    // CGS loses orthogonality in proportion to cond(V32)^2 ~ 1
+    {
       for (int i = warp; i < j; i += nwarps) {
         const double* qi = Q + i * c;
         double s = 0;
@@ -519,6 +558,22 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
   }
   __syncthreads();
   // ---------------------------------------------------------------- E
+  // The squared column norms live in cn[] and each rotation updates them from
+  // (al, be, ga), so a pair costs one dot product.  Starting from X1, whose
+  // columns are orthogonal to FP32 precision, nearly every angle is tiny: then
+  // t = tan(theta) = u - u^3 + ..., u = ga / (be - al), from an approximate FP64
+  // reciprocal refined by one Newton step (so that the confirming sweep finds
+  // nothing left to rotate), and
+  // cos = 1 - t^2/2 + 3t^4/8, sin = t cos, which is orthogonal to FP64
+  // rounding for |t| < 2^-10 (the dropped terms are below t^6).  Larger angles
+  // take the exact formulas.  The final norms are recomputed in F.
+  for (int j = warp; j < c; j += nwarps) {
+    double s2 = 0;
+    for (int i = lane; i < c; i += 32) s2 = fma(Q[j * c + i], Q[j * c + i], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) cn[j] = s2;
+  }
+  __syncthreads();
   {
     const double tol = Eps<double>::v * sqrt((double)c);
     const double tol2 = tol * tol, big2 = tol;  // squared thresholds
@@ -533,24 +588,42 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
           if (p >= c || q >= c) continue;
           double* ap = Q + p * c;
           double* aq = Q + q * c;
-          double alT = 0, beT = 0, gaT = 0;
-          for (int i = lane; i < c; i += 32) {
-            const double x = ap[i], y = aq[i];
-            alT = fma(x, x, alT); beT = fma(y, y, beT); gaT = fma(x, y, gaT);
-          }
-          const double al = warp_sum(alT), be = warp_sum(beT), ga = warp_sum(gaT);
+          double gaT = 0;
+          for (int i = lane; i < c; i += 32) gaT = fma(ap[i], aq[i], gaT);
+          const double ga = warp_sum(gaT);
+          const double al = cn[p], be = cn[q];
           const double g2 = ga * ga, ab = al * be;
           if (lane == 0 && g2 > big2 * ab) large = 1;
           if (ga != 0.0 && g2 > tol2 * ab) {
-            const double zeta = (be - al) / (2.0 * ga);
-            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double tc = 1.0 / sqrt(1.0 + t * t), ts = tc * t;
+            const double d = be - al;
+            double tc, ts;
+            if (fabs(ga) < 0.00048828125 * fabs(d) && fabs(d) > 1e-290) {  // |t| < 2^-11
+              double r;
+              asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+              r = fma(r, fma(-d, r, 1.0), r);      // one Newton step: FP64-accurate
+              const double u = ga * r;             // 1 / (2 zeta)
+              const double t = fma(-u * u, u, u);  // tan(theta) = u - u^3 + ...
+              const double t2 = t * t;
+              tc = fma(t2, fma(t2, 0.375, -0.5), 1.0);
+              ts = tc * t;
+            } else {
+              const double zeta = d / (2.0 * ga);
+              const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+              tc = 1.0 / sqrt(1.0 + t * t);
+              ts = tc * t;
+            }
             for (int i = lane; i < c; i += 32) {
               const double x = ap[i], y = aq[i];
               ap[i] = tc * x - ts * y;
               aq[i] = ts * x + tc * y;
             }
-            if (lane == 0) rotated = 1;
+            if (lane == 0) {
+              // norms after the rotation (whatever the angle's accuracy)
+              const double cs2 = 2.0 * tc * ts, c2 = tc * tc, s2 = ts * ts;
+              cn[p] = fma(c2, al, fma(-cs2, ga, s2 * be));
+              cn[q] = fma(s2, al, fma(cs2, ga, c2 * be));
+              rotated = 1;
+            }
           }
         }
         __syncthreads();
