@@ -337,6 +337,7 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
   double* Wn = W + (int64_t)node * c * c;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int nthr = blockDim.x;
+  const int pg = tid >> 3, gl = tid & 7;  // sweeps: pair slot (8 lanes each), lane in it
   // ---------------------------------------------------------------- A
   for (int idx = tid; idx < c * c; idx += nthr) {
     const int rr = idx / c, col = idx % c;
@@ -458,35 +459,42 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
       if (tid == 0) { rotated = 0; large = 0; }
       __syncthreads();
       for (int step = 0; step < cp - 1; ++step) {
-        for (int pi = warp; pi < cp / 2; pi += nwarps) {
-          const int a = pi, b = cp - 1 - pi;
-          const int p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
-          const int q = ((b - 1 + step) % (cp - 1)) + 1;
-          if (p >= c || q >= c) continue;
-          float* ap = X32 + p * c;
-          float* aq = X32 + q * c;
-          float gaT = 0;
-          for (int i = lane; i < c; i += 32) gaT = fmaf(ap[i], aq[i], gaT);
-          const float ga = warp_sum(gaT);
+        // all pairs of the step at once, one aligned 8-lane group per pair
+        int p = c, q = c;
+        if (pg < cp / 2) {
+          const int a = pg, b = cp - 1 - pg;
+          p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
+          q = ((b - 1 + step) % (cp - 1)) + 1;
+        }
+        const bool valid = p < c && q < c;
+        float* ap = X32 + (valid ? p : 0) * c;
+        float* aq = X32 + (valid ? q : 0) * c;
+        float ga = 0;
+        if (valid)
+          for (int i = gl; i < c; i += 8) ga = fmaf(ap[i], aq[i], ga);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 4);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+        if (valid) {
           const float al = cn32[p], be = cn32[q];
-          if (lane == 0 && al > 0.f && be > 0.f && (ga / al) * (ga / be) > big2) large = 1;
+          if (gl == 0 && al > 0.f && be > 0.f && (ga / al) * (ga / be) > big2) large = 1;
           if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
             const float zeta = (be - al) / (2.f * ga);
             const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
             const float tc = 1.f / sqrtf(1.f + t * t), ts = tc * t;
-            for (int i = lane; i < c; i += 32) {
+            for (int i = gl; i < c; i += 8) {
               const float x = ap[i], y = aq[i];
               ap[i] = tc * x - ts * y;
               aq[i] = ts * x + tc * y;
             }
             float* vp = V32 + p * c;
             float* vq = V32 + q * c;
-            for (int i = lane; i < c; i += 32) {
+            for (int i = gl; i < c; i += 8) {
               const float x = vp[i], y = vq[i];
               vp[i] = tc * x - ts * y;
               vq[i] = ts * x + tc * y;
             }
-            if (lane == 0) {
+            if (gl == 0) {
               const float cs2 = 2.f * tc * ts, c2 = tc * tc, s2 = ts * ts;
               cn32[p] = fmaxf(fmaf(c2, al, fmaf(-cs2, ga, s2 * be)), 0.f);
               cn32[q] = fmaxf(fmaf(s2, al, fmaf(cs2, ga, c2 * be)), 0.f);
@@ -581,19 +589,25 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
       if (tid == 0) { rotated = 0; large = 0; }
       __syncthreads();
       for (int step = 0; step < cp - 1; ++step) {
-        for (int pi = warp; pi < cp / 2; pi += nwarps) {
-          const int a = pi, b = cp - 1 - pi;
-          const int p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
-          const int q = ((b - 1 + step) % (cp - 1)) + 1;
-          if (p >= c || q >= c) continue;
-          double* ap = Q + p * c;
-          double* aq = Q + q * c;
-          double gaT = 0;
-          for (int i = lane; i < c; i += 32) gaT = fma(ap[i], aq[i], gaT);
-          const double ga = warp_sum(gaT);
+        int p = c, q = c;  // one aligned 8-lane group per pair, as in B
+        if (pg < cp / 2) {
+          const int a = pg, b = cp - 1 - pg;
+          p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
+          q = ((b - 1 + step) % (cp - 1)) + 1;
+        }
+        const bool valid = p < c && q < c;
+        double* ap = Q + (valid ? p : 0) * c;
+        double* aq = Q + (valid ? q : 0) * c;
+        double ga = 0;
+        if (valid)
+          for (int i = gl; i < c; i += 8) ga = fma(ap[i], aq[i], ga);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 4);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+        if (valid) {
           const double al = cn[p], be = cn[q];
           const double g2 = ga * ga, ab = al * be;
-          if (lane == 0 && g2 > big2 * ab) large = 1;
+          if (gl == 0 && g2 > big2 * ab) large = 1;
           if (ga != 0.0 && g2 > tol2 * ab) {
             const double d = be - al;
             double tc, ts;
@@ -612,12 +626,12 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
               tc = 1.0 / sqrt(1.0 + t * t);
               ts = tc * t;
             }
-            for (int i = lane; i < c; i += 32) {
+            for (int i = gl; i < c; i += 8) {
               const double x = ap[i], y = aq[i];
               ap[i] = tc * x - ts * y;
               aq[i] = ts * x + tc * y;
             }
-            if (lane == 0) {
+            if (gl == 0) {
               // norms after the rotation (whatever the angle's accuracy)
               const double cs2 = 2.0 * tc * ts, c2 = tc * tc, s2 = ts * ts;
               cn[p] = fma(c2, al, fma(-cs2, ga, s2 * be));
@@ -848,7 +862,8 @@ void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W
     const size_t smem = std::max((size_t)c * c * sizeof(double), off_q + (size_t)c * c * sizeof(double));
     static std::atomic<uint32_t> done{0};
     raise_smem_limit((const void*)k_jacobi_mp, done);
-    k_jacobi_mp<<<nnodes, threads, smem, st>>>(node_slot, (const double*)R, c, (double*)W,
+    // the sweeps give each of the (c + 1) / 2 <= 64 pairs of a step 8 lanes
+    k_jacobi_mp<<<nnodes, 512, smem, st>>>(node_slot, (const double*)R, c, (double*)W,
                                                (double*)sigma);
   }
 }
