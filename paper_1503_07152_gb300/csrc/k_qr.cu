@@ -332,6 +332,7 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
   __shared__ double red_v[16];
   __shared__ int red_i[16];
   __shared__ double sh_alpha, sh_beta;
+  __shared__ double psum[4][128];  // C: partial projections
   const int node = blockIdx.x;
   const double* Rs = R + (int64_t)node_slot[node] * c * c;
   double* Wn = W + (int64_t)node * c * c;
@@ -416,13 +417,20 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
     __syncthreads();
     const double beta = sh_beta;
     if (beta != 0.0) {
-      for (int k = j + 1 + warp; k < c; k += nwarps) {
-        double* mk = M + k * c;
+      for (int k0 = j + 1; k0 < c; k0 += 64) {  // one 8-lane group per trailing column
+        const int k = k0 + pg;
+        const bool on = k < c;
+        double* mk = M + (on ? k : j) * c;
         double dot = 0;
-        for (int i = j + lane; i < c; i += 32) dot = fma(mj[i], mk[i], dot);
-        dot = warp_sum(dot);
-        const double f = beta * dot;
-        for (int i = j + lane; i < c; i += 32) mk[i] = fma(-f, mj[i], mk[i]);
+        if (on)
+          for (int i = j + gl; i < c; i += 8) dot = fma(mj[i], mk[i], dot);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 4);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+        if (on) {
+          const double f = beta * dot;
+          for (int i = j + gl; i < c; i += 8) mk[i] = fma(-f, mj[i], mk[i]);
+        }
       }
     }
     __syncthreads();
@@ -518,19 +526,30 @@ __global__ __launch_bounds__(512) void k_jacobi_mp(const int32_t* __restrict__ n
     // one classical Gram-Schmidt pass: V32 is orthogonal to FP32 precision, and
     // CGS loses orthogonality in proportion to cond(V32)^2 ~ 1
     {
-      for (int i = warp; i < j; i += nwarps) {
-        const double* qi = Q + i * c;
+      for (int i0 = 0; i0 < j; i0 += 64) {  // one 8-lane group per earlier column
+        const int i = i0 + pg;
+        const bool on = i < j;
+        const double* qi = Q + (on ? i : 0) * c;
         double s = 0;
-        for (int e = lane; e < c; e += 32) s = fma(qi[e], qj[e], s);
-        s = warp_sum(s);
-        if (lane == 0) hb[i] = s;
+        if (on)
+          for (int e = gl; e < c; e += 8) s = fma(qi[e], qj[e], s);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        if (on && gl == 0) hb[i] = s;
       }
       __syncthreads();
-      for (int e = tid; e < c; e += nthr) {
+      {  // q_j -= sum_i hb[i] Q_i in four partial sums over quarters of i
+        const int e = tid & 127, part = tid >> 7;
+        const int i0 = (j * part) >> 2, i1 = (j * (part + 1)) >> 2;
         double s = 0;
-        for (int i = 0; i < j; ++i) s = fma(hb[i], Q[i * c + e], s);
-        qj[e] -= s;
+        if (e < c)
+          for (int i = i0; i < i1; ++i) s = fma(hb[i], Q[i * c + e], s);
+        psum[part][e] = s;
       }
+      __syncthreads();
+      for (int e = tid; e < c; e += nthr)
+        qj[e] -= (psum[0][e] + psum[1][e]) + (psum[2][e] + psum[3][e]);
       __syncthreads();
     }
     if (warp == 0) {
