@@ -76,7 +76,7 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
   const int64_t N = c.N;
   const int r = c.r;
   const size_t lim = 220 * 1024;
-  if (pc > 128 || (size_t)kTsqrRows * pc * sizeof(T) > lim ||
+  if (pc > 128 || (size_t)(kTsqrRows + 8) * pc * sizeof(T) > lim ||
       (size_t)pc * (pc + 1) * sizeof(T) > lim ||
       (size_t)pc * pc * sizeof(float) + (size_t)pc * pc * (sizeof(T) == 4 ? 4 : 8) + 16 > lim) {
     set_error("panel too wide for the shared-memory QR in this precision");

@@ -96,13 +96,21 @@ __global__ __launch_bounds__(256) void k_tsqr(const TsqrTask* __restrict__ tasks
     __syncthreads();
     const T beta = sh_beta;
     if (beta != (T)0) {
-      for (int k = j + 1 + warp; k < c; k += 8) {
-        T* mk = M + k * ldm;
+      // one aligned 8-lane group per trailing column, 32 columns per round
+      for (int k0 = j + 1; k0 < c; k0 += 32) {
+        const int k = k0 + (tid >> 3), gl = tid & 7;
+        const bool on = k < c;
+        T* mk = M + (on ? k : j) * ldm;
         T dot = 0;
-        for (int i = j + lane; i < m; i += 32) dot = fma(mj[i], mk[i], dot);
-        dot = warp_sum(dot);
-        const T f = beta * dot;
-        for (int i = j + lane; i < m; i += 32) mk[i] = fma(-f, mj[i], mk[i]);
+        if (on)
+          for (int i = j + gl; i < m; i += 8) dot = fma(mj[i], mk[i], dot);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 4);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+        if (on) {
+          const T f = beta * dot;
+          for (int i = j + gl; i < m; i += 8) mk[i] = fma(-f, mj[i], mk[i]);
+        }
       }
     }
     __syncthreads();
@@ -162,15 +170,24 @@ __global__ __launch_bounds__(256) void k_tsqr_merge(const TsqrTask* __restrict__
     __syncthreads();
     const T beta = sh_beta, v0 = sh_v0;
     if (beta != (T)0) {
-      for (int k = j + 1 + warp; k < c; k += 8) {
-        T* ak = A + k * (k + 1) / 2;
-        T* bk = B + k * (k + 1) / 2;
+      // one aligned 8-lane group per trailing column, 32 columns per round
+      for (int k0 = j + 1; k0 < c; k0 += 32) {
+        const int k = k0 + (tid >> 3), gl = tid & 7;
+        const bool on = k < c;
+        const int kk = on ? k : j;
+        T* ak = A + kk * (kk + 1) / 2;
+        T* bk = B + kk * (kk + 1) / 2;
         T dot = 0;
-        for (int i = lane; i <= j; i += 32) dot = fma(bj[i], bk[i], dot);
-        dot = warp_sum(dot) + v0 * ak[j];
-        const T f = beta * dot;
-        for (int i = lane; i <= j; i += 32) bk[i] = fma(-f, bj[i], bk[i]);
-        if (lane == 0) ak[j] = fma(-f, v0, ak[j]);
+        if (on)
+          for (int i = gl; i <= j; i += 8) dot = fma(bj[i], bk[i], dot);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 4);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+        if (on) {
+          const T f = beta * (dot + v0 * ak[j]);
+          for (int i = gl; i <= j; i += 8) bk[i] = fma(-f, bj[i], bk[i]);
+          if (gl == 0) ak[j] = fma(-f, v0, ak[j]);
+        }
       }
     }
     __syncthreads();
@@ -851,7 +868,9 @@ void launch_tsqr(const TsqrTask* tasks, int ntasks, int merge, const T* P, int64
                  T* R, cudaStream_t st) {
   count_launches(1);
   if (!merge) {
-    const int ldm = kTsqrRows;
+    // columns 136 entries apart: the four 8-lane groups of a warp then fall on
+    // two bank halves (the two wavefronts a 256-byte access takes anyway)
+    const int ldm = kTsqrRows + 8;
     const size_t smem = (size_t)ldm * c * sizeof(T);
     static std::atomic<uint32_t> done{0};
     raise_smem_limit((const void*)k_tsqr<T>, done);
