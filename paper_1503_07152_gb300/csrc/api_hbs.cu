@@ -72,6 +72,7 @@ struct HbsState {
   double* partial = nullptr;
   GemmItem* items = nullptr;
   size_t items_cap = 0;
+  bool df = false;  // double-float Gram products (HM_A32)
 };
 
 // S(:, 0:ncols) += sign * A^(m) X  (transpose: (A^(m))^T), column blocks of <= 128.
@@ -93,7 +94,7 @@ hm_status hbs_partial_apply(HbsState<T>& s, int m, const T* X, int64_t ldx, T* S
     T* qh = s.qhat;
     T* uh = s.uhat;
     launch_seg_tn<T>(pm.d_tn, pm.n_tn, pm.d_tn_begin, pm.nnodes, pm.node0, Vout, s.N, 0, 0, r,
-                     X + cb * ldx, ldx, 0, 0, w, s.partial, qh + pm.node0 * rw, st);
+                     X + cb * ldx, ldx, 0, 0, w, s.partial, qh + pm.node0 * rw, st, s.df);
     for (int lev = m - 1; lev >= 1; --lev) {
       for (int tau = 1 << lev; tau < (2 << lev); ++tau)
         it.add(Sout + (2 * tau) * rr, r, 1, qh + (2 * tau) * rw, r, 0, qh + tau * rw, r, r, w, r);
@@ -149,7 +150,7 @@ hm_status compress_hbs_t(Ctx<T>& c, HbsState<T>& s, T* D) {
     launch_node_copy<T, T>(lp.nnodes, lp.node0, c.sig, pc, pc, s.y, r, r, r, 1, 0, c.st);
     if (level > 0)  // U_tau short halves: U_a^T U_tau(J_a, :)
       launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Unext, N, 0, 0, r,
-                       s.Ucur, N, 0, 0, r, c.partial, s.UsH + lp.node0 * rr, c.st);
+                       s.Ucur, N, 0, 0, r, c.partial, s.UsH + lp.node0 * rr, c.st, s.df);
     launch_scatter_probe<T>(Unext, N, c.X, N, N, r, lv, c.tree->d_start, L, c.st);
     HM_TRY(box(c, 1, c.X, c.S, r));
     HM_TRY(box(c, 1, c.X + N * r, c.S + N * r, r));
@@ -165,7 +166,7 @@ hm_status compress_hbs_t(Ctx<T>& c, HbsState<T>& s, T* D) {
                            c.st);
     if (level > 0)
       launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Vnext, N, 0, 0, r,
-                       s.Vcur, N, 0, 0, r, c.partial, s.VsH + lp.node0 * rr, c.st);
+                       s.Vcur, N, 0, 0, r, c.partial, s.VsH + lp.node0 * rr, c.st, s.df);
     std::swap(s.Ucur, Unext);
     std::swap(s.Vcur, Vnext);
     c.launches += 12;
@@ -470,6 +471,7 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
   c.tol = o->tol;
   c.bf16 = (o->prec != HM_FP64);
   HbsState<T> hs;
+  hs.df = sizeof(T) == 8 && o->prec == HM_A32;
   hs.N = N;
   hs.r = r;
   hs.L = L;

@@ -58,7 +58,7 @@ hm_status hodlr_peel(Ctx<T>& c, const T* U, const T* V, int level, const T* X, T
     for (int64_t cb = 0; cb < ncols; cb += 128) {
       const int w = (int)std::min<int64_t>(128, ncols - cb);
       launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Proj, N, 0, 0, r,
-                       X + cb * N, N, 0, 0, w, c.partial, c.coef, c.st);
+                       X + cb * N, N, 0, 0, w, c.partial, c.coef, c.st, c.bf16 && sizeof(T) == 8);
       launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Expd, N, 0, 0, r, c.coef, (int64_t)r * w, r,
                        1, S + cb * N, N, 0, 0, w, (T)sign, (T)1, c.st);
       c.launches += 3;
@@ -100,7 +100,7 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
   launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, P, N, 0, 0, pc, c.T1, (int64_t)pc * r, pc, 0, Q,
                    N, 0, 0, r, (T)1, (T)0, c.st);
   launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Q, N, 0, 0, r, Q, N, 0,
-                   0, r, c.partial, c.G, c.st);
+                   0, r, c.partial, c.G, c.st, c.bf16 && sizeof(T) == 8);
   launch_cholqr<T>(lp.nnodes, c.G, r, rank_lv, c.T2, c.W, c.sig, pc, c.M, want_m ? 1 : 0, c.st);
   launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Q, N, 0, 0, r, c.T2, (int64_t)r * r, r, 0, Q, N, 0,
                    0, r, (T)1, (T)0, c.st);

@@ -105,12 +105,14 @@ void launch_dense_gemm_a32(const float* A, int64_t lda, int trans, int64_t n, in
 
 // Gram-like reduction: for every chunk, partial = A(rows, 0:ka)^T B(rows, 0:kb)
 // (column offsets chosen by node parity), then per node sum of its chunks:
-// out[node - node0] (ka x kb, column-major, ld ka) = sum.
+// out[node - node0] (ka x kb, column-major, ld ka) = sum.  df (T = double only): the
+// products in double-float arithmetic on the FP32 pipe, inputs cut to 48 bits
+// (~1e-14 relative; for HM_A32, whose operator is FP32, not for HM_FP64).
 template <typename T>
 void launch_seg_tn(const Chunk* chunks, int nchunks, const int32_t* chunk_begin, int nnodes,
                    int node0, const T* A, int64_t lda, int aoff_even, int aoff_odd, int ka,
                    const T* B, int64_t ldb, int boff_even, int boff_odd, int kb,
-                   double* partial, T* out, cudaStream_t st);
+                   double* partial, T* out, cudaStream_t st, bool df = false);
 
 // Expansion: Y(rows, yoff(node) + 0:kout) = alpha * P(rows, poff(node) + 0:kin) *
 // C[(node ^ cflip) - node0] + beta * Y(...).  C is kin x kout column-major with

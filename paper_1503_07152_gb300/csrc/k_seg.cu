@@ -87,6 +87,88 @@ __global__ __launch_bounds__(256) void k_seg_tn_partial(
     }
 }
 
+// The FP64 form of the partial products in double-float arithmetic on the FP32
+// pipe (GB300's FP64 pipe runs at a small fraction of the FP32 rate).  Each FP64
+// input is cut once, when staged, into x = hi + lo (two floats, 48 significant
+// bits); a product a b is formed as hi_a hi_b exactly (TwoProduct by FMA) plus
+// the cross terms, and summed per output in a double-float (s_hi, s_lo) through
+// TwoSum.  The partial of a chunk (<= 256 rows) is accurate to ~1e-14 relative.
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+__global__ __launch_bounds__(256) void k_seg_tn_partial_df(
+    const Chunk* __restrict__ chunks, const double* __restrict__ A, int64_t lda, int aoff_e,
+    int aoff_o, int ka, const double* __restrict__ B, int64_t ldb, int boff_e, int boff_o,
+    int kb, double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LD = TN_MAX + 1;
+  float* Ah = reinterpret_cast<float*>(smem_raw);  // [TN_ROWS][LD] each
+  float* Al = Ah + TN_ROWS * LD;
+  float* Bh = Al + TN_ROWS * LD;
+  float* Bl = Bh + TN_ROWS * LD;
+  const Chunk ch = chunks[blockIdx.x];
+  const int aoff = (ch.node & 1) ? aoff_o : aoff_e;
+  const int boff = (ch.node & 1) ? boff_o : boff_e;
+  const int tid = threadIdx.x;
+  const int ti = tid >> 4, tj = tid & 15;
+  float sh[8][8], sl[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
+  for (int64_t r0 = ch.r0; r0 < ch.r1; r0 += TN_ROWS) {
+    const int rows = (int)((ch.r1 - r0) < TN_ROWS ? (ch.r1 - r0) : TN_ROWS);
+    for (int idx = tid; idx < TN_ROWS * TN_MAX; idx += 256) {
+      const int rr = idx % TN_ROWS, c = idx / TN_ROWS;
+      float h, l;
+      split_df((rr < rows && c < ka) ? A[r0 + rr + (int64_t)(aoff + c) * lda] : 0.0, h, l);
+      Ah[rr * LD + c] = h;
+      Al[rr * LD + c] = l;
+      split_df((rr < rows && c < kb) ? B[r0 + rr + (int64_t)(boff + c) * ldb] : 0.0, h, l);
+      Bh[rr * LD + c] = h;
+      Bl[rr * LD + c] = l;
+    }
+    __syncthreads();
+    for (int rr = 0; rr < rows; ++rr) {
+      float ah[8], al[8], bh[8], bl[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        ah[i] = Ah[rr * LD + ti * 8 + i];
+        al[i] = Al[rr * LD + ti * 8 + i];
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        bh[j] = Bh[rr * LD + tj * 8 + j];
+        bl[j] = Bl[rr * LD + tj * 8 + j];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float p = ah[i] * bh[j];
+          const float e = fmaf(ah[i], bh[j], -p);               // hi hi - p, exact
+          const float t = fmaf(ah[i], bl[j], fmaf(al[i], bh[j], e));
+          const float s = sh[i][j] + p;                          // TwoSum(sh, p)
+          const float z = s - sh[i][j];
+          const float err = (sh[i][j] - (s - z)) + (p - z);
+          sh[i][j] = s;
+          sl[i][j] += err + t;
+        }
+    }
+    __syncthreads();
+  }
+  double* out = partial + (int64_t)blockIdx.x * ka * kb;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int ii = ti * 8 + i, jj = tj * 8 + j;
+      if (ii < ka && jj < kb) out[ii + jj * ka] = (double)sh[i][j] + (double)sl[i][j];
+    }
+}
+
 // out[node] = sum of the node's chunk partials, in chunk order (deterministic).
 template <typename T>
 __global__ void k_seg_tn_reduce(const double* __restrict__ partial,
@@ -178,14 +260,22 @@ template <typename T>
 void launch_seg_tn(const Chunk* chunks, int nchunks, const int32_t* chunk_begin, int nnodes,
                    int node0, const T* A, int64_t lda, int aoff_even, int aoff_odd, int ka,
                    const T* B, int64_t ldb, int boff_even, int boff_odd, int kb, double* partial,
-                   T* out, cudaStream_t st) {
+                   T* out, cudaStream_t st, bool df) {
   count_launches(2);
   (void)node0;
-  const size_t smem = 2 * TN_ROWS * (TN_MAX + 1) * sizeof(T);
-  static std::atomic<uint32_t> done{0};
-  raise_smem_limit((const void*)k_seg_tn_partial<T>, done);
-  k_seg_tn_partial<T><<<nchunks, 256, smem, st>>>(chunks, A, lda, aoff_even, aoff_odd, ka, B,
-                                                  ldb, boff_even, boff_odd, kb, partial);
+  const size_t smem = 2 * TN_ROWS * (TN_MAX + 1) * sizeof(T);  // the df form: 4 float planes
+  if (sizeof(T) == 8 && df) {
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_seg_tn_partial_df, done);
+    k_seg_tn_partial_df<<<nchunks, 256, smem, st>>>(chunks, (const double*)A, lda, aoff_even,
+                                                    aoff_odd, ka, (const double*)B, ldb,
+                                                    boff_even, boff_odd, kb, partial);
+  } else {
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_seg_tn_partial<T>, done);
+    k_seg_tn_partial<T><<<nchunks, 256, smem, st>>>(chunks, A, lda, aoff_even, aoff_odd, ka, B,
+                                                    ldb, boff_even, boff_odd, kb, partial);
+  }
   const int m = ka * kb;
   dim3 grid((unsigned)((m + 255) / 256), (unsigned)nnodes);
   k_seg_tn_reduce<T><<<grid, 256, 0, st>>>(partial, chunk_begin, ka, kb, out);
@@ -207,10 +297,10 @@ void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int6
 
 template void launch_seg_tn<float>(const Chunk*, int, const int32_t*, int, int, const float*,
                                    int64_t, int, int, int, const float*, int64_t, int, int, int,
-                                   double*, float*, cudaStream_t);
+                                   double*, float*, cudaStream_t, bool);
 template void launch_seg_tn<double>(const Chunk*, int, const int32_t*, int, int, const double*,
                                     int64_t, int, int, int, const double*, int64_t, int, int,
-                                    int, double*, double*, cudaStream_t);
+                                    int, double*, double*, cudaStream_t, bool);
 template void launch_seg_nn<float>(const Chunk*, int, int, const float*, int64_t, int, int, int,
                                    const float*, int64_t, int, int, float*, int64_t, int, int,
                                    int, float, float, cudaStream_t);
