@@ -23,7 +23,7 @@ using namespace hm;
 
 namespace hm {
 
-constexpr double kEpsScaleId = 0.005;  // ID threshold = 0.005 * tol * max(y | z on level 1)
+constexpr double kEpsScaleId = 0.004;  // ID threshold = 0.004 * tol * max(y | z on level 1)
 
 // Host-built list of small GEMMs launched in one kernel.
 template <typename T>
@@ -118,7 +118,7 @@ hm_status hbs_partial_apply(HbsState<T>& s, int m, const T* X, int64_t ldx, T* S
       }
     }
     launch_seg_nn<T>(pm.d_nn, pm.n_nn, pm.node0, Uin, s.N, 0, 0, r, uh + pm.node0 * rw, rw, r, 0,
-                     S + cb * lds, lds, 0, 0, w, sign, (T)1, st);
+                     S + cb * lds, lds, 0, 0, w, sign, (T)1, st, s.df);
   }
   return check_launch("hbs partial apply");
 }

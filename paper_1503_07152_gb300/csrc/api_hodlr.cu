@@ -60,7 +60,7 @@ hm_status hodlr_peel(Ctx<T>& c, const T* U, const T* V, int level, const T* X, T
       launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Proj, N, 0, 0, r,
                        X + cb * N, N, 0, 0, w, c.partial, c.coef, c.st, c.bf16 && sizeof(T) == 8);
       launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Expd, N, 0, 0, r, c.coef, (int64_t)r * w, r,
-                       1, S + cb * N, N, 0, 0, w, (T)sign, (T)1, c.st);
+                       1, S + cb * N, N, 0, 0, w, (T)sign, (T)1, c.st, c.bf16 && sizeof(T) == 8);
       c.launches += 3;
     }
   }
@@ -98,12 +98,12 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
   launch_truncate<T>(lp.nnodes, c.W, c.sig, pc, r, mode, kfix, kEpsScale * c.tol, c.eps_dev,
                      set_eps ? 1 : 0, floor_rel, rank_lv, c.T1, c.flags_dev + 1, c.st);
   launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, P, N, 0, 0, pc, c.T1, (int64_t)pc * r, pc, 0, Q,
-                   N, 0, 0, r, (T)1, (T)0, c.st);
+                   N, 0, 0, r, (T)1, (T)0, c.st, c.bf16 && sizeof(T) == 8);
   launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Q, N, 0, 0, r, Q, N, 0,
                    0, r, c.partial, c.G, c.st, c.bf16 && sizeof(T) == 8);
   launch_cholqr<T>(lp.nnodes, c.G, r, rank_lv, c.T2, c.W, c.sig, pc, c.M, want_m ? 1 : 0, c.st);
   launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Q, N, 0, 0, r, c.T2, (int64_t)r * r, r, 0, Q, N, 0,
-                   0, r, (T)1, (T)0, c.st);
+                   0, r, (T)1, (T)0, c.st, c.bf16 && sizeof(T) == 8);
   c.launches += (int)lp.d_rounds.size() + 8;
   return check_launch("panel svd");
 }
@@ -196,7 +196,7 @@ hm_status compress_hodlr_t(Ctx<T>& c, hm_handle* h) {
     // U_beta <- U_beta (W_k S_k R2^T) with the coefficients of the sibling's panel
     const LevelPlan& lp = c.tree->plans[lv];
     launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Ulv, N, 0, 0, r, c.M, (int64_t)r * r, r, 1, Ulv,
-                     N, 0, 0, r, (T)1, (T)0, c.st);
+                     N, 0, 0, r, (T)1, (T)0, c.st, c.bf16 && sizeof(T) == 8);
     c.launches += 6;
     HM_TRY(check_launch("hodlr level"));
   }

@@ -121,7 +121,7 @@ template <typename T>
 void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int64_t ldp,
                    int poff_even, int poff_odd, int kin, const T* C, int64_t cstride, int cld,
                    int cflip, T* Y, int64_t ldy, int yoff_even, int yoff_odd, int kout, T alpha,
-                   T beta, cudaStream_t st);
+                   T beta, cudaStream_t st, bool df = false);
 
 template <typename T>
 void launch_tsqr(const TsqrTask* tasks, int ntasks, int merge, const T* P, int64_t ldp,

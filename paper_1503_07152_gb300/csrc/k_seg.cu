@@ -254,6 +254,78 @@ __global__ __launch_bounds__(256) void k_seg_nn(
   }
 }
 
+// The FP64 expansion in double-float arithmetic (HM_A32), as k_seg_tn_partial_df:
+// inputs cut to hi + lo floats when staged, products by TwoProduct, sums by TwoSum.
+__global__ __launch_bounds__(256) void k_seg_nn_df(
+    const Chunk* __restrict__ chunks, int node0, const double* P, int64_t ldp, int poff_e,
+    int poff_o, int kin, const double* __restrict__ C, int64_t cstride, int cld, int cflip,
+    double* Y, int64_t ldy, int yoff_e, int yoff_o, int kout, double alpha, double beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ph = reinterpret_cast<float*>(smem_raw);  // [NN_MAX][NN_ROWS] each
+  float* Pl = Ph + NN_MAX * NN_ROWS;
+  float* Ch = Pl + NN_MAX * NN_ROWS;              // [NN_MAX][NN_MAX] each
+  float* Cl = Ch + NN_MAX * NN_MAX;
+  const Chunk ch = chunks[blockIdx.x];
+  const int rows = (int)(ch.r1 - ch.r0);
+  const int poff = (ch.node & 1) ? poff_o : poff_e;
+  const int yoff = (ch.node & 1) ? yoff_o : yoff_e;
+  const double* Cn = C + (int64_t)((ch.node ^ cflip) - node0) * cstride;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < kin * NN_ROWS; idx += 256) {
+    const int rr = idx % NN_ROWS, k = idx / NN_ROWS;
+    float h, l;
+    split_df((rr < rows) ? P[ch.r0 + rr + (int64_t)(poff + k) * ldp] : 0.0, h, l);
+    Ph[k * NN_ROWS + rr] = h;
+    Pl[k * NN_ROWS + rr] = l;
+  }
+  for (int idx = tid; idx < kin * NN_MAX; idx += 256) {
+    const int j = idx % NN_MAX, k = idx / NN_MAX;
+    float h, l;
+    split_df((j < kout) ? Cn[k + (int64_t)j * cld] : 0.0, h, l);
+    Ch[k * NN_MAX + j] = h;
+    Cl[k * NN_MAX + j] = l;
+  }
+  __syncthreads();
+  const int lane = tid & 31, w = tid >> 5;
+  float sh[2][16], sl[2][16];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
+  for (int k = 0; k < kin; ++k) {
+    const float ah[2] = {Ph[k * NN_ROWS + lane], Ph[k * NN_ROWS + lane + 32]};
+    const float al[2] = {Pl[k * NN_ROWS + lane], Pl[k * NN_ROWS + lane + 32]};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float chj = Ch[k * NN_MAX + w * 16 + j], clj = Cl[k * NN_MAX + w * 16 + j];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float p = ah[i] * chj;
+        const float e = fmaf(ah[i], chj, -p);
+        const float t = fmaf(ah[i], clj, fmaf(al[i], chj, e));
+        const float s = sh[i][j] + p;
+        const float z = s - sh[i][j];
+        const float err = (sh[i][j] - (s - z)) + (p - z);
+        sh[i][j] = s;
+        sl[i][j] += err + t;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int col = w * 16 + j;
+    if (col >= kout) continue;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int rr = lane + 32 * i;
+      if (rr >= rows) continue;
+      double* yp = Y + ch.r0 + rr + (int64_t)(yoff + col) * ldy;
+      const double v = alpha * ((double)sh[i][j] + (double)sl[i][j]);
+      *yp = (beta == 0.0) ? v : v + beta * (*yp);
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -285,9 +357,18 @@ template <typename T>
 void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int64_t ldp,
                    int poff_even, int poff_odd, int kin, const T* C, int64_t cstride, int cld,
                    int cflip, T* Y, int64_t ldy, int yoff_even, int yoff_odd, int kout, T alpha,
-                   T beta, cudaStream_t st) {
+                   T beta, cudaStream_t st, bool df) {
   count_launches(1);
   const size_t smem = (size_t)(NN_MAX * NN_ROWS + NN_MAX * NN_MAX) * sizeof(T);
+  if (sizeof(T) == 8 && df) {
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_seg_nn_df, done);
+    k_seg_nn_df<<<nchunks, 256, smem, st>>>(chunks, node0, (const double*)P, ldp, poff_even,
+                                            poff_odd, kin, (const double*)C, cstride, cld, cflip,
+                                            (double*)Y, ldy, yoff_even, yoff_odd, kout,
+                                            (double)alpha, (double)beta);
+    return;
+  }
   static std::atomic<uint32_t> done{0};
   raise_smem_limit((const void*)k_seg_nn<T>, done);
   k_seg_nn<T><<<nchunks, 256, smem, st>>>(chunks, node0, P, ldp, poff_even, poff_odd, kin, C,
@@ -303,9 +384,9 @@ template void launch_seg_tn<double>(const Chunk*, int, const int32_t*, int, int,
                                     int, double*, double*, cudaStream_t, bool);
 template void launch_seg_nn<float>(const Chunk*, int, int, const float*, int64_t, int, int, int,
                                    const float*, int64_t, int, int, float*, int64_t, int, int,
-                                   int, float, float, cudaStream_t);
+                                   int, float, float, cudaStream_t, bool);
 template void launch_seg_nn<double>(const Chunk*, int, int, const double*, int64_t, int, int,
                                     int, const double*, int64_t, int, int, double*, int64_t, int,
-                                    int, int, double, double, cudaStream_t);
+                                    int, int, double, double, cudaStream_t, bool);
 
 }  // namespace hm
