@@ -46,7 +46,13 @@ struct Items {
     }
     HM_CUDA_TRY(cudaMemcpyAsync(dev, v.data(), v.size() * sizeof(GemmItem),
                                 cudaMemcpyHostToDevice, st));
-    launch_batched_gemm<T>(dev, (int)v.size(), alpha, beta, st);
+    int max_m = 0, max_n = 0, max_k = 0;
+    for (const GemmItem& g : v) {
+      max_m = std::max(max_m, (int)g.m);
+      max_n = std::max(max_n, (int)g.n);
+      max_k = std::max(max_k, (int)g.k);
+    }
+    launch_batched_gemm<T>(dev, (int)v.size(), alpha, beta, st, max_m, max_n, max_k);
     v.clear();
     // the pageable source was staged by the copy call; the next batch may reuse dev only
     // after this launch has read it, which stream order guarantees

@@ -8,6 +8,8 @@
 //    for computing the HBS-ID representation"): column-pivoted Householder QR
 //    (Businger-Golub, largest remaining column norm, lowest index on ties) and
 //    T = R11^{-1} [R11 R12] in FP64, one block per node.
+#include <atomic>
+
 #include "hm_internal.h"
 #include "hm_hbs.h"
 
@@ -56,6 +58,57 @@ __global__ void k_batched_gemm(const GemmItem* __restrict__ items, T alpha, T be
     }
     T* c = Cm + i + (int64_t)j * it.ldc;
     *c = (beta == (T)0) ? alpha * acc : alpha * acc + beta * (*c);
+  }
+}
+
+// The same products tiled over blocks: block (item, column tile, row tile)
+// computes a 32 x 32 tile of C with its rows of op(A) (32 x k) and its columns of
+// op(B) (k x 32) staged in shared memory; thread (i0, j) = (tid / 32, tid % 32)
+// keeps rows i0, i0 + 8, i0 + 16, i0 + 24 of column j in registers.  A product's
+// FP64 work then spreads over many SMs (the coarse levels have few items, and one
+// SM's FP64 rate is low).  Each output is summed over p in the same order as
+// k_batched_gemm, so the results are identical.
+template <typename T>
+__global__ __launch_bounds__(256) void k_batched_gemm_tiled(const GemmItem* __restrict__ items,
+                                                            T alpha, T beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const GemmItem it = items[blockIdx.x];
+  const int m = it.m, n = it.n, k = it.k;
+  const int j0 = blockIdx.y * 32, m0 = blockIdx.z * 32;
+  if (j0 >= n || m0 >= m) return;  // uniform over the block
+  const T* A = (const T*)it.A;
+  const T* B = (const T*)it.B;
+  T* Cm = (T*)it.C;
+  T* As = reinterpret_cast<T*>(smem_raw);  // [32][k]: rows m0 .. m0 + 31 of op(A)
+  T* Bs = As + 32 * k;                      // [k][32]: columns j0 .. j0 + 31 of op(B)
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 32 * k; e += 256) {
+    const int ii = e / k, p = e % k, i = m0 + ii;
+    As[e] = (i < m) ? (it.ta ? A[p + (int64_t)i * it.lda] : A[i + (int64_t)p * it.lda]) : (T)0;
+  }
+  for (int e = tid; e < k * 32; e += 256) {
+    const int p = e >> 5, col = j0 + (e & 31);
+    Bs[e] = (col < n) ? (it.tb ? B[col + (int64_t)p * it.ldb] : B[p + (int64_t)col * it.ldb])
+                      : (T)0;
+  }
+  __syncthreads();
+  const int j = tid & 31, i0 = tid >> 5;
+  T acc[4] = {0, 0, 0, 0};
+  for (int p = 0; p < k; ++p) {
+    const T b = Bs[p * 32 + j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = fma(As[(i0 + 8 * q) * k + p], b, acc[q]);
+  }
+  const int col = j0 + j;
+  if (col < n) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = m0 + i0 + 8 * q;
+      if (i < m) {
+        T* c = Cm + i + (int64_t)col * it.ldc;
+        *c = (beta == (T)0) ? alpha * acc[q] : alpha * acc[q] + beta * (*c);
+      }
+    }
   }
 }
 
@@ -272,10 +325,20 @@ void launch_gather_parent_scaled(const T* U, int64_t ldu, T* P, int64_t ldp, int
 }
 
 template <typename T>
-void launch_batched_gemm(const GemmItem* items, int count, T alpha, T beta, cudaStream_t st) {
+void launch_batched_gemm(const GemmItem* items, int count, T alpha, T beta, cudaStream_t st,
+                         int max_m, int max_n, int max_k) {
   if (count <= 0) return;
   count_launches(1);
-  k_batched_gemm<T><<<count, 256, 0, st>>>(items, alpha, beta);
+  const size_t smem = (size_t)64 * max_k * sizeof(T);
+  if (max_m >= 1 && max_n >= 1 && max_k >= 1 && smem <= 96 * 1024 && max_n <= 32 * 65535 &&
+      max_m <= 32 * 65535) {
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_batched_gemm_tiled<T>, done);
+    dim3 grid((unsigned)count, (unsigned)((max_n + 31) / 32), (unsigned)((max_m + 31) / 32));
+    k_batched_gemm_tiled<T><<<grid, 256, smem, st>>>(items, alpha, beta);
+  } else {
+    k_batched_gemm<T><<<count, 256, 0, st>>>(items, alpha, beta);
+  }
 }
 
 template <typename TS, typename TD>
@@ -327,7 +390,7 @@ void launch_usamp_parent(int nnodes, int node0, const double* Utmp, const int32_
   template void launch_gather_parent_scaled<T>(const T*, int64_t, T*, int64_t, int64_t, int,   \
                                                int, const int64_t*, const T*, int,             \
                                                cudaStream_t);                                  \
-  template void launch_batched_gemm<T>(const GemmItem*, int, T, T, cudaStream_t);              \
+  template void launch_batched_gemm<T>(const GemmItem*, int, T, T, cudaStream_t, int, int, int);              \
   template void launch_id_prep_leaf<T>(const T*, int64_t, const int64_t*, const int64_t*, int, \
                                        const T*, int, double*, int, cudaStream_t);             \
   template void launch_id_prep_parent<T>(int, int, const double*, const T*, int, double*,      \
