@@ -42,6 +42,7 @@
 // always loaded (a zero slice contributes zeros).  Every mbarrier wait is bounded; on
 // timeout the block raises the error flag, writes NaN, lets its own TMA copies
 // land and leaves; TMEM is released unless the wait for its MMAs timed out.
+#include <algorithm>
 #include <atomic>
 
 #include "tc_util.cuh"
@@ -179,6 +180,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
   __shared__ float srow[TM];  // 2^(7 - e), e the exponent of the row of op(A)
+  __shared__ int win_lo, win_hi;  // this block's share of the windows (split over K)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ct = blockIdx.x, mt = blockIdx.y, nct = gridDim.x;
   const int64_t m0 = (int64_t)mt * TM;
@@ -210,6 +212,45 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     const int e = (m0 + tid < n) ? e_rows[m0 + tid] : 0;
     srow[tid] = pow2f(7 - e);
   }
+  if (warp == W_TMA) {
+    // blocks z = 0 .. gridDim.z - 1 of a row block share its active windows
+    // (those with a nonzero K tile of X) in equal counts, in window order
+    const int ks = (int)gridDim.z, z = (int)blockIdx.z;
+    int lo = 0, hi = nwin;
+    if (ks > 1) {
+      auto win_active = [&](int w) -> bool {
+        bool a = false;
+        for (int t = 0; t < WIN_TILES; ++t) {
+          const int kt = w * WIN_TILES + t;
+          if (kt < nkt && flags[(int64_t)kt * nct + ct]) a = true;
+        }
+        return a;
+      };
+      int total = 0;
+      for (int w0 = 0; w0 < nwin; w0 += 32) {
+        const int w = w0 + lane;
+        total += __popc(__ballot_sync(0xffffffffu, w < nwin && win_active(w)));
+      }
+      const int r0 = (int)((int64_t)z * total / ks), r1 = (int)((int64_t)(z + 1) * total / ks);
+      int seen = 0, clo = nwin, chi = nwin;
+      for (int w0 = 0; w0 < nwin; w0 += 32) {
+        const int w = w0 + lane;
+        const bool a = w < nwin && win_active(w);
+        const unsigned b = __ballot_sync(0xffffffffu, a);
+        const int rank = seen + __popc(b & ((1u << lane) - 1u));
+        if (a && rank == r0) clo = w;
+        if (a && rank == r1) chi = w;
+        seen += __popc(b);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        clo = min(clo, __shfl_xor_sync(0xffffffffu, clo, o));
+        chi = min(chi, __shfl_xor_sync(0xffffffffu, chi, o));
+      }
+      lo = clo;
+      hi = (r1 >= total) ? nwin : chi;
+    }
+    if (lane == 0) { win_lo = lo; win_hi = hi; }
+  }
   if (warp == W_MMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_slot)),
@@ -221,7 +262,11 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
-  auto active = [&](int kt) -> int { return flags[(int64_t)kt * nct + ct]; };
+  const int wlo = win_lo, whi = win_hi;
+  auto active = [&](int kt) -> int {
+    const int w = kt / WIN_TILES;
+    return (w >= wlo && w < whi) ? flags[(int64_t)kt * nct + ct] : 0;
+  };
 
   if (warp == W_TMA) {
     // ---------------------------------------------------------- TMA of A
@@ -437,9 +482,13 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int64_t col = colbase + j;
-        if (col < ncols)
-          Y[grow + col * ldy] = bad ? __longlong_as_double(0x7ff8000000000000ll)
-                                    : (double)hi[j] + (double)lo[j];
+        if (col < ncols) {
+          const double v = bad ? __longlong_as_double(0x7ff8000000000000ll)
+                               : (double)hi[j] + (double)lo[j];
+          // split over K: Y was zeroed and every block adds its share
+          if (gridDim.z > 1) atomicAdd(&Y[grow + col * ldy], v);
+          else Y[grow + col * ldy] = v;
+        }
       }
     }
   }
@@ -507,7 +556,27 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
   const int* e_rows = trans ? aexp + n : aexp;
   const size_t smem = gemm_esg_smem_bytes();
   static std::atomic<uint32_t> done[2] = {{0}, {0}};
-  dim3 grid((unsigned)nct, (unsigned)((n + TM - 1) / TM));
+  // Split over K when the row blocks alone leave the last wave of blocks
+  // (one per SM) markedly short: 2..4 blocks per row block share its windows,
+  // each keeping >= 16 windows of the (typically half active) K range.
+  const int nrb = (int)((n + TM - 1) / TM);
+  int nsm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    nsm = 1;
+  auto eff = [&](int k) {
+    const int64_t c = (int64_t)nct * nrb * k;
+    return (double)c / ((double)nsm * (double)((c + nsm - 1) / nsm));
+  };
+  int ks = 1;
+  const int ks_max = std::max(1, std::min(4, nwin / 16));
+  for (int k = 2; k <= ks_max; ++k)
+    if (eff(k) > eff(ks) + 0.05) ks = k;
+  if (ks > 1 &&
+      cudaMemset2DAsync(Y, (size_t)ldy * sizeof(double), 0, (size_t)n * sizeof(double),
+                        (size_t)ncols, st) != cudaSuccess)
+    return 2;
+  dim3 grid((unsigned)nct, (unsigned)nrb, (unsigned)ks);
   if (trans) {
     raise_smem_limit((const void*)k_gemm_esg<1>, done[1]);
     k_gemm_esg<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
