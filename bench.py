@@ -132,11 +132,12 @@ def time_events(fn, reps, torch):
     return s.elapsed_time(e) / reps
 
 
-# DRAM traffic of one k_gemm_esg launch from an ncu capture of the same call (level-0
-# A Omega_2, 60 columns) at N = 16384: 541.9 MB read + 3.4 MB written for 552.6 MB of
-# algorithmic bytes.  Traffic grows with the units processed (rows x active K), so a
+# DRAM traffic of one k_gemm_esg launch from an ncu capture of a level-0 sample
+# (60 columns, half of K active) at N = 16384: 541.4 MB read + 3.1 MB written for
+# 552.6 MB of algorithmic bytes.  Traffic grows with the units processed (rows x
+# active K; a split over K gives each block a disjoint share of the windows), so a
 # launch at another N moves this ratio times its own algorithmic bytes.
-ESG_TRAFFIC_PER_ALG_BYTE = (541.9e6 + 3.4e6) / (4.0 * 16384 * 8192 + 16.0 * 16384 * 60)
+ESG_TRAFFIC_PER_ALG_BYTE = (541.4e6 + 3.1e6) / (4.0 * 16384 * 8192 + 16.0 * 16384 * 60)
 
 
 def gemm_roofline(hm, torch, A, op, tree, n, peak_gbs, peak_kind):
