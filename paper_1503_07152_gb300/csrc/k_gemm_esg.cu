@@ -557,8 +557,10 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
   const size_t smem = gemm_esg_smem_bytes();
   static std::atomic<uint32_t> done[2] = {{0}, {0}};
   // Split over K when the row blocks alone leave the last wave of blocks
-  // (one per SM) markedly short: 2..4 blocks per row block share its windows,
-  // each keeping >= 16 windows of the (typically half active) K range.
+  // (one per SM) markedly short: two blocks per row block share its windows,
+  // each keeping >= 16 windows of the (typically half active) K range.  At most
+  // two: two FP64 partials added into a zeroed Y give the same sum in either
+  // order, so the results stay reproducible.
   const int nrb = (int)((n + TM - 1) / TM);
   int nsm = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -569,7 +571,7 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
     return (double)c / ((double)nsm * (double)((c + nsm - 1) / nsm));
   };
   int ks = 1;
-  const int ks_max = std::max(1, std::min(4, nwin / 16));
+  const int ks_max = std::max(1, std::min(2, nwin / 16));
   for (int k = 2; k <= ks_max; ++k)
     if (eff(k) > eff(ks) + 0.05) ks = k;
   if (ks > 1 &&
