@@ -7,7 +7,7 @@ The oracle keeps every long basis explicitly (the basic scheme); the storage
 efficient scheme of Sec. 4.2 computes the same numbers and keeps only the
 current level's long bases plus the vectors y, z.
 
-Readings of the paper (each also listed in the design doc):
+Readings of the paper:
 * Sibling matrices: the figure assigns X1 to B_alphabeta; from
   Z1^loc(:, 1:r) = A_ba^T U_b = V_a diag(b21) X1(1:r,:)^T it follows that
   B_ba = X1(1:r,:) diag(b21) and B_ab = X2(1:r,:) diag(b12).

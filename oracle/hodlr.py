@@ -7,7 +7,7 @@ V_beta^T with orthonormal long bases, and a dense D_tau for every leaf.
 ``U[a]`` / ``B[a]`` / ``V[a ^ 1]`` hold the factors of the block (a, sibling);
 the rank of that block is the column count of U[a].
 
-Readings of the paper (each also listed in the design doc):
+Readings of the paper:
 * The factorization display of Sec. 2.8 is read as A_ab = U_a B_ab V_b^T with
   U, V orthonormal.
 * In the figure the second SVD of a sibling pair returns \\hat U_alpha (the
