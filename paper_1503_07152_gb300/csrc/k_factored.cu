@@ -9,6 +9,8 @@
 // runs one block per leaf: every row of the leaf gathers the contributions of
 // its L ancestors' siblings (ancestor of leaf l on level j = l >> (L - j)) and
 // of the leaf block D, and, for the adjoint, writes the gradient rows.
+#include <atomic>
+
 #include "hm_internal.h"
 
 namespace hm {
@@ -17,7 +19,10 @@ namespace {
 constexpr int kMaxK = 64;
 
 // partial[chunk][0:k] = V_j(rows)^T x(rows); with second operand pair for the
-// adjoint: partial[chunk][k:2k] = U_j(rows)^T res(rows).
+// adjoint: partial[chunk][k:2k] = U_j(rows)^T res(rows).  Thread t loads row t's k
+// factor entries at once (independent, coalesced loads), the products go to
+// shared memory (row-major, stride k + 1: conflict-free both ways), thread
+// (col, part) sums its 32-row part of a column, and the 8 parts are added.
 __global__ __launch_bounds__(256) void k_fact_partial(const FactChunk* __restrict__ ch,
                                                       int64_t n, int k,
                                                       const float* __restrict__ A0,
@@ -25,22 +30,30 @@ __global__ __launch_bounds__(256) void k_fact_partial(const FactChunk* __restric
                                                       const float* __restrict__ A1,
                                                       const float* __restrict__ v1,
                                                       float* __restrict__ partial) {
+  extern __shared__ float prod[];  // [256][k + 1]
   __shared__ float red[8][2 * kMaxK];
   const FactChunk c = ch[blockIdx.x];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
+  const int ldp = k + 1;
   const int64_t row = c.r0 + tid;
   const bool live = row < c.r1;
   const int npair = A1 ? 2 : 1;
+  const int cl = tid & 31, part = tid >> 5;
   for (int p = 0; p < npair; ++p) {
     const float* A = (p == 0 ? A0 : A1) + (int64_t)(c.level - 1) * n * k;
     const float xv = live ? (p == 0 ? v0 : v1)[row] : 0.f;
-    for (int col = 0; col < k; ++col) {
-      float v = live ? A[row + (int64_t)col * n] * xv : 0.f;
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][p * k + col] = v;
+#pragma unroll 8
+    for (int col = 0; col < k; ++col)
+      prod[tid * ldp + col] = live ? A[row + (int64_t)col * n] * xv : 0.f;
+    __syncthreads();
+    for (int col = cl; col < k; col += 32) {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) s += prod[(part * 32 + i) * ldp + col];
+      red[part][p * k + col] = s;
     }
+    __syncthreads();
   }
-  __syncthreads();
   for (int e = tid; e < npair * k; e += 256) {
     float s = 0.f;
     for (int w = 0; w < 8; ++w) s += red[w][e];
@@ -175,6 +188,13 @@ __global__ __launch_bounds__(256) void k_fact_adjoint(
 
 }  // namespace
 
+// dynamic shared memory of k_fact_partial (66.5 KB at k = 64: limit raised once)
+static size_t fact_partial_smem(int k) {
+  static std::atomic<uint32_t> done{0};
+  raise_smem_limit((const void*)k_fact_partial, done);
+  return sizeof(float) * 256 * (size_t)(k + 1);
+}
+
 size_t factored_scratch_bytes(const hm_tree* t, int k) {
   const size_t nodes = (size_t)1 << (t->L + 1);
   return sizeof(float) * ((size_t)t->n_fchunks * 2 * k + nodes * 2 * k) + 256;
@@ -189,7 +209,7 @@ void launch_factored_apply(const hm_tree* t, int k, const float* U, const float*
   float* partial = scratch;
   float* coef = scratch + (size_t)t->n_fchunks * k;
   // t_node = Proj(I_node)^T x with Proj = V (H x) or U (H^T x)
-  k_fact_partial<<<t->n_fchunks, 256, 0, st>>>(t->d_fchunks, t->n, k, trans ? U : V, x, nullptr,
+  k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, trans ? U : V, x, nullptr,
                                                 nullptr, partial);
   k_fact_reduce<<<nodes - 2, 128, 0, st>>>(partial, t->d_fbegin, k, nodes, coef);
   const int nmax = (int)t->nmax;
@@ -207,7 +227,7 @@ void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const floa
   const int nodes = 1 << (L + 1);
   float* partial = scratch;
   float* coef = scratch + (size_t)t->n_fchunks * 2 * k;
-  k_fact_partial<<<t->n_fchunks, 256, 0, st>>>(t->d_fchunks, t->n, k, V, x, U, res, partial);
+  k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, V, x, U, res, partial);
   k_fact_reduce<<<nodes - 2, 128, 0, st>>>(partial, t->d_fbegin, 2 * k, nodes, coef);
   const int nmax = (int)t->nmax;
   const size_t smem = sizeof(float) * (2 * L * kMaxK + 3 * nmax);
