@@ -61,16 +61,28 @@ __global__ __launch_bounds__(256) void k_fact_partial(const FactChunk* __restric
   }
 }
 
-// out[node][e] = sum over the node's chunks (heap ids 2 .. 2^(L+1)-1).
-__global__ void k_fact_reduce(const float* __restrict__ partial, const int32_t* __restrict__ fbegin,
-                              int width, int nnodes_total, float* __restrict__ out) {
+// out[node][e] = sum over the node's chunks (heap ids 2 .. 2^(L+1)-1).  The
+// 256 threads form 256 / width groups; group q sums chunks q, q + groups, ...
+// and the group sums are added in group order (deterministic).  width <= 128.
+__global__ __launch_bounds__(256) void k_fact_reduce(const float* __restrict__ partial,
+                                                     const int32_t* __restrict__ fbegin,
+                                                     int width, int nnodes_total,
+                                                     float* __restrict__ out) {
+  __shared__ float sred[256];
   const int node = 2 + blockIdx.x;
-  if (node >= nnodes_total) return;
+  if (node >= nnodes_total) return;  // uniform over the block
   const int c0 = fbegin[node], c1 = fbegin[node + 1];
-  for (int e = threadIdx.x; e < width; e += blockDim.x) {
-    float s = 0.f;
-    for (int c = c0; c < c1; ++c) s += partial[(int64_t)c * width + e];
-    out[(int64_t)node * width + e] = s;
+  const int groups = 256 / width;
+  const int t = threadIdx.x, e = t % width, q = t / width;
+  float s = 0.f;
+  if (q < groups)
+    for (int c = c0 + q; c < c1; c += groups) s += partial[(int64_t)c * width + e];
+  sred[t] = s;
+  __syncthreads();
+  if (t < width) {
+    float tot = 0.f;
+    for (int g = 0; g < groups; ++g) tot += sred[g * width + t];
+    out[(int64_t)node * width + t] = tot;
   }
 }
 
@@ -211,7 +223,7 @@ void launch_factored_apply(const hm_tree* t, int k, const float* U, const float*
   // t_node = Proj(I_node)^T x with Proj = V (H x) or U (H^T x)
   k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, trans ? U : V, x, nullptr,
                                                 nullptr, partial);
-  k_fact_reduce<<<nodes - 2, 128, 0, st>>>(partial, t->d_fbegin, k, nodes, coef);
+  k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, k, nodes, coef);
   const int nmax = (int)t->nmax;
   const size_t smem = sizeof(float) * (L * kMaxK + 2 * nmax);
   k_fact_expand<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, k,
@@ -228,7 +240,7 @@ void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const floa
   float* partial = scratch;
   float* coef = scratch + (size_t)t->n_fchunks * 2 * k;
   k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, V, x, U, res, partial);
-  k_fact_reduce<<<nodes - 2, 128, 0, st>>>(partial, t->d_fbegin, 2 * k, nodes, coef);
+  k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, 2 * k, nodes, coef);
   const int nmax = (int)t->nmax;
   const size_t smem = sizeof(float) * (2 * L * kMaxK + 3 * nmax);
   k_fact_adjoint<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, U, V, D,
