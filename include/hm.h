@@ -163,6 +163,26 @@ hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_
 void hm_dense_operator_destroy(hm_operator* op);
 
 /*
+ * Status of a dense operator's tensor-core GEMMs (dtypes 1 and 4): synchronizes
+ * `stream`, then returns HM_ETIMEOUT if one of their bounded device-side waits
+ * gave up since the last check (those outputs were written as NaN; the flag is
+ * cleared), else HM_OK.  The compress calls run this check themselves at their
+ * end for dense operators and return HM_ETIMEOUT ahead of HM_ENONFINITE.
+ */
+hm_status hm_dense_operator_check(const hm_operator* op, void* stream);
+
+/*
+ * Poll limit of the bounded mbarrier waits inside the tensor-core GEMMs'
+ * pipelines (process-wide; polls <= 0 restores the default 2^25, seconds of
+ * waiting).  A wait that runs out makes the block give up: it raises the
+ * operator's error flag, writes NaN, and leaves only after its own TMA copies
+ * have landed and its issued MMAs have completed (those waits always take the
+ * default limit).  A small limit makes normal calls fail with HM_ETIMEOUT; it
+ * exists to exercise that path.
+ */
+hm_status hm_set_wait_limit(int64_t polls);
+
+/*
  * The sampling GEMM behind the dense operator, callable directly:
  * Y = op(A) X for the row-major dense A above.  Same argument rules as
  * hm_apply_fn.  Returns HM_OK or an error status.
@@ -269,11 +289,50 @@ hm_status hm_rel_frob_error(const hm_handle* h, const void* A, int64_t lda, int3
 hm_status hm_hodlr_export_level(const hm_handle* h, int32_t level, void* U, void* V,
                                 void* stream);
 
+/*
+ * Phase profile of a compression (the time split of Sec. 5's tables, T_net
+ * against the black box, refined per level and phase).  With profiling on
+ * (process-wide, hm_set_profiling(1)), the compress calls record a CUDA event
+ * at the start of every phase of every level and side, and the handle keeps
+ * one segment per phase: node level `level` (0 .. L - 1 for the sweeps, L for
+ * the identity probe), side 0 (samples of A) or 1 (samples of A^T), phase, and
+ * its device time in ms.  hm_profile copies up to cap segments to `out` (host)
+ * and writes the total count to *count.  Profiling adds a few hundred events
+ * per compression; off by default.
+ */
+typedef enum {
+  HM_PHASE_SAMPLE = 0,  /* test matrix, black-box calls, non-finite check */
+  HM_PHASE_PEEL = 1,    /* subtraction of A^(l) Omega (partial apply) */
+  HM_PHASE_TSQR = 2,    /* Householder QR of the sample panels */
+  HM_PHASE_SVD = 3,     /* SVD of the panels' R factors and the rank decision */
+  HM_PHASE_ORTH = 4,    /* bases from the SVD (Q = P T1), CholQR pass */
+  HM_PHASE_BASES = 5,   /* gathers, scatters, short bases, coefficient copies */
+  HM_PHASE_ID = 6       /* HBS-ID upward sweep (interpolative decompositions) */
+} hm_phase;
+typedef struct {
+  int32_t level;
+  int32_t side;
+  int32_t phase;
+  double ms;
+} hm_phase_t;
+hm_status hm_set_profiling(int32_t on);
+hm_status hm_profile(const hm_handle* h, hm_phase_t* out, int32_t cap, int32_t* count);
+
 /* Summary of the representation (ranks, black-box column counts, bytes M). */
 hm_status hm_info(const hm_handle* h, hm_info_t* out);
 /* Rank of the sibling block (node, node ^ 1) (HODLR) or of node's basis (HBS,
  * HBS-ID incoming skeleton).  Synchronous small read. */
 hm_status hm_node_rank(const hm_handle* h, int64_t node, int32_t* rank);
+/*
+ * Skeleton index set of an HBS-ID node (Sec. 4.3: the row skeleton I~_tau of
+ * the incoming interpolative decomposition, side 0, or the column skeleton
+ * I^_tau of the outgoing one, side 1; B_skel = A(I~_alpha, I^_beta)).  Writes
+ * the node's k global indices in [0, n), in the pivot order of its
+ * interpolative decomposition, to idx[0 .. k) and -1 to idx[k .. r); idx is a
+ * HOST buffer of at least r entries (r = hm_info's r).  2 <= node < 2^(L+1).
+ * Synchronous (a small device-to-host copy); HM_EINVAL for other handles.
+ */
+hm_status hm_skeleton(const hm_handle* h, int64_t node, int32_t side, int64_t* idx, int32_t* k);
 void hm_destroy(hm_handle* h);
 
 /* ------------------------------------------- factored HODLR and adjoint --- */
@@ -289,7 +348,9 @@ void hm_destroy(hm_handle* h);
  *        (ld n_max, entries beyond the leaf size are ignored).
  *  x, y: device float vectors of length N (y is overwritten).
  * trans = 1 applies H^T.  1 <= k <= 64.  Stream-ordered scratch as for the
- * adjoint below.
+ * adjoint below.  The per-leaf kernel keeps the leaf's slice of x in shared
+ * memory: leaves too large for the device's per-block shared memory (about
+ * 55k points on a GB300) return HM_EINVAL naming the sizes.
  */
 hm_status hm_hodlr_factored_apply(const hm_tree* tree, int32_t k, const float* U,
                                   const float* V, const float* D, int trans, const float* x,
@@ -316,11 +377,14 @@ hm_status hm_hodlr_factored_apply(const hm_tree* tree, int32_t k, const float* U
  *    between them) race on it and give wrong results.  Order them on one
  *    stream or with events.
  *  - The first call on a device looks up the buffer's address
- *    (cudaGetSymbolAddress, with that device current) and caches it; make that
- *    first call before any stream capture.
- *  - The tree's index tables must already be on the device (uploading them
- *    allocates): one call of hm_hodlr_factored_apply with this tree, on the
- *    same device, uploads them; otherwise HM_EINVAL.
+ *    (cudaGetSymbolAddress, with that device current) and caches it for the
+ *    life of the process; make that first call before any stream capture.  A
+ *    cudaDeviceReset of that device invalidates the cached address: do not
+ *    call this entry point again in the same process after one.
+ *  - The tree's index tables must already be on the current device (uploading
+ *    them allocates): one call of hm_hodlr_factored_apply with this tree, on
+ *    the same device, uploads them; otherwise (not uploaded, or uploaded to
+ *    another device) HM_EINVAL.
  */
 hm_status hm_hodlr_factored_apply_noalloc(const hm_tree* tree, int32_t k, const float* U,
                                           const float* V, const float* D, int trans,
@@ -336,6 +400,8 @@ hm_status hm_hodlr_factored_apply_noalloc(const hm_tree* tree, int32_t k, const 
  * r = H x - b and scale = 2 these are the gradients of ||H x - b||^2.
  * Stream-ordered scratch of O(k * (N / 256 * L + 2^(L+1))) floats is taken
  * from the CUDA memory pool of the stream's device and released in order.
+ * Leaves too large for the per-leaf kernel's shared memory (about 37k points
+ * on a GB300) return HM_EINVAL naming the sizes.
  */
 hm_status hm_hodlr_factored_adjoint(const hm_tree* tree, int32_t k, const float* U,
                                     const float* V, const float* D, const float* x,

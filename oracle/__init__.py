@@ -23,6 +23,7 @@ hbs       HBS compression (Figs. basic / storage-efficient HBS, Sec. 4.1-4.2),
 grad      factored HODLR apply, its transpose and the gradients of
           ||Hx - b||^2 with respect to x, U, V, D
 metrics   relative Frobenius error and the randomized estimate E (Sec. 5)
+cost      operation counts of the oracle's own arithmetic (T_net, Sec. 5)
 
 Parity status of each function is stated in its docstring; every function is
 pinned by a ``-m "not gpu"`` test except where the docstring says

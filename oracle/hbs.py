@@ -46,6 +46,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from .cost import mm, svd
 from .hodlr import ApplyFn, gaussian_test_matrix, identity_test_matrix
 from .lowrank import RANGE_FLOOR, fix_signs, interp_decomp
 from .tree import Tree
@@ -88,24 +89,24 @@ def partial_apply(h: HBS, m: int, Q: np.ndarray, transpose: bool = False) -> np.
     qhat = {}
     # outgoing expansions on level m
     for tau in t.level_nodes(m):
-        qhat[tau] = Vout[tau].T @ Q[t.rows(tau)]
+        qhat[tau] = mm(Vout[tau].T, Q[t.rows(tau)])
     # upward pass, levels m-1 .. 1
     for lev in range(m - 1, 0, -1):
         for tau in t.level_nodes(lev):
             a, b = 2 * tau, 2 * tau + 1
-            qhat[tau] = Sout[tau].T @ np.vstack([qhat[a], qhat[b]])
+            qhat[tau] = mm(Sout[tau].T, np.vstack([qhat[a], qhat[b]]))
     # incoming expansions for the children of the root
-    uhat = {2: Bmat(2) @ qhat[3], 3: Bmat(3) @ qhat[2]}
+    uhat = {2: mm(Bmat(2), qhat[3]), 3: mm(Bmat(3), qhat[2])}
     # downward pass, levels 1 .. m-1
     r = h.r
     for lev in range(1, m):
         for tau in t.level_nodes(lev):
             a, b = 2 * tau, 2 * tau + 1
-            uhat[a] = Bmat(a) @ qhat[b] + Sin[tau][:r] @ uhat[tau]
-            uhat[b] = Bmat(b) @ qhat[a] + Sin[tau][r:] @ uhat[tau]
+            uhat[a] = mm(Bmat(a), qhat[b]) + mm(Sin[tau][:r], uhat[tau])
+            uhat[b] = mm(Bmat(b), qhat[a]) + mm(Sin[tau][r:], uhat[tau])
     # incoming expansions on level m
     for tau in t.level_nodes(m):
-        out[t.rows(tau)] = Uin[tau] @ uhat[tau]
+        out[t.rows(tau)] = mm(Uin[tau], uhat[tau])
     return out
 
 
@@ -114,7 +115,7 @@ def apply(h: HBS, X: np.ndarray, transpose: bool = False) -> np.ndarray:
     Y = partial_apply(h, t.L, X, transpose)
     for tau in t.leaves():
         I = t.rows(tau)
-        Y[I] += (h.D[tau].T if transpose else h.D[tau]) @ X[I]
+        Y[I] += mm(h.D[tau].T if transpose else h.D[tau], X[I])
     return Y
 
 
@@ -126,7 +127,7 @@ def _svd_r(M: np.ndarray, r: int, floor: bool = False):
     """svd(M, r): the leading r singular triplets.  With floor, directions whose
     singular value is below RANGE_FLOOR * sigma_1 are returned as zero columns
     (significant-range reading, as for ``lowrank.range_basis``)."""
-    U, s, Vt = np.linalg.svd(M, full_matrices=False)
+    U, s, Vt = svd(M)
     U, Vt = fix_signs(U, Vt)
     U, s, V = U[:, :r].copy(), s[:r].copy(), Vt[:r].T.copy()
     if floor and s.size:
@@ -166,8 +167,8 @@ def compress(apply_A: ApplyFn, tree: Tree, r: int, seed: int = 2, mixed: bool = 
             Xt[t.rows(a), r:] = h.Ulong[a]
             Xt[t.rows(b), :r] = h.Ulong[b]
             if tau != 1:
-                h.Ushort[tau] = np.vstack([h.Ulong[a].T @ h.Ulong[tau][Ja],
-                                           h.Ulong[b].T @ h.Ulong[tau][Jb]])
+                h.Ushort[tau] = np.vstack([mm(h.Ulong[a].T, h.Ulong[tau][Ja]),
+                                           mm(h.Ulong[b].T, h.Ulong[tau][Jb])])
         Z = apply_A(Xt, True) - partial_apply(h, level, Xt, transpose=True)
         h.cols_At += Xt.shape[1]
         for tau in t.level_nodes(level):
@@ -186,8 +187,8 @@ def compress(apply_A: ApplyFn, tree: Tree, r: int, seed: int = 2, mixed: bool = 
             h.B[b] = X1[:r] * b21[None, :]   # B_ba = X1(1:r,:) diag(b21)
             h.B[a] = X2[:r] * b12[None, :]   # B_ab = X2(1:r,:) diag(b12)
             if tau != 1:
-                h.Vshort[tau] = np.vstack([h.Vlong[a].T @ h.Vlong[tau][Ja],
-                                           h.Vlong[b].T @ h.Vlong[tau][Jb]])
+                h.Vshort[tau] = np.vstack([mm(h.Vlong[a].T, h.Vlong[tau][Ja]),
+                                           mm(h.Vlong[b].T, h.Vlong[tau][Jb])])
     X = identity_test_matrix(t)
     Y = apply_A(X, False) - partial_apply(h, t.L, X)
     h.cols_A += X.shape[1]

@@ -35,6 +35,7 @@ from typing import Callable
 
 import numpy as np
 
+from .cost import mm, svd
 from .lowrank import qr_basis, range_basis, svd_trunc
 from .philox import level_field
 from .tree import Tree
@@ -69,9 +70,9 @@ def partial_apply(h: HODLR, level: int, X: np.ndarray, transpose: bool = False) 
             b = a ^ 1
             Ia, Ib = t.rows(a), t.rows(b)
             if not transpose:
-                Y[Ia] += h.U[a] @ (h.B[a] @ (h.V[b].T @ X[Ib]))
+                Y[Ia] += mm(h.U[a], mm(h.B[a], mm(h.V[b].T, X[Ib])))
             else:
-                Y[Ib] += h.V[b] @ (h.B[a].T @ (h.U[a].T @ X[Ia]))
+                Y[Ib] += mm(h.V[b], mm(h.B[a].T, mm(h.U[a].T, X[Ia])))
     return Y
 
 
@@ -81,7 +82,7 @@ def apply(h: HODLR, X: np.ndarray, transpose: bool = False) -> np.ndarray:
     Y = partial_apply(h, t.L, X, transpose)
     for tau in t.leaves():
         I = t.rows(tau)
-        Y[I] += (h.D[tau].T if transpose else h.D[tau]) @ X[I]
+        Y[I] += mm(h.D[tau].T if transpose else h.D[tau], X[I])
     return Y
 
 
@@ -147,8 +148,8 @@ def compress(apply_A: ApplyFn, tree: Tree, r: int, k: int | None = None,
         svds = {}
         for tau in tree.level_nodes(level):
             a, b = 2 * tau, 2 * tau + 1
-            svds[tau] = (np.linalg.svd(Z[tree.rows(a), :r], full_matrices=False),  # A_ba^T U_b
-                         np.linalg.svd(Z[tree.rows(b), r:], full_matrices=False))  # A_ab^T U_a
+            svds[tau] = (svd(Z[tree.rows(a), :r]),  # A_ba^T U_b
+                         svd(Z[tree.rows(b), r:]))  # A_ab^T U_a
         if tol is not None and h.eps_abs is None:
             h.eps_abs = EPS_SCALE * tol * max(max(s1[1][0], s2[1][0]) for s1, s2 in svds.values())
         for tau in tree.level_nodes(level):
@@ -157,8 +158,8 @@ def compress(apply_A: ApplyFn, tree: Tree, r: int, k: int | None = None,
             # [V_a, B_ba, \hat U_b] = svd(Z1(I_a,:)); [V_b, B_ab, \hat U_a] = svd(Z2(I_b,:))
             Va, sa, Wat = _truncate(Va, sa, Wat, k, h.eps_abs)
             Vb, sb, Wbt = _truncate(Vb, sb, Wbt, k, h.eps_abs)
-            h.V[a], h.B[b], h.U[b] = Va, np.diag(sa), Ucur[b] @ Wat[:, :Ucur[b].shape[1]].T
-            h.V[b], h.B[a], h.U[a] = Vb, np.diag(sb), Ucur[a] @ Wbt[:, :Ucur[a].shape[1]].T
+            h.V[a], h.B[b], h.U[b] = Va, np.diag(sa), mm(Ucur[b], Wat[:, :Ucur[b].shape[1]].T)
+            h.V[b], h.B[a], h.U[a] = Vb, np.diag(sb), mm(Ucur[a], Wbt[:, :Ucur[a].shape[1]].T)
     # diagonal blocks: Y = A Omega - A^(L) Omega with the identity probe
     X = identity_test_matrix(tree)
     Y = apply_A(X, False) - partial_apply(h, tree.L, X)

@@ -30,10 +30,12 @@ from __future__ import annotations
 import numpy as np
 from scipy.linalg import solve_triangular
 
+from . import cost
+
 
 def qr_basis(A: np.ndarray) -> np.ndarray:
     """Q factor of the economy QR of A (orthonormal columns spanning range(A))."""
-    Q, _ = np.linalg.qr(A, mode="reduced")
+    Q, _ = cost.qr(A)
     return Q
 
 
@@ -61,7 +63,7 @@ def range_basis(A: np.ndarray, rel_floor: float = RANGE_FLOOR) -> np.ndarray:
     up an arbitrary share of the coarser levels' truncation error through the
     transpose peel).  The default floor 1e-12 lies well above FP64 rounding and
     far below any compression tolerance."""
-    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    U, s, Vt = cost.svd(A)
     U, Vt = fix_signs(U, Vt)
     if s.size == 0 or s[0] == 0.0:
         return U[:, :0]

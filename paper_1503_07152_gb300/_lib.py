@@ -43,6 +43,12 @@ class _Info(C.Structure):
                 ("launches", C.c_int32)]
 
 
+class _Phase(C.Structure):
+    _fields_ = [("level", C.c_int32), ("side", C.c_int32), ("phase", C.c_int32), ("ms", C.c_double)]
+
+
+PHASES = ["sample", "peel", "tsqr", "svd", "orth", "bases", "id"]
+
 _P = C.c_void_p
 _sig = {
     "hm_tree_create": ([C.c_int64, C.c_int32, C.POINTER(_P)], C.c_int),
@@ -63,6 +69,9 @@ _sig = {
     "hm_info": ([_P, C.POINTER(_Info)], C.c_int),
     "hm_node_rank": ([_P, C.c_int64, C.POINTER(C.c_int32)], C.c_int),
     "hm_destroy": ([_P], None),
+    "hm_set_profiling": ([C.c_int32], C.c_int),
+    "hm_profile": ([_P, C.POINTER(_Phase), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+    "hm_skeleton": ([_P, C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)], C.c_int),
     "hm_hodlr_factored_apply": ([_P, C.c_int32, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
     "hm_hodlr_factored_apply_noalloc": ([_P, C.c_int32, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
     "hm_hodlr_factored_adjoint": ([_P, C.c_int32, _P, _P, _P, _P, _P, C.c_float, _P, _P, _P, _P, _P],
@@ -71,6 +80,8 @@ _sig = {
     "hm_hodlr_export_level": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "hm_gaussian_test_matrix": ([_P, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, _P, C.c_int64, _P],
                                 C.c_int),
+    "hm_dense_operator_check": ([C.POINTER(_Operator), _P], C.c_int),
+    "hm_set_wait_limit": ([C.c_int64], C.c_int),
     "hm_last_error": ([], C.c_char_p),
     "hm_version": ([], C.c_char_p),
     "hm_launch_count": ([], C.c_int64),
@@ -192,6 +203,17 @@ def callback_operator(n: int, fn) -> Operator:
     return Operator(op, keep=cb)
 
 
+def hm_dense_operator_check(op: Operator, stream=None) -> None:
+    """Raises HmError (HM_ETIMEOUT) if a bounded wait of the operator's GEMMs gave up."""
+    _check(lib.hm_dense_operator_check(C.byref(op.op), C.c_void_p(_stream(stream))),
+           "hm_dense_operator_check")
+
+
+def hm_set_wait_limit(polls: int) -> None:
+    """Poll limit of the tensor-core GEMMs' pipeline waits (<= 0: the default)."""
+    _check(lib.hm_set_wait_limit(int(polls)), "hm_set_wait_limit")
+
+
 def hm_dense_apply(op: Operator, trans: int, X: torch.Tensor, Y: torch.Tensor, stream=None):
     px, ldx, ncols = _colmajor(X, op.n, "X")
     py, ldy, _ = _colmajor(Y, op.n, "Y")
@@ -300,6 +322,30 @@ def hm_node_rank(h: Handle, node: int) -> int:
     k = C.c_int32()
     _check(lib.hm_node_rank(h.ptr, node, C.byref(k)), "hm_node_rank")
     return k.value
+
+
+def hm_set_profiling(on: bool) -> None:
+    """Record a CUDA event at the start of every phase of later compressions."""
+    _check(lib.hm_set_profiling(1 if on else 0), "hm_set_profiling")
+
+
+def hm_profile(h: Handle) -> list:
+    """Phase segments of a profiled compression: dicts of level, side, phase name, ms."""
+    n = C.c_int32()
+    _check(lib.hm_profile(h.ptr, None, 0, C.byref(n)), "hm_profile")
+    buf = (_Phase * max(1, n.value))()
+    _check(lib.hm_profile(h.ptr, buf, n.value, C.byref(n)), "hm_profile")
+    return [{"level": p.level, "side": p.side, "phase": PHASES[p.phase], "ms": p.ms}
+            for p in buf[:n.value]]
+
+
+def hm_skeleton(h: Handle, node: int, side: int) -> list:
+    """Global skeleton indices of an HBS-ID node in pivot order (side 0: rows, 1: columns)."""
+    r = h.info["r"]
+    buf = (C.c_int64 * r)()
+    k = C.c_int32()
+    _check(lib.hm_skeleton(h.ptr, node, side, buf, C.byref(k)), "hm_skeleton")
+    return [int(buf[i]) for i in range(k.value)]
 
 
 def hm_hodlr_factored_apply(tree: Tree, k: int, U, V, D, x, y, trans: int = 0, stream=None) -> None:

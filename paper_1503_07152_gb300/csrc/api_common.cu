@@ -18,6 +18,9 @@ void set_error(const std::string& msg) {
 const char* get_error() { return g_err.c_str(); }
 void clear_error() { g_err.clear(); }
 
+static std::atomic<long long> g_wait_limit{1ll << 25};
+long long wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
@@ -300,6 +303,9 @@ hm_status tree_device(hm_tree* t, cudaStream_t st) {
     lp.d_final_slot = (const int32_t*)(base + o_fs);
   }
   HM_CUDA_TRY(cudaStreamSynchronize(st));
+  int dev = -1;
+  HM_CUDA_TRY(cudaGetDevice(&dev));
+  t->dev = dev;
   t->d_start = ds;  // set last: marks the upload complete
   return HM_OK;
 }
@@ -441,6 +447,39 @@ void hm_dense_operator_destroy(hm_operator* op) {
   delete d;
   op->ctx = nullptr;
   op->apply = nullptr;
+}
+
+}  // extern "C"
+
+hm_status hm::dense_take_timeout(const hm_operator* op) {
+  if (!op || op->apply != dense_cb || !op->ctx) return HM_OK;
+  hm_dense_ctx* d = (hm_dense_ctx*)op->ctx;
+  int flag = 0;
+  HM_CUDA_TRY(cudaMemcpy(&flag, d->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!flag) return HM_OK;
+  HM_CUDA_TRY(cudaMemset(d->err, 0, sizeof(int)));
+  HM_CUDA_TRY(cudaDeviceSynchronize());
+  set_error("a bounded wait of the tensor-core sampling GEMM gave up; its outputs were "
+            "written as NaN (see hm_set_wait_limit)");
+  return HM_ETIMEOUT;
+}
+
+extern "C" {
+
+hm_status hm_set_wait_limit(int64_t polls) {
+  clear_error();
+  g_wait_limit.store(polls > 0 ? (long long)polls : (1ll << 25), std::memory_order_relaxed);
+  return HM_OK;
+}
+
+hm_status hm_dense_operator_check(const hm_operator* op, void* stream) {
+  clear_error();
+  if (!op || !op->ctx || op->apply != dense_cb) {
+    set_error("hm_dense_operator_check: need an operator made by hm_dense_operator_create");
+    return HM_EINVAL;
+  }
+  HM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  return dense_take_timeout(op);
 }
 
 hm_status hm_dense_apply(const hm_operator* op, int trans, int64_t ncols, const void* X,

@@ -12,6 +12,7 @@
 using namespace hm;
 
 namespace hm {
+void set_profiling(int on);
 template <typename T>
 hm_status hbs_apply_t(const hm_handle* h, int trans, int64_t ncols, const T* X, int64_t ldx,
                       T* Y, int64_t ldy, cudaStream_t st);
@@ -191,6 +192,40 @@ hm_status hm_node_rank(const hm_handle* h, int64_t node, int32_t* rank) {
   return HM_OK;
 }
 
+hm_status hm_set_profiling(int32_t on) {
+  clear_error();
+  set_profiling(on);
+  return HM_OK;
+}
+
+hm_status hm_profile(const hm_handle* h, hm_phase_t* out, int32_t cap, int32_t* count) {
+  clear_error();
+  if (!h || !count || cap < 0 || (cap > 0 && !out)) {
+    set_error("hm_profile: need handle, count, cap >= 0 and out when cap > 0");
+    return HM_EINVAL;
+  }
+  const int32_t n = (int32_t)h->prof.size();
+  for (int32_t i = 0; i < n && i < cap; ++i) out[i] = h->prof[i];
+  *count = n;
+  return HM_OK;
+}
+
+hm_status hm_skeleton(const hm_handle* h, int64_t node, int32_t side, int64_t* idx, int32_t* k) {
+  clear_error();
+  if (!h || h->format != HM_FORMAT_HBSID || !h->skel || !idx || !k || node < 2 ||
+      node >= ((int64_t)1 << (h->L + 1)) || (side != 0 && side != 1)) {
+    set_error("hm_skeleton: need an HBS-ID handle, 2 <= node < 2^(L+1), side 0|1, idx, k");
+    return HM_EINVAL;
+  }
+  const int64_t nheap = (int64_t)1 << (h->L + 1);
+  const int32_t kk = side == 0 ? h->kin[node] : h->kout[node];
+  const int64_t* src = h->skel + (int64_t)side * nheap * h->r + node * h->r;
+  HM_CUDA_TRY(cudaMemcpy(idx, src, sizeof(int64_t) * (size_t)h->r, cudaMemcpyDeviceToHost));
+  for (int32_t a = kk; a < h->r; ++a) idx[a] = -1;
+  *k = kk;
+  return HM_OK;
+}
+
 void hm_destroy(hm_handle* h) {
   if (!h) return;
   if (h->U) cudaFree(h->U);
@@ -212,6 +247,7 @@ hm_status hm_hodlr_factored_apply(const hm_tree* tree, int32_t k, const float* U
     return HM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  HM_TRY(factored_check(tree, false));
   HM_TRY(tree_device(const_cast<hm_tree*>(tree), st));
   float* scratch = nullptr;
   const size_t sbytes = factored_scratch_bytes(tree, k);
@@ -231,6 +267,7 @@ hm_status hm_hodlr_factored_adjoint(const hm_tree* tree, int32_t k, const float*
     return HM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  HM_TRY(factored_check(tree, true));
   HM_TRY(tree_device(const_cast<hm_tree*>(tree), st));
   float* scratch = nullptr;
   const size_t sbytes = factored_scratch_bytes(tree, k);

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "hm_hbs.h"
@@ -143,30 +144,40 @@ hm_status compress_hbs_t(Ctx<T>& c, HbsState<T>& s, T* D) {
     const int lv = level + 1;
     const LevelPlan& lp = c.tree->plans[lv];
     const int pc = level == 0 ? r : 2 * r;
+    mark(c, level, 0, HM_PHASE_SAMPLE);
     launch_gauss_fill<T>(c.X, N, N, r, level, c.seed, bf16, c.tree->d_start, L, c.st);
     HM_TRY(box(c, 0, c.X, c.S, r));
     HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));
     nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+    mark(c, level, 0, HM_PHASE_PEEL);
     HM_TRY(hbs_partial_apply(s, level, c.X, N, c.S, N, 2 * r, 0, (T)-1, c.st));
     // Y_loc = [Y(I_a, sample half), U_tau(J_a,:) diag(y_tau)] -> [U_a, y_a] = svd(Y_loc, r)
+    mark(c, level, 0, HM_PHASE_BASES);
     launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
     if (level > 0)
       launch_gather_parent_scaled<T>(s.Ucur, N, c.P, N, N, r, lv, c.tree->d_start, s.y, r, c.st);
+    c.side = 0;
     HM_TRY(panel_svd(c, lv, c.P, pc, 2, r, false, Unext, false, c.rank_tmp));
+    mark(c, level, 0, HM_PHASE_BASES);
     launch_node_copy<T, T>(lp.nnodes, lp.node0, c.sig, pc, pc, s.y, r, r, r, 1, 0, c.st);
     if (level > 0)  // U_tau short halves: U_a^T U_tau(J_a, :)
       launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Unext, N, 0, 0, r,
                        s.Ucur, N, 0, 0, r, c.partial, s.UsH + lp.node0 * rr, c.st, s.df);
     launch_scatter_probe<T>(Unext, N, c.X, N, N, r, lv, c.tree->d_start, L, c.st);
+    mark(c, level, 1, HM_PHASE_SAMPLE);
     HM_TRY(box(c, 1, c.X, c.S, r));
     HM_TRY(box(c, 1, c.X + N * r, c.S + N * r, r));
     nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+    mark(c, level, 1, HM_PHASE_PEEL);
     HM_TRY(hbs_partial_apply(s, level, c.X, N, c.S, N, 2 * r, 1, (T)-1, c.st));
     // Z_loc -> [V_a, b, X] = svd(Z_loc, r); B_ba = X(1:r,:) diag(b) (R2-corrected)
+    mark(c, level, 1, HM_PHASE_BASES);
     launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
     if (level > 0)
       launch_gather_parent_scaled<T>(s.Vcur, N, c.P, N, N, r, lv, c.tree->d_start, s.z, r, c.st);
+    c.side = 1;
     HM_TRY(panel_svd(c, lv, c.P, pc, 2, r, false, Vnext, true, c.rank_tmp));
+    mark(c, level, 1, HM_PHASE_BASES);
     launch_node_copy<T, T>(lp.nnodes, lp.node0, c.sig, pc, pc, s.z, r, r, r, 1, 0, c.st);
     launch_node_copy<T, T>(lp.nnodes, lp.node0, c.M, (int64_t)pc * r, pc, s.Bm, rr, r, r, r, 1,
                            c.st);
@@ -178,9 +189,12 @@ hm_status compress_hbs_t(Ctx<T>& c, HbsState<T>& s, T* D) {
     c.launches += 12;
     HM_TRY(check_launch("hbs level"));
   }
+  mark(c, L, 0, HM_PHASE_SAMPLE);
   launch_identity_probe<T>(c.XI, N, N, nmax, c.tree->d_start, L, c.st);
   HM_TRY(box(c, 0, c.XI, c.YI, nmax));
+  mark(c, L, 0, HM_PHASE_PEEL);
   HM_TRY(hbs_partial_apply(s, L, c.XI, N, c.YI, N, nmax, 0, (T)-1, c.st));
+  mark(c, L, 0, HM_PHASE_BASES);
   launch_extract_diag<T>(c.YI, N, D, nmax, c.tree->d_start, c.tree->d_size, L, c.st);
   return check_launch("hbs diagonal");
 }
@@ -517,13 +531,16 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
+  c.profile = profiling_on();
   if (s == HM_OK) {
     cudaEventRecord(t0, st);
     s = compress_hbs_t<T>(c, hs, D);
     if (s == HM_OK) {
       // hbs_partial_apply swaps nothing; after the sweep Ucur/Vcur hold the leaf bases
+      mark(c, L, 0, HM_PHASE_ID);
       s = hbsid_sweep<T>(c, hs, D, h);
     }
+    mark(c, L, 0, -1);  // end of the last phase
     cudaEventRecord(t1, st);
   }
   if (s == HM_OK) {
@@ -533,6 +550,7 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
       s = HM_ECUDA;
     }
   }
+  if (s == HM_OK) s = dense_take_timeout(op);
   int32_t flags[4] = {0, 0, 0, 0};
   if (s == HM_OK) {
     cudaMemcpy(flags, c.flags_dev, sizeof(flags), cudaMemcpyDeviceToHost);
@@ -565,9 +583,15 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
     in.t_blackbox_ms = box_ms(c);
     in.launches = c.launches;
     in.eps_abs = 0.0;
+    if (o->strict_rank && in.saturated) {
+      set_error("hm_compress_hbs: " + std::to_string(in.saturated) +
+                " skeleton ranks reached r (raise r)");
+      s = HM_ERANK_SATURATED;
+    }
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
+  marks_finish(c, s == HM_OK ? h : nullptr);
   ctx_free(c);
   if (rank_block) cudaFree(rank_block);
   if (sblk) cudaFree(sblk);

@@ -12,6 +12,7 @@
 //   U_beta <- U_beta \hat U_beta B  (the sibling matrix is absorbed into U)
 // then the identity probe gives the leaf blocks D.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -24,6 +25,36 @@ using namespace hm;
 namespace hm {
 
 constexpr double kEpsScale = 0.1;  // eps_abs = 0.1 * tol * nu (tolerance reading)
+
+static std::atomic<int> g_profile{0};
+bool profiling_on() { return g_profile.load(std::memory_order_relaxed) != 0; }
+void set_profiling(int on) { g_profile.store(on ? 1 : 0, std::memory_order_relaxed); }
+
+template <typename T>
+void mark(Ctx<T>& c, int level, int side, int phase) {
+  if (!c.profile) return;
+  typename Ctx<T>::Mark m{level, side, phase, nullptr};
+  if (cudaEventCreate(&m.ev) != cudaSuccess) return;
+  cudaEventRecord(m.ev, c.st);
+  c.marks.push_back(m);
+}
+
+template <typename T>
+void marks_finish(Ctx<T>& c, hm_handle* h) {
+  for (size_t i = 0; i + 1 < c.marks.size(); ++i) {
+    float ms = 0.f;
+    if (h && cudaEventElapsedTime(&ms, c.marks[i].ev, c.marks[i + 1].ev) == cudaSuccess) {
+      hm_phase_t p;
+      p.level = c.marks[i].level;
+      p.side = c.marks[i].side;
+      p.phase = c.marks[i].phase;
+      p.ms = ms;
+      h->prof.push_back(p);
+    }
+  }
+  for (auto& m : c.marks) cudaEventDestroy(m.ev);
+  c.marks.clear();
+}
 
 template <typename T>
 hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols) {
@@ -82,9 +113,11 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
     set_error("panel too wide for the shared-memory QR in this precision");
     return HM_EUNSUPPORTED;
   }
+  mark(c, lv - 1, c.side, HM_PHASE_TSQR);
   for (size_t rd = 0; rd < lp.d_rounds.size(); ++rd)
     launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rd > 0 ? 1 : 0, P, N, pc,
                    c.Rw, c.st);
+  mark(c, lv - 1, c.side, HM_PHASE_SVD);
   launch_jacobi<T>(lp.d_final_slot, lp.nnodes, c.Rw, pc, c.W, c.sig, c.st);
   // Directions of the sample range below floor_rel * sigma_1 are dropped.  In
   // FP64 the floor sits well above rounding noise (1e-12): directions near the
@@ -97,6 +130,7 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
                                            : (mode == 1 ? 1.1102230246251565e-16 : 1e-12));
   launch_truncate<T>(lp.nnodes, c.W, c.sig, pc, r, mode, kfix, kEpsScale * c.tol, c.eps_dev,
                      set_eps ? 1 : 0, floor_rel, rank_lv, c.T1, c.flags_dev + 1, c.st);
+  mark(c, lv - 1, c.side, HM_PHASE_ORTH);
   launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, P, N, 0, 0, pc, c.T1, (int64_t)pc * r, pc, 0, Q,
                    N, 0, 0, r, (T)1, (T)0, c.st, c.bf16 && sizeof(T) == 8);
   launch_seg_tn<T>(lp.d_tn, lp.n_tn, lp.d_tn_begin, lp.nnodes, lp.node0, Q, N, 0, 0, r, Q, N, 0,
@@ -178,22 +212,31 @@ hm_status compress_hodlr_t(Ctx<T>& c, hm_handle* h) {
     T* Ulv = U + (int64_t)(lv - 1) * N * r;
     T* Vlv = V + (int64_t)(lv - 1) * N * r;
     int32_t* rank_lv = c.rank_dev + ((int64_t)1 << lv);
+    mark(c, level, 0, HM_PHASE_SAMPLE);
     launch_gauss_fill<T>(c.X, N, N, r, level, c.seed, bf16, c.tree->d_start, L, c.st);
     HM_TRY(box(c, 0, c.X, c.S, r));                      // Y_1 = A Omega_2
     HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));      // Y_2 = A Omega_1
     nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+    mark(c, level, 0, HM_PHASE_PEEL);
     HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 0, -1.0));
+    mark(c, level, 0, HM_PHASE_BASES);
     launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
+    c.side = 0;
     HM_TRY(panel_svd(c, lv, c.P, r, 0, 0, false, Ulv, false, c.rank_tmp));
+    mark(c, level, 1, HM_PHASE_SAMPLE);
     launch_scatter_probe<T>(Ulv, N, c.X, N, N, r, lv, c.tree->d_start, L, c.st);
     HM_TRY(box(c, 1, c.X, c.S, r));                      // Z_1 = A^T Omega_2
     HM_TRY(box(c, 1, c.X + N * r, c.S + N * r, r));      // Z_2 = A^T Omega_1
     nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+    mark(c, level, 1, HM_PHASE_PEEL);
     HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 1, -1.0));
+    mark(c, level, 1, HM_PHASE_BASES);
     launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
     const int mode = c.mode_tol ? 1 : 2;
+    c.side = 1;
     HM_TRY(panel_svd(c, lv, c.P, r, mode, c.kfix, level == 0, Vlv, true, rank_lv));
     // U_beta <- U_beta (W_k S_k R2^T) with the coefficients of the sibling's panel
+    mark(c, level, 1, HM_PHASE_BASES);
     const LevelPlan& lp = c.tree->plans[lv];
     launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Ulv, N, 0, 0, r, c.M, (int64_t)r * r, r, 1, Ulv,
                      N, 0, 0, r, (T)1, (T)0, c.st, c.bf16 && sizeof(T) == 8);
@@ -201,9 +244,12 @@ hm_status compress_hodlr_t(Ctx<T>& c, hm_handle* h) {
     HM_TRY(check_launch("hodlr level"));
   }
   // leaf blocks through the identity probe
+  mark(c, L, 0, HM_PHASE_SAMPLE);
   launch_identity_probe<T>(c.XI, N, N, nmax, c.tree->d_start, L, c.st);
   HM_TRY(box(c, 0, c.XI, c.YI, nmax));
+  mark(c, L, 0, HM_PHASE_PEEL);
   HM_TRY(hodlr_peel(c, U, V, L, c.XI, c.YI, nmax, 0, -1.0));
+  mark(c, L, 0, HM_PHASE_BASES);
   launch_extract_diag<T>(c.YI, N, (T*)h->D, nmax, c.tree->d_start, c.tree->d_size, L, c.st);
   c.launches += 2;
   return check_launch("hodlr diagonal");
@@ -343,12 +389,14 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
+  c.profile = profiling_on();
   if (s == HM_OK) {
     cudaMemsetAsync(h->U, 0, sizeof(T) * (size_t)tree->L * N * r, st);
     cudaMemsetAsync(h->V, 0, sizeof(T) * (size_t)tree->L * N * r, st);
     cudaMemsetAsync(rank_block, 0, sizeof(int32_t) * 2 * ((size_t)1 << (tree->L + 1)), st);
     cudaEventRecord(t0, st);
     s = compress_hodlr_t<T>(c, h);
+    mark(c, tree->L, 0, -1);  // end of the last phase
     cudaEventRecord(t1, st);
   }
   if (s == HM_OK) {
@@ -358,6 +406,9 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
       s = HM_ECUDA;
     }
   }
+  // a sampling GEMM whose bounded wait gave up wrote NaN: report the timeout
+  // itself rather than the non-finite samples it caused
+  if (s == HM_OK) s = dense_take_timeout(op);
   int32_t flags[4] = {0, 0, 0, 0};
   double eps[2] = {0, 0};
   if (s == HM_OK) {
@@ -402,6 +453,7 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
+  marks_finish(c, s == HM_OK ? h : nullptr);
   ctx_free(c);
   if (rank_block) cudaFree(rank_block);
   if (s != HM_OK) {
@@ -430,7 +482,9 @@ namespace hm {
                                   int32_t*);                                                \
   template hm_status ctx_alloc<T>(Ctx<T>&, int, int64_t);                                   \
   template void ctx_free<T>(Ctx<T>&);                                                       \
-  template double box_ms<T>(Ctx<T>&);
+  template double box_ms<T>(Ctx<T>&);                                                       \
+  template void mark<T>(Ctx<T>&, int, int, int);                                            \
+  template void marks_finish<T>(Ctx<T>&, hm_handle*);
 HM_INST(float)
 HM_INST(double)
 #undef HM_INST

@@ -17,7 +17,8 @@ constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 // Address of the buffer per device ordinal, looked up on the first call made
-// with that device current.
+// with that device current and kept for the life of the process (a
+// cudaDeviceReset of that device invalidates it).
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mutex;
 void* g_addr[kMaxDevices] = {};
@@ -36,10 +37,9 @@ extern "C" hm_status hm_hodlr_factored_apply_noalloc(const hm_tree* tree, int32_
   }
   // partial projections (one row of k per 256-row chunk of every node) and the
   // coefficients (k per node), as laid out by the shared launcher
+  // (hm_tree_create builds the chunk list, so n_fchunks is exact here)
   const size_t nodes = (size_t)1 << (tree->L + 1);
-  const size_t chunks = tree->fchunks.empty() ? (size_t)tree->L * (size_t)((tree->n + 255) / 256) +
-                                                    nodes
-                                              : (size_t)tree->n_fchunks;
+  const size_t chunks = (size_t)tree->n_fchunks;
   const size_t need = sizeof(float) * (chunks * (size_t)k + nodes * (size_t)k);
   if (need > kNoallocScratchBytes) {
     set_error("hm_hodlr_factored_apply_noalloc: this tree and k need " + std::to_string(need) +
@@ -60,6 +60,12 @@ extern "C" hm_status hm_hodlr_factored_apply_noalloc(const hm_tree* tree, int32_
     set_error("hm_hodlr_factored_apply_noalloc: device ordinal out of range");
     return HM_EINVAL;
   }
+  if (tree->dev != dev) {
+    set_error("hm_hodlr_factored_apply_noalloc: the tree's index tables were uploaded to device " +
+              std::to_string(tree->dev) + ", but device " + std::to_string(dev) + " is current");
+    return HM_EINVAL;
+  }
+  HM_TRY(factored_check(tree, false));
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_addr_mutex);

@@ -31,7 +31,25 @@ struct Ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> box_events;
   int64_t cols_A = 0, cols_At = 0;
   int launches = 0;
+  // phase profile (hm_set_profiling): one event at the start of every phase
+  struct Mark {
+    int level, side, phase;
+    cudaEvent_t ev;
+  };
+  bool profile = false;
+  int side = 0;  // side of the panel being factored (0: A samples, 1: A^T samples)
+  std::vector<Mark> marks;
 };
+
+// Records the start of a phase on the compression's stream (no-op unless
+// profiling is on).  Phases are the HM_PHASE_* values of hm.h.
+template <typename T>
+void mark(Ctx<T>& c, int level, int side, int phase);
+// Turns the marks into (level, side, phase, ms) segments on the handle and
+// destroys the events; the stream has been synchronized.
+template <typename T>
+void marks_finish(Ctx<T>& c, hm_handle* h);
+bool profiling_on();
 
 template <typename T>
 hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols);

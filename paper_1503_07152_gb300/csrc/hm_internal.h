@@ -33,6 +33,12 @@ void clear_error();
   } while (0)
 
 hm_status check_launch(const char* what);
+// Poll limit of the tensor-core GEMMs' pipeline waits (hm_set_wait_limit).
+long long wait_limit();
+// For a black box made by hm_dense_operator_create: reads and clears the flag
+// its GEMMs raise when a bounded wait gave up (HM_ETIMEOUT if it was set).
+// Other black boxes: HM_OK.  Synchronous (the caller has synchronized).
+hm_status dense_take_timeout(const hm_operator* op);
 // Process-wide count of kernels launched by the library (all devices).
 void count_launches(int n);
 
@@ -206,6 +212,9 @@ struct FactChunk {
 struct hm_tree;
 namespace hm {
 size_t factored_scratch_bytes(const hm_tree* t, int k);
+// Checks that the per-leaf kernels' shared memory fits the device (HM_EINVAL
+// naming the sizes otherwise) and raises their limit once per device.
+hm_status factored_check(const hm_tree* t, bool adjoint);
 void launch_factored_apply(const hm_tree* t, int k, const float* U, const float* V,
                            const float* D, int trans, const float* x, float* y, float* scratch,
                            cudaStream_t st);
@@ -246,6 +255,7 @@ struct hm_tree {
   int64_t* d_start = nullptr;        // device copies
   int64_t* d_size = nullptr;
   int64_t nmax = 0;
+  int32_t dev = -1;                  // device the tables were uploaded to
   std::vector<hm::LevelPlan> plans;  // index = node level (1..L)
   // 256-row chunks of every node of levels 1..L, level-major (heap-id order),
   // and the first chunk of every heap id (fbegin[2^(L+1)] = n_fchunks)
@@ -289,4 +299,5 @@ struct hm_handle {
   std::vector<int64_t> iin_off, iout_off;            // skeleton index offsets
   int64_t* skel = nullptr;                           // device skeleton indices
   hm_info_t info{};
+  std::vector<hm_phase_t> prof;                      // phase profile (hm_profile)
 };

@@ -10,6 +10,7 @@
 // its L ancestors' siblings (ancestor of leaf l on level j = l >> (L - j)) and
 // of the leaf block D, and, for the adjoint, writes the gradient rows.
 #include <atomic>
+#include <string>
 
 #include "hm_internal.h"
 
@@ -196,6 +197,14 @@ __global__ __launch_bounds__(256) void k_fact_adjoint(
         gDl[i + (int64_t)m * nmax] = (m < ns) ? scale * rr * xs[m] : 0.f;
     }
   }
+  // rows past the leaf's size (a leaf smaller than n_max): zero, so that the
+  // whole n_max x n_max block of every leaf is written
+  if (gD && ns < nmax) {
+    float* gDl = gD + (int64_t)blockIdx.x * nmax * nmax;
+    const int pad = nmax - ns;
+    for (int e = tid; e < pad * nmax; e += blockDim.x)
+      gDl[ns + e % pad + (int64_t)(e / pad) * nmax] = 0.f;
+  }
 }
 
 }  // namespace
@@ -205,6 +214,31 @@ static size_t fact_partial_smem(int k) {
   static std::atomic<uint32_t> done{0};
   raise_smem_limit((const void*)k_fact_partial, done);
   return sizeof(float) * 256 * (size_t)(k + 1);
+}
+
+// dynamic shared memory of the per-leaf kernels: the sibling coefficients of
+// every level plus the leaf's slices of x (and res, D^T res); grows with n_max
+static size_t fact_leaf_smem(const hm_tree* t, bool adjoint) {
+  const size_t nmax = (size_t)t->nmax, L = (size_t)t->L;
+  return adjoint ? sizeof(float) * (2 * L * kMaxK + 3 * nmax)
+                 : sizeof(float) * (L * kMaxK + 2 * nmax);
+}
+
+hm_status factored_check(const hm_tree* t, bool adjoint) {
+  int dev = 0, optin = 0;
+  HM_CUDA_TRY(cudaGetDevice(&dev));
+  HM_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t need = fact_leaf_smem(t, adjoint);
+  if (need > (size_t)optin) {
+    set_error(std::string(adjoint ? "hm_hodlr_factored_adjoint" : "hm_hodlr_factored_apply") +
+              ": leaves of " + std::to_string(t->nmax) + " points need " + std::to_string(need) +
+              " bytes of shared memory per block; the device allows " + std::to_string(optin));
+    return HM_EINVAL;
+  }
+  static std::atomic<uint32_t> done_e{0}, done_a{0};
+  if (adjoint) raise_smem_limit((const void*)k_fact_adjoint, done_a);
+  else raise_smem_limit((const void*)k_fact_expand, done_e);
+  return HM_OK;
 }
 
 size_t factored_scratch_bytes(const hm_tree* t, int k) {
@@ -225,7 +259,7 @@ void launch_factored_apply(const hm_tree* t, int k, const float* U, const float*
                                                 nullptr, partial);
   k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, k, nodes, coef);
   const int nmax = (int)t->nmax;
-  const size_t smem = sizeof(float) * (L * kMaxK + 2 * nmax);
+  const size_t smem = fact_leaf_smem(t, false);
   k_fact_expand<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, k,
                                            trans ? V : U, coef, D, trans, x, y);
 }
@@ -242,7 +276,7 @@ void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const floa
   k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, V, x, U, res, partial);
   k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, 2 * k, nodes, coef);
   const int nmax = (int)t->nmax;
-  const size_t smem = sizeof(float) * (2 * L * kMaxK + 3 * nmax);
+  const size_t smem = fact_leaf_smem(t, true);
   k_fact_adjoint<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, U, V, D,
                                             coef, x, res, scale, gx, gU, gV, gD);
 }

@@ -39,9 +39,11 @@
 //   warps 9-16: drain once per window (two warps per TMEM lane quarter, 32
 //     columns each) and write Y.
 // All-zero K tiles of X are skipped; the four X slices of an active tile are
-// always loaded (a zero slice contributes zeros).  Every mbarrier wait is bounded; on
-// timeout the block raises the error flag, writes NaN, lets its own TMA copies
-// land and leaves; TMEM is released unless the wait for its MMAs timed out.
+// always loaded (a zero slice contributes zeros).  Every mbarrier wait is bounded
+// (the pipeline waits by the limit the host sets, hm_set_wait_limit); on timeout
+// the block raises the error flag, writes NaN, lets its own TMA copies land and
+// its issued MMAs complete (waits of the full limit) and leaves; TMEM is
+// released unless even the full-limit wait for its MMAs ran out.
 #include <algorithm>
 #include <atomic>
 
@@ -173,7 +175,8 @@ template <int TRANS>
 __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int64_t n,
     int64_t ncols, const uint8_t* __restrict__ flags, const int* __restrict__ ex,
-    const int* __restrict__ e_rows, double* __restrict__ Y, int64_t ldy, int* __restrict__ err) {
+      const int* __restrict__ e_rows, double* __restrict__ Y, int64_t ldy, int* __restrict__ err,
+    long long poll_limit) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t raw_full, raw_empty, st_full[SSTAGES], x_full[SSTAGES],
       st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final, bar_chain;
@@ -274,7 +277,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       int it = 0;
       for (int kt = 0; kt < nkt; ++kt) {
         if (!active(kt)) continue;
-        if (!mbar_wait(smem_u32(&raw_empty), (it & 1) ^ 1, &abort_flag)) break;
+        if (!mbar_wait(smem_u32(&raw_empty), (it & 1) ^ 1, &abort_flag, poll_limit)) break;
         mbar_arrive_tx(smem_u32(&raw_full), RAW_BYTES);
         if (!TRANS)
           tma_load_2d(raw_addr, &tmA, kt * TK, (int)m0, smem_u32(&raw_full));
@@ -291,7 +294,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       const int fl = active(kt);
       if (!fl) continue;
       const int s = it % SSTAGES;
-      if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag)) break;
+      if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag, poll_limit)) break;
       const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
       if (tid == 0) {
         mbar_arrive_tx(smem_u32(&x_full[s]), (uint32_t)(NSL * B_SLICE));
@@ -300,7 +303,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
                       smem_u32(&x_full[s]));
         xissued = it + 1;
       }
-      if (!mbar_wait(smem_u32(&raw_full), it & 1, &abort_flag)) break;
+      if (!mbar_wait(smem_u32(&raw_full), it & 1, &abort_flag, poll_limit)) break;
       const unsigned char* rw = sbase;  // the raw stage sits at the aligned base
       unsigned char* sp = sbase + (st - base);
       int bad = 0;
@@ -383,15 +386,15 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
             ++wc;
           }
           cur = w;
-          ok = mbar_wait(smem_u32(&acc_empty[wc & 1]), ((wc >> 1) & 1) ^ 1, &abort_flag);
+          ok = mbar_wait(smem_u32(&acc_empty[wc & 1]), ((wc >> 1) & 1) ^ 1, &abort_flag, poll_limit);
           if (!ok) break;
           dbase = tmem + (uint32_t)((wc & 1) * 4 * TN);
           started = 0;
           pos = 0;
         }
         const int s = it % SSTAGES;
-        ok = mbar_wait(smem_u32(&st_full[s]), (it / SSTAGES) & 1, &abort_flag) &&
-             mbar_wait(smem_u32(&x_full[s]), (it / SSTAGES) & 1, &abort_flag);
+        ok = mbar_wait(smem_u32(&st_full[s]), (it / SSTAGES) & 1, &abort_flag, poll_limit) &&
+             mbar_wait(smem_u32(&x_full[s]), (it / SSTAGES) & 1, &abort_flag, poll_limit);
         if (!ok) break;
         tc_fence_after();
         const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
@@ -401,7 +404,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
           const int sa = (pos & 1) ? NSL - 1 - c : c;
           if (c > 0) {  // the previous chain had another shape: let it complete
             mma_commit(smem_u32(&bar_chain));
-            ok = mbar_wait(smem_u32(&bar_chain), chain_ph, &abort_flag);
+            ok = mbar_wait(smem_u32(&bar_chain), chain_ph, &abort_flag, poll_limit);
             chain_ph ^= 1;
             if (!ok) break;
           }
@@ -420,8 +423,11 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
         ++it;
       }
       if (ok && cur >= 0) mma_commit(smem_u32(&acc_full[wc & 1]));
+      // every MMA issued by this thread completes before TMEM is released: this
+      // wait ignores the other roles' abort and takes the full limit; only if
+      // even that runs out is TMEM left allocated (the error flag reports it)
       mma_commit(smem_u32(&bar_final));
-      if (!mbar_wait(smem_u32(&bar_final), 0, &abort_flag)) abort_flag = 2;
+      if (!mbar_wait_drain(smem_u32(&bar_final), 0)) abort_flag = 2;
     }
   } else {
     // ---------------------------------------------------------- drain / epilogue
@@ -441,7 +447,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       if (!any) continue;
       const int b = wc & 1;
       const int exl = ex[((int64_t)w * nct + ct) * TN + half * 32 + lane];  // column lane
-      if (!mbar_wait(smem_u32(&acc_full[b]), (wc >> 1) & 1, &abort_flag)) break;
+      if (!mbar_wait(smem_u32(&acc_full[b]), (wc >> 1) & 1, &abort_flag, poll_limit)) break;
       tc_fence_after();
       const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 4 * TN + half * 32);
 #pragma unroll
@@ -582,11 +588,11 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
   if (trans) {
     raise_smem_limit((const void*)k_gemm_esg<1>, done[1]);
     k_gemm_esg<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
-                                                err);
+                                                err, wait_limit());
   } else {
     raise_smem_limit((const void*)k_gemm_esg<0>, done[0]);
     k_gemm_esg<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
-                                                err);
+                                                err, wait_limit());
   }
   return 0;
 }

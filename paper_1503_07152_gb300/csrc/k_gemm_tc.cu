@@ -113,7 +113,7 @@ template <int TRANS>
 __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_tc(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int64_t n,
     int64_t ncols, const uint8_t* __restrict__ flags, float* __restrict__ Y, int64_t ldy,
-    int* __restrict__ err) {
+    int* __restrict__ err, long long poll_limit) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t raw_full[MAX_RAW], raw_empty[MAX_RAW], st_full[SSTAGES],
       x_full[SSTAGES], st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final;
@@ -173,7 +173,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_tc(
       for (int kt = 0; kt < nkt; ++kt) {
         if (!active(kt)) continue;
         const int rs = it % nraw;
-        if (!mbar_wait(smem_u32(&raw_empty[rs]), ((it / nraw) & 1) ^ 1, &abort_flag)) break;
+        if (!mbar_wait(smem_u32(&raw_empty[rs]), ((it / nraw) & 1) ^ 1, &abort_flag, poll_limit)) break;
         mbar_arrive_tx(smem_u32(&raw_full[rs]), RAW_BYTES);
         const int k0 = kt * TK;
         if (!TRANS)
@@ -193,7 +193,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_tc(
       const int fl = active(kt);
       if (!fl) continue;
       const int rs = it % nraw, s = it % SSTAGES;
-      if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag)) break;
+      if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag, poll_limit)) break;
       const uint32_t st = stage_addr0 + (uint32_t)s * stage_bytes;
       if (tid == 0) {
         const uint32_t nsl = (uint32_t)__popc(fl & 7);
@@ -204,7 +204,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_tc(
                         smem_u32(&x_full[s]));
         xissued = it + 1;
       }
-      if (!mbar_wait(smem_u32(&raw_full[rs]), (it / nraw) & 1, &abort_flag)) break;
+      if (!mbar_wait(smem_u32(&raw_full[rs]), (it / nraw) & 1, &abort_flag, poll_limit)) break;
       const unsigned char* rw = sbase + (size_t)(raw_addr0 - base) + (size_t)rs * RAW_BYTES;
       unsigned char* sp = sbase + (st - base);
       if (!TRANS) {
@@ -257,9 +257,9 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_tc(
         const int fl = active(kt);
         if (!fl) continue;
         const int b = it & 1, s = it % SSTAGES;
-        ok = mbar_wait(smem_u32(&acc_empty[b]), ((it >> 1) & 1) ^ 1, &abort_flag) &&
-             mbar_wait(smem_u32(&st_full[s]), (it / SSTAGES) & 1, &abort_flag) &&
-             mbar_wait(smem_u32(&x_full[s]), (it / SSTAGES) & 1, &abort_flag);
+        ok = mbar_wait(smem_u32(&acc_empty[b]), ((it >> 1) & 1) ^ 1, &abort_flag, poll_limit) &&
+             mbar_wait(smem_u32(&st_full[s]), (it / SSTAGES) & 1, &abort_flag, poll_limit) &&
+             mbar_wait(smem_u32(&x_full[s]), (it / SSTAGES) & 1, &abort_flag, poll_limit);
         if (!ok) break;
         tc_fence_after();
         const uint32_t st = stage_addr0 + (uint32_t)s * stage_bytes;
@@ -289,9 +289,10 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_tc(
       }
       // every MMA issued by this thread has completed before TMEM can be released
       mma_commit(smem_u32(&bar_final));
-      if (!mbar_wait(smem_u32(&bar_final), 0, &abort_flag)) {
-        // the wait itself gave up: leave TMEM allocated rather than free it under
-        // running MMAs (the error flag reports the block)
+      if (!mbar_wait_drain(smem_u32(&bar_final), 0)) {
+        // even the full-limit wait (which ignores the other roles' abort) gave
+        // up: leave TMEM allocated rather than free it under running MMAs (the
+        // error flag reports the block)
         abort_flag = 2;
       }
     }
@@ -309,7 +310,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_tc(
       const int fl = active(kt);
       if (!fl) continue;
       const int b = it & 1;
-      if (!mbar_wait(smem_u32(&acc_full[b]), (it >> 1) & 1, &abort_flag)) break;
+      if (!mbar_wait(smem_u32(&acc_full[b]), (it >> 1) & 1, &abort_flag, poll_limit)) break;
       tc_fence_after();
       const uint32_t t_lane = (uint32_t)(q4 * 32) << 16;
       const uint32_t t_lead = tmem + t_lane + (uint32_t)(b * 2 * TN), t_corr = t_lead + TN;
@@ -427,10 +428,10 @@ int launch_gemm_tc(const float* A, int64_t lda, int trans, int64_t n, int64_t nc
   dim3 grid((unsigned)nct, (unsigned)((n + TM - 1) / TM));
   if (trans) {
     raise_smem_limit((const void*)k_gemm_tc<1>, done[1]);
-    k_gemm_tc<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, Y, ldy, err);
+    k_gemm_tc<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, Y, ldy, err, wait_limit());
   } else {
     raise_smem_limit((const void*)k_gemm_tc<0>, done[0]);
-    k_gemm_tc<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, Y, ldy, err);
+    k_gemm_tc<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, Y, ldy, err, wait_limit());
   }
   return 0;
 }

@@ -32,20 +32,24 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false on timeout (or when another role already gave up)
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort) {
-  for (long long i = 0; i < kMaxPolls; ++i) {
+// bounded wait of the pipeline roles: false after `limit` polls (the limit the
+// host set, hm_set_wait_limit) or when another role already gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort,
+                                          long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(a, parity)) return true;
     if ((i & 1023) == 1023 && *abort) return false;
   }
   *abort = 1;
   return false;
 }
-// bounded wait that ignores the abort flag: used on the way out, to let the
-// block's own TMA copies land before its shared memory is given up
-__device__ __forceinline__ void mbar_wait_drain(uint32_t a, uint32_t parity) {
+// bounded wait that ignores the abort flag and always allows the full
+// kMaxPolls: used on the way out, to let the block's own TMA copies land before
+// its shared memory is given up and its MMAs complete before TMEM is released
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t a, uint32_t parity) {
   for (long long i = 0; i < kMaxPolls; ++i)
-    if (mbar_try(a, parity)) return;
+    if (mbar_try(a, parity)) return true;
+  return false;
 }
 __device__ __forceinline__ void mbar_arrive_tx(uint32_t a, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)

@@ -112,6 +112,10 @@ def test_hbsid_log_kernel(prec):
         assert e_gpu < 1e-7
         assert e_par < 1e-12
         assert np.array_equal(k_gpu, k_or)
+        # skeleton index sets (Sec. 4.3), in pivot order, bit for bit
+        for tau in nodes:
+            assert hm.hm_skeleton(h, tau, 0) == [int(v) for v in g.Iin[tau]], tau
+            assert hm.hm_skeleton(h, tau, 1) == [int(v) for v in g.Iout[tau]], tau
 
 
 def test_hbsid_log_kernel_mixed_bound():
@@ -140,3 +144,33 @@ def test_hbsid_apply_transpose():
         torch.cuda.synchronize()
         want = (Ag.T if trans else Ag) @ X
         assert np.linalg.norm(Y.cpu().numpy().T - want) <= 1e-12 * np.linalg.norm(want)
+
+
+def test_phase_profile_covers_the_compression():
+    """hm_set_profiling: the per-level, per-phase segments of a compression add up
+    to its device time, and every level and side has sample, peel and factor
+    phases (Sec. 5 splits T_compress into the black box and T_net)."""
+    N, m = 2048, 128
+    A = W.log_kernel(N)
+    At = torch.from_numpy(A).to(DEV)
+    op = hm.hm_dense_operator_create(At, fp64_blocks=True, tensor_cores=True)
+    t = hm.Tree(N, m)
+    hm.hm_set_profiling(True)
+    try:
+        h = hm.hm_compress_hbs(op, t, tol=1e-7, r=40, seed=2, prec=hm.HM_A32, hbs_id=1)
+    finally:
+        hm.hm_set_profiling(False)
+    segs = hm.hm_profile(h)
+    total = sum(s_["ms"] for s_ in segs)
+    assert abs(total - h.info["t_compress_ms"]) <= 0.05 * h.info["t_compress_ms"] + 0.5
+    L = t.levels
+    for level in range(L):
+        for side in (0, 1):
+            ph = {s_["phase"] for s_ in segs if s_["level"] == level and s_["side"] == side}
+            assert {"sample", "peel", "tsqr", "svd", "orth"} <= ph, (level, side, ph)
+    assert any(s_["phase"] == "id" for s_ in segs)
+    # the black-box share agrees with the library's own black-box timer
+    samp = sum(s_["ms"] for s_ in segs if s_["phase"] == "sample")
+    assert samp >= 0.9 * h.info["t_blackbox_ms"]
+    h2 = hm.hm_compress_hbs(op, t, tol=1e-7, r=40, seed=2, prec=hm.HM_A32, hbs_id=1)
+    assert hm.hm_profile(h2) == []

@@ -1,0 +1,85 @@
+"""GPU parity at the shapes of the measured HBS-ID workload (leaves 256, r = 60,
+tol 1e-7, HM_A32) on the N = 8192 log kernel, where the FP64 oracle still runs
+in seconds (Sec. 4.2 compression, Sec. 4.3 HBS-ID conversion).
+
+* CUDA-core black box (exact FP64 products of the FP32 operator): the
+  reconstruction agrees with the oracle's element by element to 1e-12 of ||A||,
+  every node's skeleton rank equals the oracle's, and every skeleton index set
+  equals the oracle's bit for bit, in pivot order.
+* Tensor-core black box (the split products the bench times): the
+  reconstruction is within 1e-7 of the oracle's; the number of nodes whose rank
+  differs from the oracle's is reported (the split products differ from exact
+  FP64 products by ~1e-8 relative, which may move a near-threshold decision).
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import hbs as ohbs
+from oracle import hodlr as ohodlr
+from oracle.tree import build_tree
+
+pytestmark = pytest.mark.gpu
+hm = pytest.importorskip("paper_1503_07152_gb300")
+DEV = "cuda:0"
+N, M, R, TOL, SEED = 8192, 256, 60, 1e-7, 2
+
+
+@pytest.fixture(scope="module")
+def oracle_result():
+    A = W.log_kernel(N)
+    A64 = A.astype(np.float64)
+    o = ohbs.compress(ohodlr.dense_apply_fn(A64), build_tree(N, M), r=R, seed=SEED, mixed=True,
+                      floor=True)
+    g = ohbs.to_hbsid(o, tol=TOL)
+    return A, A64, g, ohbs.hbsid_dense(g)
+
+
+def _gpu(A, tensor_cores):
+    At = torch.from_numpy(A).to(DEV)
+    op = hm.hm_dense_operator_create(At, fp64_blocks=True, tensor_cores=tensor_cores)
+    h = hm.hm_compress_hbs(op, hm.Tree(N, M), tol=TOL, r=R, seed=SEED, prec=hm.HM_A32, hbs_id=1)
+    out = torch.empty((N, N), device=DEV, dtype=torch.float64)
+    hm.hm_reconstruct_block(h, 0, N, 0, N, out)
+    torch.cuda.synchronize()
+    return h, out.cpu().numpy().T
+
+
+def _ranks(h, g):
+    nodes = list(range(2, 2 ** (build_tree(N, M).L + 1)))
+    k_gpu = np.array([hm.hm_node_rank(h, tau) for tau in nodes])
+    k_or = np.array([len(g.Iin[tau]) for tau in nodes])
+    return nodes, k_gpu, k_or
+
+
+def test_headline_shapes_exact_products(oracle_result):
+    A, A64, g, Ao = oracle_result
+    h, Ag = _gpu(A, tensor_cores=False)
+    nA = np.linalg.norm(A64)
+    e_par = np.linalg.norm(Ag - Ao) / nA
+    e_gpu = np.linalg.norm(Ag - A64) / nA
+    nodes, k_gpu, k_or = _ranks(h, g)
+    print(f"N={N} leaves {M} r={R}: GPU err {e_gpu:.3e}, vs oracle {e_par:.3e}, ranks "
+          f"{h.info['min_rank']}..{h.info['max_rank']}")
+    assert h.info["saturated"] == 0
+    assert e_gpu <= TOL
+    assert e_par <= 1e-12
+    assert np.array_equal(k_gpu, k_or)
+    for tau in nodes:
+        assert hm.hm_skeleton(h, tau, 0) == [int(v) for v in g.Iin[tau]], tau
+        assert hm.hm_skeleton(h, tau, 1) == [int(v) for v in g.Iout[tau]], tau
+
+
+def test_headline_shapes_tensor_core_products(oracle_result):
+    A, A64, g, Ao = oracle_result
+    h, Ag = _gpu(A, tensor_cores=True)
+    nA = np.linalg.norm(A64)
+    e_par = np.linalg.norm(Ag - Ao) / nA
+    e_gpu = np.linalg.norm(Ag - A64) / nA
+    nodes, k_gpu, k_or = _ranks(h, g)
+    mism = int(np.count_nonzero(k_gpu != k_or))
+    print(f"N={N} tensor-core black box: GPU err {e_gpu:.3e}, vs oracle {e_par:.3e}, rank "
+          f"mismatches {mism}/{len(nodes)}")
+    assert e_gpu <= TOL
+    assert e_par <= TOL

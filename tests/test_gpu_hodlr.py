@@ -190,7 +190,7 @@ def test_factored_apply_and_adjoint(N, m, k):
     assert np.linalg.norm(y.cpu().numpy() - want) <= 1e-5 * np.linalg.norm(want)
     assert np.linalg.norm(yt.cpu().numpy() - wantt) <= 1e-5 * np.linalg.norm(wantt)
     res = y - torch.from_numpy(b).to(DEV)
-    gx, gU, gV, gD = (torch.empty_like(a) for a in (xd, U, V, D))
+    gx, gU, gV, gD = (torch.full_like(a, float("nan")) for a in (xd, U, V, D))
     hm.hm_hodlr_factored_adjoint(t, k, U, V, D, xd, res, 2.0, gx, gU, gV, gD)
     torch.cuda.synchronize()
     dx, dU, dV, dD = ograd.gradients(f, x.astype(np.float64), b.astype(np.float64))
@@ -199,9 +199,12 @@ def test_factored_apply_and_adjoint(N, m, k):
     for j in range(1, L + 1):
         assert rel(gU[j - 1].cpu().numpy().T, dU[j]) < 1e-5
         assert rel(gV[j - 1].cpu().numpy().T, dV[j]) < 1e-5
+    gDh = gD.cpu().numpy()
     for i, d in enumerate(dD):
         n = d.shape[0]
-        assert rel(gD[i, :n, :n].cpu().numpy().T, d) < 1e-5
+        assert rel(gDh[i, :n, :n].T, d) < 1e-5
+        # the padding of a leaf smaller than n_max is written as zero (uneven leaves at N=3000)
+        assert np.all(gDh[i, n:, :] == 0.0) and np.all(gDh[i, :, n:] == 0.0)
 
 
 def test_autograd_function_matches_adjoint():
@@ -218,8 +221,14 @@ def test_autograd_function_matches_adjoint():
     loss = ((y - b) ** 2).sum()
     loss.backward()
     dx, dU, dV, dD = ograd.gradients(f, x.detach().cpu().double().numpy(), b.cpu().double().numpy())
-    assert np.linalg.norm(x.grad.cpu().numpy() - dx) <= 1e-5 * np.linalg.norm(dx)
-    assert np.linalg.norm(U.grad[0].cpu().numpy().T - dU[1]) <= 1e-5 * np.linalg.norm(dU[1])
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)  # noqa: E731
+    assert rel(x.grad.cpu().numpy(), dx) <= 1e-5
+    for j in range(1, L + 1):
+        assert rel(U.grad[j - 1].cpu().numpy().T, dU[j]) <= 1e-5
+        assert rel(V.grad[j - 1].cpu().numpy().T, dV[j]) <= 1e-5
+    gD = D.grad.cpu().numpy()
+    for i, d in enumerate(dD):
+        assert rel(gD[i].T, d) <= 1e-5
 
 
 @pytest.mark.parametrize("N,m", [(2048, 128), (3000, 100)])

@@ -107,3 +107,33 @@ def test_singular_vector_sign_convention_closed_form():
     rows = np.arange(Vtf.shape[0])
     assert np.all(Vtf[rows, np.argmax(np.abs(Vtf), axis=1)] > 0)
     assert np.allclose(Uf @ np.diag(sb) @ Vtf, B, atol=1e-13)
+
+
+def test_svd_r_floor_zeroes_rounding_level_directions():
+    """hbs._svd_r(floor=True), the significant-range reading of svd(., r): a
+    closed-form matrix with singular values 3, 1e-11 and 1e-14 (orthonormal
+    factors built from Householder reflections) keeps the first two triplets
+    (1e-11 > 1e-12 sigma_1) and returns the third as zero columns with a zero
+    singular value; without the floor all three come back."""
+    from oracle.hbs import _svd_r
+
+    rng = np.random.default_rng(17)
+
+    def reflector(n):
+        v = rng.standard_normal(n)
+        return np.eye(n) - 2.0 * np.outer(v, v) / (v @ v)
+
+    Uf, Vf = reflector(9)[:, :3], reflector(5)[:, :3]
+    s = np.array([3.0, 1e-11, 1e-14])
+    M = (Uf * s) @ Vf.T
+    U, sv, V = _svd_r(M, 3, floor=True)
+    assert sv[0] == pytest.approx(3.0, rel=1e-14)
+    assert sv[1] == pytest.approx(1e-11, rel=1e-3)
+    assert sv[2] == 0.0
+    assert np.all(U[:, 2] == 0.0) and np.all(V[:, 2] == 0.0)
+    for j in range(2):  # kept triplets: the closed-form ones up to sign
+        sg = np.sign(U[:, j] @ Uf[:, j])
+        assert np.allclose(U[:, j], sg * Uf[:, j], atol=1e-4 if j else 1e-14)
+        assert np.allclose(V[:, j], sg * Vf[:, j], atol=1e-4 if j else 1e-14)
+    U2, sv2, V2 = _svd_r(M, 3, floor=False)
+    assert sv2[2] > 0.0 and np.linalg.norm(U2[:, 2]) == pytest.approx(1.0)
