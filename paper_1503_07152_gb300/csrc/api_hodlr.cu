@@ -118,7 +118,11 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
     launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rd > 0 ? 1 : 0, P, N, pc,
                    c.Rw, c.st);
   mark(c, lv - 1, c.side, HM_PHASE_SVD);
-  launch_jacobi<T>(lp.d_final_slot, lp.nnodes, c.Rw, pc, c.W, c.sig, c.st);
+  if (sizeof(T) == 8 && c.bf16)  // HM_A32: the FP64 phases in double-float
+    launch_jacobi_df(lp.d_final_slot, lp.nnodes, (const double*)c.Rw, pc, (double*)c.W,
+                     (double*)c.sig, c.st);
+  else
+    launch_jacobi<T>(lp.d_final_slot, lp.nnodes, c.Rw, pc, c.W, c.sig, c.st);
   // Directions of the sample range below floor_rel * sigma_1 are dropped.  In
   // FP64 the floor sits well above rounding noise (1e-12): directions near the
   // noise level are arbitrary functions of the rounding and would capture an

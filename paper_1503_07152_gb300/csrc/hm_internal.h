@@ -139,6 +139,11 @@ template <typename T>
 void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W, T* sigma,
                    cudaStream_t st);
 
+// The FP64-accurate SVD of k_jacobi_mp with its FP64 phases in double-float
+// (HM_A32): same outputs, ~2^-46 relative accuracy.
+void launch_jacobi_df(const int32_t* node_slot, int nnodes, const double* R, int c, double* W,
+                      double* sigma, cudaStream_t st);
+
 // Rank decision + T1 = W(:, :k) diag(1/sigma) (c x kcap, zero padded).
 // mode 0: numerical range (sigma > floor * sigma1), at most kcap.
 // mode 1: tolerance (sigma > eps_abs, with eps_abs computed at the first level

@@ -1,0 +1,516 @@
+// FP64-accurate SVD of the panels' R factors in double-float arithmetic
+// (HM_A32): the phases of k_jacobi_mp (k_qr.cu) with every bulk FP64 operation
+// carried by float pairs on the FP32 pipe, which GB300 runs at many times its
+// FP64 rate.  Inputs and outputs stay FP64.
+#include <atomic>
+
+#include "df.cuh"
+#include "hm_internal.h"
+
+namespace hm {
+namespace {
+
+// (xh, xl) <- c x - s y and (yh, yl) <- s x + c y for DF c, s, x, y: the leading
+// products exactly by TwoProduct, the cross terms in FP32, one TwoSum and a
+// renormalization per output.
+__device__ __forceinline__ void rot_df(float ch, float cl, float sh, float sl, float& xh, float& xl,
+                                       float& yh, float& yl) {
+  const float x0 = xh, x1 = xl, y0 = yh, y1 = yl;
+  {
+    const float p1 = ch * x0, p2 = sh * y0;
+    const float e1 = fmaf(ch, x0, -p1), e2 = fmaf(sh, y0, -p2);
+    float r, e3;
+    df::two_sum(p1, -p2, r, e3);
+    float lo = (e1 - e2) + e3;
+    lo = fmaf(ch, x1, fmaf(cl, x0, lo));
+    lo = fmaf(-sh, y1, fmaf(-sl, y0, lo));
+    df::fast_two_sum(r, lo, xh, xl);
+  }
+  {
+    const float p1 = sh * x0, p2 = ch * y0;
+    const float e1 = fmaf(sh, x0, -p1), e2 = fmaf(ch, y0, -p2);
+    float r, e3;
+    df::two_sum(p1, p2, r, e3);
+    float lo = (e1 + e2) + e3;
+    lo = fmaf(sh, x1, fmaf(sl, x0, lo));
+    lo = fmaf(ch, y1, fmaf(cl, y0, lo));
+    df::fast_two_sum(r, lo, yh, yl);
+  }
+}
+
+// SVD of R (c x c, c <= 128) to about 2^-46 relative accuracy for HM_A32, the
+// phases of k_jacobi_mp with every bulk FP64 operation in double-float:
+//   A. column-pivoted Householder QR R P = Q2 R2 (Businger-Golub; DF entries,
+//      column norms and reflector scalars in FP64); X = R2^T (graded columns)
+//      parked in the node's W slot;
+//   B. one-sided Jacobi on float(X), rotations accumulated into V32 (FP32);
+//   C. Q = classical Gram-Schmidt of V32 in DF;
+//   D. X1 = X Q in DF: the left singular vectors of X, columns orthogonal to
+//      FP32 precision;
+//   E. one-sided Jacobi sweeps on X1 in DF until every pair's correlation is
+//      below the DF rounding level (angles from FP32 ratios of DF quantities:
+//      small-angle series for |t| < 2^-11, FP64 formulas otherwise; the
+//      rotations themselves in DF, orthogonal to DF rounding);
+//   F. sigma_j = |X1_j|, W = P U_x from the normalized columns, sorted
+//      descending, the sign convention of k_jacobi_mp.
+// R is scaled by a power of two (exact) so that its largest entry lies in
+// [1, 2): squared column norms then stay inside the float range.
+__global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ node_slot,
+                                                   const double* __restrict__ R, int c,
+                                                   double* __restrict__ W,
+                                                   double* __restrict__ sigma) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int cc = c * c;
+  float* reg0 = reinterpret_cast<float*>(smem_raw);
+  float* reg1 = reg0 + cc;
+  float* reg2 = reg1 + cc;
+  float* Mh = reg0;   // A: R, then R2 (column-major)
+  float* Ml = reg1;
+  float* V32 = reg0;  // B, C
+  float* X32 = reg1;  // B
+  float* Qh = reg1;   // C - F
+  float* Ql = reg2;
+  __shared__ int rotated, large;
+  __shared__ double sv[128], cn[128], hb[128];
+  __shared__ float cnh[128], cnl[128], hbh[128], hbl[128];
+  __shared__ float psh[4][128], psl[4][128];
+  __shared__ int perm[128], order[128];
+  __shared__ signed char sgn[128];
+  __shared__ double red_v[16];
+  __shared__ int red_i[16];
+  __shared__ double sh_alpha;
+  __shared__ float sh_sh, sh_sl;
+  __shared__ int sh_exp;
+  const int node = blockIdx.x;
+  const double* Rs = R + (int64_t)node_slot[node] * cc;
+  double* Wn = W + (int64_t)node * cc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int nthr = blockDim.x;
+  const int pg = tid >> 3, gl = tid & 7;
+  // ------------------------------------------------------------- scale
+  {
+    double mx = 0.0;
+    for (int idx = tid; idx < cc; idx += nthr) mx = fmax(mx, fabs(Rs[idx]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red_v[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+      double m2 = 0.0;
+      for (int w = 0; w < nwarps; ++w) m2 = fmax(m2, red_v[w]);
+      int e = 0;
+      if (m2 > 0.0 && isfinite(m2)) frexp(m2, &e);  // m2 in [2^(e-1), 2^e)
+      sh_exp = e - 1;
+    }
+    __syncthreads();
+  }
+  const int ex = sh_exp;
+  // ---------------------------------------------------------------- A
+  for (int idx = tid; idx < cc; idx += nthr) {
+    const int rr = idx / c, col = idx % c;
+    df::split(ldexp(Rs[idx], -ex), Mh[col * c + rr], Ml[col * c + rr]);
+  }
+  for (int j = tid; j < c; j += nthr) perm[j] = j;
+  __syncthreads();
+  for (int k = warp; k < c; k += nwarps) {
+    float sh = 0.f, sl = 0.f;
+    for (int i = lane; i < c; i += 32) df::dot_acc(Mh[k * c + i], Ml[k * c + i], Mh[k * c + i], Ml[k * c + i], sh, sl);
+    df::warp_sum(sh, sl);
+    if (lane == 0) { cn[k] = df::join(sh, sl); hb[k] = cn[k]; }
+  }
+  __syncthreads();
+  for (int j = 0; j < c; ++j) {
+    for (int k = j + warp; k < c; k += nwarps) {
+      if (!(cn[k] > 1.4901161193847656e-08 * hb[k])) {
+        float sh = 0.f, sl = 0.f;
+        for (int i = j + lane; i < c; i += 32)
+          df::dot_acc(Mh[k * c + i], Ml[k * c + i], Mh[k * c + i], Ml[k * c + i], sh, sl);
+        df::warp_sum(sh, sl);
+        if (lane == 0) { cn[k] = df::join(sh, sl); hb[k] = cn[k]; }
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = c;
+      for (int k = j + lane; k < c; k += 32)
+        if (cn[k] > best) { best = cn[k]; bi = k; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) red_i[0] = bi;
+    }
+    __syncthreads();
+    const int p = red_i[0];
+    if (p != j && p < c) {
+      for (int i = tid; i < c; i += nthr) {
+        float t = Mh[j * c + i]; Mh[j * c + i] = Mh[p * c + i]; Mh[p * c + i] = t;
+        t = Ml[j * c + i]; Ml[j * c + i] = Ml[p * c + i]; Ml[p * c + i] = t;
+      }
+      if (tid == 0) {
+        const int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+        double u = cn[j]; cn[j] = cn[p]; cn[p] = u;
+        u = hb[j]; hb[j] = hb[p]; hb[p] = u;
+      }
+    }
+    __syncthreads();
+    float* mjh = Mh + j * c;
+    float* mjl = Ml + j * c;
+    if (warp == 0) {  // the reflector needs the pivot column's exact norm
+      float sh = 0.f, sl = 0.f;
+      for (int i = j + lane; i < c; i += 32) df::dot_acc(mjh[i], mjl[i], mjh[i], mjl[i], sh, sl);
+      df::warp_sum(sh, sl);
+      if (lane == 0) red_v[0] = df::join(sh, sl);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double tot = red_v[0] > 0.0 ? red_v[0] : 0.0;
+      const double x0 = df::join(mjh[j], mjl[j]);
+      const double nrm = sqrt(tot);
+      const double alpha = (x0 > 0.0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      const double vtv = 2.0 * nrm * (nrm + fabs(x0));
+      const double sc = (vtv > 0.0) ? sqrt(2.0 / vtv) : 0.0;
+      sh_alpha = alpha;
+      df::split(sc, sh_sh, sh_sl);
+      df::split(v0 * sc, mjh[j], mjl[j]);
+    }
+    __syncthreads();
+    const float sch = sh_sh, scl = sh_sl;
+    for (int i = j + 1 + tid; i < c; i += nthr) df::mul(sch, scl, mjh[i], mjl[i], mjh[i], mjl[i]);
+    __syncthreads();
+    if (sch != 0.f) {
+      for (int k0 = j + 1; k0 < c; k0 += 64) {  // one 8-lane group per trailing column
+        const int k = k0 + pg;
+        const bool on = k < c;
+        float* mkh = Mh + (on ? k : j) * c;
+        float* mkl = Ml + (on ? k : j) * c;
+        float dh = 0.f, dl = 0.f;
+        if (on)
+          for (int i = j + gl; i < c; i += 8) df::dot_acc(mjh[i], mjl[i], mkh[i], mkl[i], dh, dl);
+        df::group8_sum(dh, dl);
+        if (on) {
+          float fh, fl;
+          df::fast_two_sum(dh, dl, fh, fl);
+          for (int i = j + gl; i < c; i += 8) df::axpy_neg(fh, fl, mjh[i], mjl[i], mkh[i], mkl[i]);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && sch != 0.f) df::split(sh_alpha, mjh[j], mjl[j]);
+    for (int k = j + 1 + tid; k < c; k += nthr) {
+      const double r = df::join(Mh[k * c + j], Ml[k * c + j]);
+      cn[k] -= r * r;
+    }
+    __syncthreads();
+  }
+  // X = R2^T, column-major, parked in the W slot as float pairs (hi parts, then
+  // lo parts: the c x c doubles of the slot hold both), so that phase D reads it
+  // without conversions
+  float* Xph = reinterpret_cast<float*>(Wn);
+  float* Xpl = Xph + cc;
+  for (int idx = tid; idx < cc; idx += nthr) {
+    const int col = idx / c, row = idx % c;  // X(row, col) = R2(col, row), zero above
+    const bool low = row >= col;
+    Xph[idx] = low ? Mh[row * c + col] : 0.f;
+    Xpl[idx] = low ? Ml[row * c + col] : 0.f;
+  }
+  __syncthreads();
+  // ---------------------------------------------------------------- B
+  for (int idx = tid; idx < cc; idx += nthr) {
+    X32[idx] = Xph[idx];
+    V32[idx] = (idx / c == idx % c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int cp = (c + 1) & ~1;
+  float* cn32 = cnh;  // FP32 squared column norms of X32 (cnh is free until E)
+  for (int j = warp; j < c; j += nwarps) {
+    float s2 = 0.f;
+    for (int i = lane; i < c; i += 32) s2 = fmaf(X32[j * c + i], X32[j * c + i], s2);
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane == 0) cn32[j] = s2;
+  }
+  __syncthreads();
+  {
+    const float tol = (float)(5.960464477539063e-08 * sqrt((double)c));
+    const float big2 = tol;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      if (tid == 0) { rotated = 0; large = 0; }
+      __syncthreads();
+      for (int step = 0; step < cp - 1; ++step) {
+        int p = c, q = c;
+        if (pg < cp / 2) {
+          const int a = pg, b = cp - 1 - pg;
+          p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
+          q = ((b - 1 + step) % (cp - 1)) + 1;
+        }
+        const bool valid = p < c && q < c;
+        float* ap = X32 + (valid ? p : 0) * c;
+        float* aq = X32 + (valid ? q : 0) * c;
+        float ga = 0;
+        if (valid)
+          for (int i = gl; i < c; i += 8) ga = fmaf(ap[i], aq[i], ga);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 4);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+        ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+        if (valid) {
+          const float al = cn32[p], be = cn32[q];
+          if (gl == 0 && al > 0.f && be > 0.f && (ga / al) * (ga / be) > big2) large = 1;
+          if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+            const float zeta = (be - al) / (2.f * ga);
+            const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            const float tc = 1.f / sqrtf(1.f + t * t), ts = tc * t;
+            for (int i = gl; i < c; i += 8) {
+              const float x = ap[i], y = aq[i];
+              ap[i] = tc * x - ts * y;
+              aq[i] = ts * x + tc * y;
+            }
+            float* vp = V32 + p * c;
+            float* vq = V32 + q * c;
+            for (int i = gl; i < c; i += 8) {
+              const float x = vp[i], y = vq[i];
+              vp[i] = tc * x - ts * y;
+              vq[i] = ts * x + tc * y;
+            }
+            if (gl == 0) {
+              const float cs2 = 2.f * tc * ts, c2 = tc * tc, s2 = ts * ts;
+              cn32[p] = fmaxf(fmaf(c2, al, fmaf(-cs2, ga, s2 * be)), 0.f);
+              cn32[q] = fmaxf(fmaf(s2, al, fmaf(cs2, ga, c2 * be)), 0.f);
+              rotated = 1;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      const int any = rotated && large;
+      __syncthreads();
+      if (!any) break;
+    }
+  }
+  // ---------------------------------------------------------------- C
+  // (X32 is dead; Q overlays it and the third region)
+  for (int j = 0; j < c; ++j) {
+    float* qjh = Qh + j * c;
+    float* qjl = Ql + j * c;
+    for (int i = tid; i < c; i += nthr) { qjh[i] = V32[j * c + i]; qjl[i] = 0.f; }
+    __syncthreads();
+    for (int i0 = 0; i0 < j; i0 += 64) {  // one 8-lane group per earlier column
+      const int i = i0 + pg;
+      const bool on = i < j;
+      const float* qih = Qh + (on ? i : 0) * c;
+      const float* qil = Ql + (on ? i : 0) * c;
+      float sh = 0.f, sl = 0.f;
+      if (on)
+        for (int e = gl; e < c; e += 8) df::dot_acc(qih[e], qil[e], qjh[e], qjl[e], sh, sl);
+      df::group8_sum(sh, sl);
+      if (on && gl == 0) { hbh[i] = sh; hbl[i] = sl; }
+    }
+    __syncthreads();
+    {  // q_j -= sum_i hb[i] Q_i in four partial sums over quarters of i
+      const int e = tid & 127, part = tid >> 7;
+      const int i0 = (j * part) >> 2, i1 = (j * (part + 1)) >> 2;
+      float sh = 0.f, sl = 0.f;
+      if (e < c)
+        for (int i = i0; i < i1; ++i) df::dot_acc(hbh[i], hbl[i], Qh[i * c + e], Ql[i * c + e], sh, sl);
+      df::add_to(sh, sl, 0.f, 0.f);
+      psh[part][e] = sh;
+      psl[part][e] = sl;
+    }
+    __syncthreads();
+    for (int e = tid; e < c; e += nthr) {
+      float sh = psh[0][e], sl = psl[0][e];
+      df::add_to(sh, sl, psh[1][e], psl[1][e]);
+      df::add_to(sh, sl, psh[2][e], psl[2][e]);
+      df::add_to(sh, sl, psh[3][e], psl[3][e]);
+      df::add_to(qjh[e], qjl[e], -sh, -sl);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float sh = 0.f, sl = 0.f;
+      for (int e = lane; e < c; e += 32) df::dot_acc(qjh[e], qjl[e], qjh[e], qjl[e], sh, sl);
+      df::warp_sum(sh, sl);
+      if (lane == 0) {
+        const double s = df::join(sh, sl);
+        df::split((s > 0.0) ? 1.0 / sqrt(s) : 0.0, sh_sh, sh_sl);
+      }
+    }
+    __syncthreads();
+    const float ih = sh_sh, il = sh_sl;
+    for (int e = tid; e < c; e += nthr) df::mul(ih, il, qjh[e], qjl[e], qjh[e], qjl[e]);
+    __syncthreads();
+  }
+  // ---------------------------------------------------------------- D
+  for (int j = warp; j < c; j += nwarps) {
+    float ah[4] = {0.f, 0.f, 0.f, 0.f}, alo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < c; ++k) {
+      const float qh = Qh[j * c + k], ql = Ql[j * c + k];
+      const float* xkh = Xph + k * c;
+      const float* xkl = Xpl + k * c;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int row = lane + 32 * rr;
+        if (row < c) df::dot_acc(xkh[row], xkl[row], qh, ql, ah[rr], alo[rr]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int row = lane + 32 * rr;
+      if (row < c) df::fast_two_sum(ah[rr], alo[rr], Qh[j * c + row], Ql[j * c + row]);
+    }
+  }
+  __syncthreads();
+  // ---------------------------------------------------------------- E
+  for (int j = warp; j < c; j += nwarps) {
+    float sh = 0.f, sl = 0.f;
+    for (int i = lane; i < c; i += 32) df::dot_acc(Qh[j * c + i], Ql[j * c + i], Qh[j * c + i], Ql[j * c + i], sh, sl);
+    df::warp_sum(sh, sl);
+    if (lane == 0) df::fast_two_sum(sh, sl, cnh[j], cnl[j]);
+  }
+  __syncthreads();
+  {
+    // a pair is rotated while its correlation exceeds the DF rounding level of
+    // the length-c dot products that measure it
+    const float tol = (float)(3.552713678800501e-15 * sqrt((double)c));  // 2^-48 sqrt(c)
+    const float tol2 = tol * tol, big2 = tol;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      if (tid == 0) { rotated = 0; large = 0; }
+      __syncthreads();
+      for (int step = 0; step < cp - 1; ++step) {
+        int p = c, q = c;
+        if (pg < cp / 2) {
+          const int a = pg, b = cp - 1 - pg;
+          p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
+          q = ((b - 1 + step) % (cp - 1)) + 1;
+        }
+        const bool valid = p < c && q < c;
+        float* aph = Qh + (valid ? p : 0) * c;
+        float* apl = Ql + (valid ? p : 0) * c;
+        float* aqh = Qh + (valid ? q : 0) * c;
+        float* aql = Ql + (valid ? q : 0) * c;
+        float gh = 0.f, glo = 0.f;
+        if (valid)
+          for (int i = gl; i < c; i += 8) df::dot_acc(aph[i], apl[i], aqh[i], aql[i], gh, glo);
+        df::group8_sum(gh, glo);
+        df::fast_two_sum(gh, glo, gh, glo);
+        if (valid) {
+          const float al = cnh[p], be = cnh[q];
+          const bool live = al > 0.f && be > 0.f && gh != 0.f;
+          const float r2 = live ? (gh / al) * (gh / be) : 0.f;  // correlation squared
+          if (gl == 0 && r2 > big2) large = 1;
+          if (r2 > tol2) {
+            const float d = (be - al) + (cnl[q] - cnl[p]);
+            float ch, cl, sh, sl;
+            if (fabsf(gh) < 0.00048828125f * fabsf(d)) {  // |t| < 2^-11
+              const float u = gh / d;                       // 1 / (2 zeta)
+              const float t = fmaf(-u * u, u, u);           // tan(theta) = u - u^3 + ...
+              const float t2 = t * t;
+              ch = 1.f;
+              cl = t2 * fmaf(t2, 0.375f, -0.5f);            // cos - 1 = -t^2/2 + 3t^4/8
+              sh = t;
+              sl = t * cl;                                  // sin = t cos
+            } else {
+              const double zeta = ((double)be - (double)al + ((double)cnl[q] - (double)cnl[p])) /
+                                  (2.0 * df::join(gh, glo));
+              const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+              const double cd = 1.0 / sqrt(1.0 + t * t);
+              df::split(cd, ch, cl);
+              df::split(cd * t, sh, sl);
+            }
+            for (int i = gl; i < c; i += 8) rot_df(ch, cl, sh, sl, aph[i], apl[i], aqh[i], aql[i]);
+            if (gl == 0) {
+              // norms after the rotation: c^2 al - 2cs ga + s^2 be, s^2 al + 2cs ga + c^2 be
+              float c2h, c2l, s2h, s2l, csh, csl, th, tl;
+              df::mul(ch, cl, ch, cl, c2h, c2l);
+              df::mul(sh, sl, sh, sl, s2h, s2l);
+              df::mul(ch, cl, sh, sl, csh, csl);
+              csh *= 2.f;
+              csl *= 2.f;
+              const float alh = cnh[p], all = cnl[p], beh = cnh[q], bel = cnl[q];
+              float ph = 0.f, pl = 0.f, qh = 0.f, ql = 0.f;
+              df::mul(c2h, c2l, alh, all, ph, pl);
+              df::mul(csh, csl, gh, glo, th, tl);
+              df::add_to(ph, pl, -th, -tl);
+              df::mul(s2h, s2l, beh, bel, th, tl);
+              df::add_to(ph, pl, th, tl);
+              df::mul(s2h, s2l, alh, all, qh, ql);
+              df::mul(csh, csl, gh, glo, th, tl);
+              df::add_to(qh, ql, th, tl);
+              df::mul(c2h, c2l, beh, bel, th, tl);
+              df::add_to(qh, ql, th, tl);
+              cnh[p] = ph; cnl[p] = pl;
+              cnh[q] = qh; cnl[q] = ql;
+              rotated = 1;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      const int any = rotated && large;
+      __syncthreads();
+      if (!any) break;
+    }
+  }
+  // ---------------------------------------------------------------- F
+  for (int j = warp; j < c; j += nwarps) {
+    float sh = 0.f, sl = 0.f;
+    for (int i = lane; i < c; i += 32) df::dot_acc(Qh[j * c + i], Ql[j * c + i], Qh[j * c + i], Ql[j * c + i], sh, sl);
+    df::warp_sum(sh, sl);
+    if (lane == 0) {
+      const double s = df::join(sh, sl);
+      sv[j] = isfinite(s) ? sqrt(s) : -1.0;
+    }
+  }
+  __syncthreads();
+  for (int j = tid; j < c; j += nthr) {
+    int rk = 0;
+    for (int i = 0; i < c; ++i) rk += (sv[i] > sv[j]) || (sv[i] == sv[j] && i < j);
+    order[rk] = j;
+  }
+  __syncthreads();
+  for (int j = warp; j < c; j += nwarps) {
+    const float* xh = Qh + order[j] * c;
+    const float* xl = Ql + order[j] * c;
+    double best = -1.0, bv = 0.0;
+    int bi = c;
+    for (int i = lane; i < c; i += 32) {
+      const double x = df::join(xh[i], xl[i]);
+      const double a = fabs(x);
+      const int row = perm[i];
+      if (a > best || (a == best && row < bi)) { best = a; bi = row; bv = x; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bv = ov; }
+    }
+    if (lane == 0) {
+      sgn[j] = (bv < 0.0) ? -1 : 1;
+      hb[j] = (sv[order[j]] > 0.0) ? 1.0 / sv[order[j]] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < cc; idx += nthr) {
+    const int i = idx % c, col = idx / c;
+    const int j = order[col];
+    const double u = df::join(Qh[j * c + i], Ql[j * c + i]) * hb[col];
+    Wn[perm[i] + col * c] = sgn[col] < 0 ? -u : u;
+  }
+  for (int j = tid; j < c; j += nthr)
+    sigma[(int64_t)node * c + j] = sv[order[j]] > 0.0 ? ldexp(sv[order[j]], ex) : 0.0;
+}
+
+}  // namespace
+
+void launch_jacobi_df(const int32_t* node_slot, int nnodes, const double* R, int c, double* W,
+                      double* sigma, cudaStream_t st) {
+  count_launches(1);
+  const size_t smem = (size_t)3 * c * c * sizeof(float);
+  static std::atomic<uint32_t> done{0};
+  raise_smem_limit((const void*)k_jacobi_df, done);
+  k_jacobi_df<<<nnodes, 512, smem, st>>>(node_slot, R, c, W, sigma);
+}
+
+}  // namespace hm

@@ -88,5 +88,5 @@ def test_adjoint_against_central_differences():
     worst["D"] = np.linalg.norm(np.array(g_gpu) - g_fd) / np.linalg.norm(g_fd)
     print("adjoint vs central differences (relative, per argument): "
           + ", ".join(f"{k_}: {v:.2e}" for k_, v in worst.items()))
-    for name, v in worst.items():
-        assert v < 1e-5, (name, v)
+    for name, v in worst.items():  # measured 1.9e-7 .. 3.8e-7 (FP32 rounding of the kernels)
+        assert v < 1e-6, (name, v)
