@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--skip-frob", action="store_true", help="skip the full Frobenius error check")
     ap.add_argument("--skip-mixed", action="store_true", help="skip the HM_MIXED comparison run")
     ap.add_argument("--skip-batched", action="store_true", help="skip the batched many-operator run")
+    ap.add_argument("--skip-matrix-free", action="store_true",
+                    help="skip the matrix-free log-kernel runs")
     return ap.parse_args()
 
 
@@ -163,6 +165,99 @@ def gemm_roofline(hm, torch, A, op, tree, n, peak_gbs, peak_kind):
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": round(ms, 4),
             "peak_source": f"{peak_kind} HBM copy bandwidth",
             "note": "launch_ms covers hm_dense_apply: the X pre-cut kernel and the GEMM"}
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["bf16_tflops"]), "measured"
+        except Exception:
+            pass
+    return 1900.0, "fallback"
+
+
+def matrix_free_bench(hm, torch, dev, steps, n, big_n):
+    """The headline compression with the matrix-free log-kernel black box (entries
+    formed in the sampling GEMM from two tables, no operator in HBM), its GEMM
+    against the tensor roofline, and one compression at big_n (twice the headline
+    size) with its error estimated on 64 sampled rows."""
+    op = hm.hm_log_kernel_operator_create(n)
+    tree = hm.Tree(n, LEAF_HEAD)
+    kw = dict(tol=TOL_HEAD, r=R_HEAD, seed=2, prec=hm.HM_A32, hbs_id=1)
+    h = hm.hm_compress_hbs(op, tree, **kw)
+    del h
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h = hm.hm_compress_hbs(op, tree, **kw)
+        if _ < steps - 1:
+            del h
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    Wv = torch.randn((10, n), device=dev, generator=torch.Generator(device=dev).manual_seed(11),
+                     dtype=torch.float64)
+    Wv /= Wv.norm(dim=1, keepdim=True)
+    Yt, Yc = torch.empty_like(Wv), torch.empty_like(Wv)
+    hm.hm_dense_apply(op, 0, Wv, Yt)
+    hm.hm_apply(h, 0, Wv, Yc)
+    torch.cuda.synchronize()
+    E = float(((Yt - Yc).norm(dim=1) / Yt.norm(dim=1)).max())
+    # one level-0 black-box call (Y_1 = A Omega_2): 10 slice products of the
+    # active half of K against 64 (60 used) columns on the tensor cores
+    r = R_HEAD
+    X = torch.empty((2 * r, n), device=dev, dtype=torch.float64)
+    hm.hm_gaussian_test_matrix(tree, 0, r, 2, hm.HM_A32, X)
+    Xh = X[:r]
+    Y = torch.empty_like(Xh)
+    call = lambda: hm.hm_dense_apply(op, 0, Xh, Y)  # noqa: E731
+    for _ in range(2):
+        call()
+    cms = time_events(call, 5, torch)
+    k_active = n - tree.node(2)[1]
+    flops = 10.0 * 2.0 * n * k_active * 64
+    peak, kind = bf16_peak()
+    tf = flops / (cms * 1e-3) / 1e12
+    out = {"ms": round(ms, 3), "estimate_E": E, "ranks": [h.info["min_rank"], h.info["max_rank"]],
+           "saturated": h.info["saturated"], "t_blackbox_ms": round(h.info["t_blackbox_ms"], 3),
+           "operator_bytes_in_hbm": 12 * n,
+           "gemm": {"bound": "tensor", "kernel": "k_gemm_esg<0,1> (entries generated in the cutter "
+                                                  "warps)",
+                    "achieved": round(tf, 1), "peak": peak, "unit": "TFLOP/s",
+                    "frac": round(tf / peak, 4), "launch_ms": round(cms, 4),
+                    "algorithmic_flops_per_launch": flops,
+                    "peak_source": f"{kind} dense bf16 (burst)",
+                    "definition": "10 BF16 slice products x 2 x rows x active K x 64 columns"}}
+    del h, op
+    if big_n:
+        opb = hm.hm_log_kernel_operator_create(big_n)
+        eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eb0.record()
+        hb = hm.hm_compress_hbs(opb, hm.Tree(big_n, LEAF_HEAD), **dict(kw, r=64, tol=5e-8))
+        eb1.record()
+        torch.cuda.synchronize()
+        rows = torch.randperm(big_n, generator=torch.Generator().manual_seed(8))[:64].sort().values
+        Eb = torch.zeros((64, big_n), device=dev, dtype=torch.float64)
+        Eb[torch.arange(64), rows.to(dev)] = 1.0
+        Rc = torch.empty_like(Eb)
+        hm.hm_apply(hb, 1, Eb, Rc)
+        Ar = torch.empty((64, big_n), device=dev, dtype=torch.float32)
+        for q, i in enumerate(rows.tolist()):
+            hm.hm_log_kernel_entries(opb, i, i + 1, 0, big_n, Ar[q:q + 1])
+        torch.cuda.synchronize()
+        est = float((Rc - Ar.double()).norm() / Ar.double().norm())
+        out["n%d" % big_n] = {"ms": round(eb0.elapsed_time(eb1), 2), "rel_frob_err_sampled": est,
+                              "ranks": [hb.info["min_rank"], hb.info["max_rank"]],
+                              "saturated": hb.info["saturated"],
+                              "r": 64, "tol": 5e-8,
+                              "note": "one compression (first call on the operator), r = 64, tol "
+                                      "5e-8 (the relative Frobenius error of absolute thresholds "
+                                      "grows as sqrt(N)); error on 64 sampled rows against the "
+                                      "operator's entries"}
+        del hb, opb
+    return out
 
 
 def adjoint_bench(hm, torch, dev, steps, warmup):
@@ -450,6 +545,8 @@ def run_gpu(args):
                        "of one leaf block -> pinned host"}
         del A_host
     adj = None if args.skip_adjoint else adjoint_bench(hm, torch, dev, max(3, args.steps), 3)
+    mfree = None if args.skip_matrix_free else matrix_free_bench(
+        hm, torch, dev, max(3, args.steps), n, 2 * n if n == N_HEAD else 0)
     del op
     batched = None if args.skip_batched else batched_bench(hm, torch, dev)
     cpu = None
@@ -485,6 +582,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "e2e": e2e,
         "adjoint": adj,
+        "matrix_free": mfree,
         "batched": batched,
         "cpu_baseline": cpu,
     }

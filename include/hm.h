@@ -163,6 +163,36 @@ hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_
 void hm_dense_operator_destroy(hm_operator* op);
 
 /*
+ * Matrix-free black box (Sec. 5: the paper's black boxes are fast matrix-vector
+ * multipliers, an FMM in Sec. 5.3, not stored matrices): the log kernel of n
+ * points on the ellipse x_i = (cos t_i, 0.5 sin t_i), t_i = 2 pi i / n, with
+ * its entries formed in registers inside the sampling GEMM and never stored.
+ * With d = pi (i - j) / n and f = pi (i + j) / n,
+ *   |x_i - x_j|^2 = sin^2(d) (1 + 3 sin^2(f)),
+ * so log|x_i - x_j| = S[|i - j|] + P[i + j] with the tables
+ *   S[m] = log|sin(pi m / n)|,  P[s] = log(1 + 3 sin^2(pi s / n)) / 2,
+ * each computed in FP64 on the host and kept as a float pair (hi = the value
+ * rounded to FP32, lo = the remainder rounded to FP32).  The operator's entries
+ * are DEFINED as fl32(fl32(Sh + Ph) + fl32(Sl + Pl)) for i != j and 1 on the
+ * diagonal: within about one FP32 ulp of log|x_i - x_j| even where the two
+ * terms cancel (distances near 1).  It is
+ * symmetric; its products are those of dtype 4 of hm_dense_operator_create
+ * (FP64 blocks, exact-accumulation split on the tensor cores) on these
+ * entries, with no operator bytes read from HBM (24 n bytes of tables).
+ * Element type double (HM_A32).  Destroy with hm_dense_operator_destroy.
+ */
+hm_status hm_log_kernel_operator_create(int64_t n, hm_operator* out);
+
+/*
+ * Entries A(r0:r1, c0:c1) of a matrix-free log-kernel operator, written
+ * row-major to the device buffer `out` (element (i, j) at
+ * out[(i - r0) * ld + (j - c0)], ld >= c1 - c0).  For checks and for forming a
+ * dense copy; the compression never calls it.
+ */
+hm_status hm_log_kernel_entries(const hm_operator* op, int64_t r0, int64_t r1, int64_t c0,
+                                int64_t c1, float* out, int64_t ld, void* stream);
+
+/*
  * Status of a dense operator's tensor-core GEMMs (dtypes 1 and 4): synchronizes
  * `stream`, then returns HM_ETIMEOUT if one of their bounded device-side waits
  * gave up since the last check (those outputs were written as NaN; the flag is

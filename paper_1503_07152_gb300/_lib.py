@@ -81,6 +81,9 @@ _sig = {
     "hm_gaussian_test_matrix": ([_P, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, _P, C.c_int64, _P],
                                 C.c_int),
     "hm_dense_operator_check": ([C.POINTER(_Operator), _P], C.c_int),
+    "hm_log_kernel_operator_create": ([C.c_int64, C.POINTER(_Operator)], C.c_int),
+    "hm_log_kernel_entries": ([C.POINTER(_Operator), C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P,
+                               C.c_int64, _P], C.c_int),
     "hm_set_wait_limit": ([C.c_int64], C.c_int),
     "hm_last_error": ([], C.c_char_p),
     "hm_version": ([], C.c_char_p),
@@ -201,6 +204,22 @@ def callback_operator(n: int, fn) -> Operator:
     cb = APPLY_FN(tramp)
     op = _Operator(cb, None, n)
     return Operator(op, keep=cb)
+
+
+def hm_log_kernel_operator_create(n: int) -> Operator:
+    """Matrix-free log-kernel black box of n ellipse points (HM_A32, double blocks)."""
+    op = _Operator()
+    _check(lib.hm_log_kernel_operator_create(n, C.byref(op)), "hm_log_kernel_operator_create")
+    return Operator(op, dense=True)
+
+
+def hm_log_kernel_entries(op: Operator, r0: int, r1: int, c0: int, c1: int, out: torch.Tensor,
+                          stream=None) -> None:
+    """out: row-major float32 CUDA tensor of shape (r1 - r0, ld >= c1 - c0)."""
+    if out.dtype != torch.float32 or out.dim() != 2 or out.stride(1) != 1:
+        raise ValueError("out must be a row-major float32 CUDA tensor")
+    _check(lib.hm_log_kernel_entries(C.byref(op.op), r0, r1, c0, c1, _ptr(out), out.stride(0),
+                                     C.c_void_p(_stream(stream))), "hm_log_kernel_entries")
 
 
 def hm_dense_operator_check(op: Operator, stream=None) -> None:

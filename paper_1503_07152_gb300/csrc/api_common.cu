@@ -6,6 +6,7 @@
 #include <cstring>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "hm_api.h"
 
@@ -362,7 +363,19 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
   cudaStream_t st = (cudaStream_t)stream;
   for (int64_t c0 = 0; c0 < ncols; c0 += 1024) {
     const int64_t w = std::min<int64_t>(1024, ncols - c0);
-    if (d->dtype == 0)
+    if (d->dtype == 5) {  // matrix-free log kernel: symmetric, either product
+      const int64_t need = gemm_esg_work_bytes(n, w);
+      if (need > d->xs_bytes) {
+        if (d->xs) cudaFree(d->xs);
+        d->xs = nullptr;
+        d->xs_bytes = 0;
+        if (cudaMalloc(&d->xs, (size_t)need) != cudaSuccess) return 3;
+        d->xs_bytes = need;
+      }
+      if (launch_gemm_esg_gen(d->tabS, d->tabP, d->aexp, n, w, (const double*)X + c0 * ldx, ldx,
+                              (double*)Y + c0 * ldy, ldy, d->xs, d->flags, d->err, st) != 0)
+        return 2;
+    } else if (d->dtype == 0)
       launch_dense_gemm<double>((const double*)d->A, d->lda, trans, n, w,
                                 (const double*)X + c0 * ldx, ldx, (double*)Y + c0 * ldy, ldy,
                                 d->flags, st);
@@ -437,9 +450,87 @@ hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_
   return HM_OK;
 }
 
+hm_status hm_log_kernel_operator_create(int64_t n, hm_operator* out) {
+  clear_error();
+  if (!out || n < 2) {
+    set_error("hm_log_kernel_operator_create: need n >= 2 and out");
+    return HM_EINVAL;
+  }
+  // tables of the entries' two terms, S[m] = log|sin(pi m / n)| (m >= 1) and
+  // P[s] = log(1 + 3 sin^2(pi s / n)) / 2, as float pairs (hi = the FP64 value
+  // rounded to FP32, lo = the FP64 remainder rounded to FP32): high parts of
+  // all entries first, then the low parts
+  const double pi = 3.14159265358979323846;
+  const int64_t np = 2 * n - 1;
+  std::vector<float> hs((size_t)(2 * n), 0.f), hp((size_t)(2 * np));
+  auto put = [](std::vector<float>& v, int64_t i, int64_t stride, double x) {
+    const float hi = (float)x;
+    v[i] = hi;
+    v[stride + i] = (float)(x - (double)hi);
+  };
+  for (int64_t m = 1; m < n; ++m)
+    put(hs, m, n, std::log(std::fabs(std::sin(pi * (double)m / (double)n))));
+  for (int64_t t = 0; t < np; ++t) {
+    const double sn = std::sin(pi * (double)t / (double)n);
+    put(hp, t, np, 0.5 * std::log1p(3.0 * sn * sn));
+  }
+  hm_dense_ctx* d = new hm_dense_ctx();
+  d->n = n;
+  d->lda = n;
+  d->dtype = 5;
+  d->flags_bytes = dense_flags_bytes(n, 1024, 0);
+  hm_status s = device_alloc((void**)&d->flags, (size_t)d->flags_bytes);
+  if (s == HM_OK) s = device_alloc((void**)&d->err, sizeof(int));
+  if (s == HM_OK) s = device_alloc((void**)&d->tabS, sizeof(float) * hs.size());
+  if (s == HM_OK) s = device_alloc((void**)&d->tabP, sizeof(float) * hp.size());
+  if (s == HM_OK) s = device_alloc((void**)&d->aexp, sizeof(int) * (size_t)n);
+  if (s == HM_OK &&
+      (cudaMemcpy(d->tabS, hs.data(), sizeof(float) * hs.size(), cudaMemcpyHostToDevice) !=
+           cudaSuccess ||
+       cudaMemcpy(d->tabP, hp.data(), sizeof(float) * hp.size(), cudaMemcpyHostToDevice) !=
+           cudaSuccess ||
+       cudaMemset(d->err, 0, sizeof(int)) != cudaSuccess))
+    s = HM_ECUDA;
+  if (s == HM_OK) {
+    launch_logtab_rowexp(d->tabS, d->tabP, n, d->aexp, cudaStreamLegacy);
+    if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) s = HM_ECUDA;
+  }
+  if (s != HM_OK) {
+    if (s == HM_ECUDA) set_error("hm_log_kernel_operator_create: table upload failed");
+    if (d->flags) cudaFree(d->flags);
+    if (d->err) cudaFree(d->err);
+    if (d->tabS) cudaFree(d->tabS);
+    if (d->tabP) cudaFree(d->tabP);
+    if (d->aexp) cudaFree(d->aexp);
+    delete d;
+    return s;
+  }
+  out->apply = dense_cb;
+  out->ctx = d;
+  out->n = n;
+  return HM_OK;
+}
+
+hm_status hm_log_kernel_entries(const hm_operator* op, int64_t r0, int64_t r1, int64_t c0,
+                                int64_t c1, float* out, int64_t ld, void* stream) {
+  clear_error();
+  if (!op || op->apply != dense_cb || !op->ctx || ((hm_dense_ctx*)op->ctx)->dtype != 5 || !out ||
+      r0 < 0 || r1 < r0 || r1 > op->n || c0 < 0 || c1 < c0 || c1 > op->n || ld < c1 - c0) {
+    set_error("hm_log_kernel_entries: need a matrix-free log-kernel operator, a range inside "
+              "[0, n) and ld >= c1 - c0");
+    return HM_EINVAL;
+  }
+  if (r1 == r0 || c1 == c0) return HM_OK;
+  const hm_dense_ctx* d = (const hm_dense_ctx*)op->ctx;
+  launch_logtab_block(d->tabS, d->tabP, d->n, r0, r1, c0, c1, out, ld, (cudaStream_t)stream);
+  return check_launch("hm_log_kernel_entries");
+}
+
 void hm_dense_operator_destroy(hm_operator* op) {
   if (!op || !op->ctx) return;
   hm_dense_ctx* d = (hm_dense_ctx*)op->ctx;
+  if (d->tabS) cudaFree(d->tabS);
+  if (d->tabP) cudaFree(d->tabP);
   if (d->flags) cudaFree(d->flags);
   if (d->xs) cudaFree(d->xs);
   if (d->err) cudaFree(d->err);

@@ -105,6 +105,17 @@ int launch_gemm_tc(const float* A, int64_t lda, int trans, int64_t n, int64_t nc
                    const float* X, int64_t ldx, float* Y, int64_t ldy, void* xs_work,
                    uint8_t* flags, int* err, cudaStream_t st);
 
+// Matrix-free log kernel of the ellipse (hm_log_kernel_operator_create): row
+// exponents, a block of entries, and the sampling GEMM that forms the entries in
+// registers from the tables S (n float pairs) and P (2n - 1 float pairs), high
+// parts first.
+void launch_logtab_rowexp(const float* S, const float* P, int64_t n, int* e_row, cudaStream_t st);
+void launch_logtab_block(const float* S, const float* P, int64_t n, int64_t r0, int64_t r1,
+                         int64_t c0, int64_t c1, float* out, int64_t ld, cudaStream_t st);
+int launch_gemm_esg_gen(const float* S, const float* P, const int* rowexp, int64_t n,
+                        int64_t ncols, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                        void* work, uint8_t* flags, int* err, cudaStream_t st);
+
 void launch_dense_gemm_a32(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
                            const double* X, int64_t ldx, double* Y, int64_t ldy, uint8_t* flags,
                            cudaStream_t st);
@@ -282,6 +293,8 @@ struct hm_dense_ctx {
   int64_t xs_bytes = 0;
   int* err = nullptr;        // device flag raised by a kernel that gave up waiting
   int* aexp = nullptr;       // dtype 4: row then column exponents of A (taken at first use)
+  float* tabS = nullptr;     // dtype 5 (matrix-free log kernel): S[|i - j|] and P[i + j]
+  float* tabP = nullptr;
 };
 
 struct hm_handle {

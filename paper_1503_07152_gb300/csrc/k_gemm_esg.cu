@@ -171,12 +171,31 @@ __global__ __launch_bounds__(256) void k_split_x64(const double* __restrict__ X,
   }
 }
 
-template <int TRANS>
+// Named barrier 1 of the 256 cutter threads (warps 0-7), and its AND-reduction
+// form: the generating cutters (GEN) stage table windows in shared memory and
+// must leave their loop together.
+__device__ __forceinline__ void cutters_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool cutters_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 256, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+// GEN = 1: the operator is the matrix-free log kernel of the ellipse (see
+// launch_gemm_esg_gen): the cutters generate each tile's entries from two
+// tables instead of reading a TMA tile of A (no A bytes from HBM); the
+// operator is symmetric, so only TRANS = 0 is instantiated.
+template <int TRANS, int GEN>
 __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int64_t n,
     int64_t ncols, const uint8_t* __restrict__ flags, const int* __restrict__ ex,
-      const int* __restrict__ e_rows, double* __restrict__ Y, int64_t ldy, int* __restrict__ err,
-    long long poll_limit) {
+    const int* __restrict__ e_rows, double* __restrict__ Y, int64_t ldy, int* __restrict__ err,
+    long long poll_limit, const float* __restrict__ tabS, const float* __restrict__ tabP) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t raw_full, raw_empty, st_full[SSTAGES], x_full[SSTAGES],
       st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final, bar_chain;
@@ -273,7 +292,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
 
   if (warp == W_TMA) {
     // ---------------------------------------------------------- TMA of A
-    if (lane == 0) {
+    if (!GEN && lane == 0) {
       int it = 0;
       for (int kt = 0; kt < nkt; ++kt) {
         if (!active(kt)) continue;
@@ -287,6 +306,89 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       }
       if (it > 0) mbar_wait_drain(smem_u32(&raw_full), (it - 1) & 1);
     }
+  } else if (GEN && warp < 8) {
+    // ---------------------------------------------------------- generate A, cut, TMA of X
+    // A(i, j) = (S[|i - j|] + P[i + j]) in float pairs: fl((Sh + Ph) + (Sl + Pl)),
+    // 1 on the diagonal, 0 outside [0, n).  A tile's entries use TM + TK - 1
+    // values of each table, staged in the (unused) raw stage: window entry e
+    // holds S[|d|] for i - j = d = dbase + e, and P[m0 + k0 + e].
+    int it = 0, xissued = 0;
+    constexpr int WN = TM + TK;  // window stride (TM + TK - 1 used)
+    float* swh = reinterpret_cast<float*>(sbase);
+    float* swl = swh + WN;
+    float* pwh = swl + WN;
+    float* pwl = pwh + WN;
+    for (int kt = 0; kt < nkt; ++kt) {
+      const int fl = active(kt);  // the same for every cutter
+      if (!fl) continue;
+      const int s = it % SSTAGES;
+      const bool ok = !abort_flag &&
+                      mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag,
+                                poll_limit);
+      // all cutters leave together (they share the table windows); the barrier
+      // also orders the previous tile's window reads before the new writes
+      if (!cutters_all(ok)) break;
+      const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
+      if (tid == 0) {
+        mbar_arrive_tx(smem_u32(&x_full[s]), (uint32_t)(NSL * B_SLICE));
+        for (int t = 0; t < NSL; ++t)
+          tma_load_2d(st + NSL * A_SLICE + t * B_SLICE, &tmX, kt * TK, (ct * NSL + t) * TN,
+                      smem_u32(&x_full[s]));
+        xissued = it + 1;
+      }
+      const int64_t k0 = (int64_t)kt * TK;
+      const int64_t dbase = m0 - k0 - (TK - 1);
+      for (int e = tid; e < TM + TK - 1; e += NCONV) {
+        const int64_t d = dbase + e, ad = d < 0 ? -d : d, sidx = m0 + k0 + e;
+        const bool sin_ = ad > 0 && ad < n, pin = sidx < 2 * n - 1;
+        swh[e] = sin_ ? tabS[ad] : 0.f;
+        swl[e] = sin_ ? tabS[n + ad] : 0.f;
+        pwh[e] = pin ? tabP[sidx] : 0.f;
+        pwl[e] = pin ? tabP[2 * n - 1 + sidx] : 0.f;
+      }
+      cutters_sync();
+      // tiles that hold a diagonal entry or reach past n take the per-entry fixes
+      const bool fix = (m0 + TM > n) || (k0 + TK > n) || (m0 < k0 + TK && k0 < m0 + TM);
+      const int dk = (int)(fix ? k0 - m0 : 0);  // i == j  <=>  m - (4 k4 + e) == dk
+      const int mrow = (int)(n - m0 < TM ? n - m0 : TM), kcol = (int)(n - k0 < TK ? n - k0 : TK);
+      unsigned char* sp = sbase + (st - base);
+      int bad = 0;
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const int f = p * NCONV + tid, m = f >> 4, k4 = f & 15;
+        const float sc = srow[m];
+        const int ds = m - 4 * k4 + (TK - 1), ps = m + 4 * k4;
+        float a[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float v = (swh[ds - e] + pwh[ps + e]) + (swl[ds - e] + pwl[ps + e]);
+          if (fix) {
+            const int kk = 4 * k4 + e;
+            if (m - kk == dk) v = 1.f;
+            if (m >= mrow || kk >= kcol) v = 0.f;
+          }
+          a[e] = v * sc;
+        }
+        float sl[4][4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          bad |= !(fabsf(a[e]) < 128.f);
+          cut4(a[e], sl[0][e], sl[1][e], sl[2][e], sl[3][e]);
+        }
+        const uint32_t off = sw_off(m, k4 >> 1) + (uint32_t)((k4 & 1) * 8);
+#pragma unroll
+        for (int t = 0; t < NSL; ++t)
+          *reinterpret_cast<uint2*>(sp + t * A_SLICE + off) =
+              make_uint2(pack_bf16(sl[t][0], sl[t][1]), pack_bf16(sl[t][2], sl[t][3]));
+      }
+      if (bad) abort_flag = 3;
+      fence_proxy_async();
+      mbar_arrive(smem_u32(&st_full[s]));
+      ++it;
+    }
+    if (tid == 0)
+      for (int j = (xissued > SSTAGES ? xissued - SSTAGES : 0); j < xissued; ++j)
+        mbar_wait_drain(smem_u32(&x_full[j % SSTAGES]), (j / SSTAGES) & 1);
   } else if (warp < 8) {
     // ---------------------------------------------------------- cut A, TMA of X
     int it = 0, xissued = 0;
@@ -586,14 +688,125 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
     return 2;
   dim3 grid((unsigned)nct, (unsigned)nrb, (unsigned)ks);
   if (trans) {
-    raise_smem_limit((const void*)k_gemm_esg<1>, done[1]);
-    k_gemm_esg<1><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
-                                                err, wait_limit());
+    raise_smem_limit((const void*)k_gemm_esg<1, 0>, done[1]);
+    k_gemm_esg<1, 0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
+                                                   err, wait_limit(), nullptr, nullptr);
   } else {
-    raise_smem_limit((const void*)k_gemm_esg<0>, done[0]);
-    k_gemm_esg<0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
-                                                err, wait_limit());
+    raise_smem_limit((const void*)k_gemm_esg<0, 0>, done[0]);
+    k_gemm_esg<0, 0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
+                                                   err, wait_limit(), nullptr, nullptr);
   }
+  return 0;
+}
+
+}  // namespace hm
+
+namespace hm {
+namespace {
+
+// The tables hold float pairs: S[0 .. n) high parts then S[n .. 2n) low parts,
+// P[0 .. 2n - 1) high parts then P[2n - 1 .. 4n - 2) low parts.
+// Row exponents of the matrix-free log kernel: e with max_j |A(i, j)| < 2^e
+// (clamped to >= -120), the entries formed exactly as the generating cutters
+// form them.  One warp per row.  The operator is symmetric: these are also the
+// column exponents.
+__global__ __launch_bounds__(256) void k_row_exp_logtab(const float* __restrict__ S,
+                                                        const float* __restrict__ P, int64_t n,
+                                                        int* __restrict__ e_row) {
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  float mx = 0.f;
+  for (int64_t j = lane; j < n; j += 32) {
+    const int64_t d = row > j ? row - j : j - row;
+    const float v = (d == 0) ? 1.f : (S[d] + P[row + j]) + (S[n + d] + P[2 * n - 1 + row + j]);
+    mx = fmaxf(mx, fabsf(v));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) e_row[row] = max(exp_above(mx), -120);
+}
+
+// out[(i - r0) * ld + (j - c0)] = A(i, j) of the matrix-free log kernel.
+__global__ void k_logtab_block(const float* __restrict__ S, const float* __restrict__ P,
+                               int64_t n, int64_t r0, int64_t r1, int64_t c0, int64_t c1,
+                               float* __restrict__ out, int64_t ld) {
+  for (int64_t i = r0 + blockIdx.y; i < r1; i += gridDim.y)
+    for (int64_t j = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < c1;
+         j += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t d = i > j ? i - j : j - i;
+      out[(i - r0) * ld + (j - c0)] =
+          (d == 0) ? 1.f : (S[d] + P[i + j]) + (S[n + d] + P[2 * n - 1 + i + j]);
+    }
+}
+
+}  // namespace
+
+void launch_logtab_rowexp(const float* S, const float* P, int64_t n, int* e_row, cudaStream_t st) {
+  count_launches(1);
+  k_row_exp_logtab<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(S, P, n, e_row);
+}
+
+void launch_logtab_block(const float* S, const float* P, int64_t n, int64_t r0, int64_t r1,
+                         int64_t c0, int64_t c1, float* out, int64_t ld, cudaStream_t st) {
+  count_launches(1);
+  const int64_t w = c1 - c0, h = r1 - r0;
+  dim3 grid((unsigned)std::min<int64_t>((w + 255) / 256, 1024),
+            (unsigned)std::min<int64_t>(h, 65535));
+  k_logtab_block<<<grid, 256, 0, st>>>(S, P, n, r0, r1, c0, c1, out, ld);
+}
+
+// Y = A X for the matrix-free log kernel (symmetric, so either product), FP64
+// X and Y, with the exact-accumulation split of launch_gemm_esg; the entries of
+// A are formed in the cutter warps from the tables S and P and never stored.
+int launch_gemm_esg_gen(const float* S, const float* P, const int* rowexp, int64_t n,
+                        int64_t ncols, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                        void* work, uint8_t* flags, int* err, cudaStream_t st) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tc::encode_fn();
+  if (!enc) return 1;
+  const int64_t kpad = ((n + TK - 1) / TK) * TK;
+  const int nct = (int)((ncols + TN - 1) / TN);
+  const int nkt = (int)(kpad / TK);
+  __nv_bfloat16* Xs = (__nv_bfloat16*)work;
+  const int64_t xs_bytes = (int64_t)nct * NSL * TN * kpad * 2;
+  int* ex = (int*)((unsigned char*)work + ((xs_bytes + 255) / 256) * 256);
+  CUtensorMap tmX;
+  const cuuint32_t one[2] = {1, 1};
+  const cuuint64_t xdim[2] = {(cuuint64_t)kpad, (cuuint64_t)NSL * TN * nct};
+  const cuuint64_t xstr[1] = {(cuuint64_t)kpad * 2};
+  const cuuint32_t xbox[2] = {(cuuint32_t)TK, (cuuint32_t)TN};
+  if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Xs, xdim, xstr, xbox, one,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return 2;
+  count_launches(2);
+  const int nwin = (nkt + WIN_TILES - 1) / WIN_TILES;
+  k_split_x64<<<dim3(nwin, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, ex, flags);
+  const size_t smem = gemm_esg_smem_bytes();
+  static std::atomic<uint32_t> done{0};
+  // the same K split as the dense engine: two blocks share a row block's windows
+  // when the grid's last wave is short
+  const int nrb = (int)((n + TM - 1) / TM);
+  int nsm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    nsm = 1;
+  auto eff = [&](int k) {
+    const int64_t c = (int64_t)nct * nrb * k;
+    return (double)c / ((double)nsm * (double)((c + nsm - 1) / nsm));
+  };
+  int ks = 1;
+  const int ks_max = std::max(1, std::min(2, nwin / 16));
+  for (int k = 2; k <= ks_max; ++k)
+    if (eff(k) > eff(ks) + 0.05) ks = k;
+  if (ks > 1 &&
+      cudaMemset2DAsync(Y, (size_t)ldy * sizeof(double), 0, (size_t)n * sizeof(double),
+                        (size_t)ncols, st) != cudaSuccess)
+    return 2;
+  dim3 grid((unsigned)nct, (unsigned)nrb, (unsigned)ks);
+  raise_smem_limit((const void*)k_gemm_esg<0, 1>, done);
+  // the kernel takes no TMA map of A in this form; the X map fills the slot
+  k_gemm_esg<0, 1><<<grid, NTHREADS, smem, st>>>(tmX, tmX, n, ncols, flags, ex, rowexp, Y, ldy,
+                                                 err, wait_limit(), S, P);
   return 0;
 }
 

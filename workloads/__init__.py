@@ -89,6 +89,38 @@ def log_kernel(N: int, rows=None, cols=None) -> np.ndarray:
     return A.astype(np.float32)
 
 
+def log_kernel_tables(N: int):
+    """Tables of the matrix-free log kernel: S[m] = log|sin(pi m / N)| (m >= 1,
+    S[0] unused) and P[s] = log(1 + 3 sin^2(pi s / N)) / 2 (s < 2N - 1), each FP64
+    value kept as a float32 pair (hi, lo = remainder).  With d = pi (i - j) / N,
+    f = pi (i + j) / N the ellipse points give
+    |x_i - x_j|^2 = sin^2(d) (1 + 3 sin^2(f)).  Returns (Sh, Sl, Ph, Pl)."""
+    m = np.arange(N, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        S = np.log(np.abs(np.sin(np.pi * m / N)))
+    S[0] = 0.0
+    t = np.arange(2 * N - 1, dtype=np.float64)
+    sn = np.sin(np.pi * t / N)
+    P = 0.5 * np.log1p(3.0 * sn * sn)
+    Sh, Ph = S.astype(np.float32), P.astype(np.float32)
+    Sl = (S - Sh.astype(np.float64)).astype(np.float32)
+    Pl = (P - Ph.astype(np.float64)).astype(np.float32)
+    return Sh, Sl, Ph, Pl
+
+
+def log_kernel_tab(N: int, rows=None, cols=None, tables=None) -> np.ndarray:
+    """Entries of the matrix-free log kernel: fl32(fl32(Sh + Ph) + fl32(Sl + Pl))
+    off the diagonal (float32 arithmetic throughout), 1 on it."""
+    Sh, Sl, Ph, Pl = tables if tables is not None else log_kernel_tables(N)
+    ri = np.arange(N) if rows is None else np.asarray(rows)
+    ci = np.arange(N) if cols is None else np.asarray(cols)
+    d = np.abs(ri[:, None] - ci[None, :])
+    s = ri[:, None] + ci[None, :]
+    A = (Sh[d] + Ph[s]) + (Sl[d] + Pl[s])  # float32 + float32 -> float32
+    A[d == 0] = np.float32(1.0)
+    return A.astype(np.float32)
+
+
 def batched_hodlr_specs(count: int = 64, seed: int = 4):
     """Sizes and ranks of the batched workload: N log-uniform in [2048, 32768]
     rounded to a multiple of 64, k uniform in [8, 40]; operator i is seeded 1000+i
