@@ -348,6 +348,56 @@ typedef struct {
 hm_status hm_set_profiling(int32_t on);
 hm_status hm_profile(const hm_handle* h, hm_phase_t* out, int32_t cap, int32_t* count);
 
+/*
+ * Fast direct solver for a HODLR handle (Sec. 1: fast inversion is what the
+ * compressed formats are for).  With A^(j) the block-diagonal part of A_c on
+ * the nodes of level j, A_c = D (I + W_L Z_L^T) ... (I + W_1 Z_1^T), where for a
+ * parent with children a, b: W = diag((A^(j)|a)^{-1} U_a, (A^(j)|b)^{-1} U_b) and
+ * Z^T = [[0, V_b^T], [V_a^T, 0]]; each factor is inverted by
+ * Sherman-Morrison-Woodbury with a 2k x 2k matrix per parent.
+ * hm_hodlr_factorize builds the factors (leaf inverses, W per level, the
+ * Woodbury matrices; O(k N log N) device memory held by the handle, O(k^2 N
+ * log^2 N) work; leaves of at most 256 points) and synchronizes the stream.
+ * HM_ENONFINITE if a leaf block or a Woodbury matrix is singular to working
+ * precision.  Calling it again recomputes the factors.
+ */
+hm_status hm_hodlr_factorize(hm_handle* h, void* stream);
+
+/*
+ * X = A_c^{-1} B (trans = 0) or A_c^{-T} B (trans = 1) for a factorized HODLR
+ * handle; B, X device, column-major, n x ncols, the handle's element type.
+ * O(k N log N) per column.  HM_EINVAL if the handle is not factorized.
+ */
+hm_status hm_solve(const hm_handle* h, int trans, int64_t ncols, const void* B, int64_t ldb,
+                   void* X, int64_t ldx, void* stream);
+
+/*
+ * Black box built from compressed handles (Sec. 5.2: operators such as the
+ * Neumann-to-Dirichlet map S (I/2 + D)^{-1} are compressed by peeling the
+ * product through its factors' fast applies and solves; Sec. 1: sums and
+ * products of rank-structured matrices).  The operator is
+ *   op(X) = alpha F_0 F_1 ... F_{nf-1} X + shift X,
+ * where F_i is, by kinds[i], handles[i] (HM_FACTOR_APPLY), its transpose
+ * (HM_FACTOR_TRANSPOSE), its inverse (HM_FACTOR_SOLVE) or its inverse
+ * transpose (HM_FACTOR_SOLVE_TRANSPOSE; the solves need a HODLR handle
+ * factorized by hm_hodlr_factorize).  Its transpose is applied exactly
+ * (reversed order, transposed factors), so it can be compressed like any black
+ * box.  All handles have the same n and element type (double: HM_FP64 and
+ * HM_A32, float: HM_MIXED); they are referenced, not copied, and must outlive
+ * the operator.  Each apply takes two n x ncols temporaries from the stream's
+ * memory pool.  Release with hm_product_operator_destroy.
+ */
+typedef enum {
+  HM_FACTOR_APPLY = 0,
+  HM_FACTOR_TRANSPOSE = 1,
+  HM_FACTOR_SOLVE = 2,
+  HM_FACTOR_SOLVE_TRANSPOSE = 3
+} hm_factor_kind;
+hm_status hm_product_operator_create(int32_t nf, const hm_handle* const* handles,
+                                     const int32_t* kinds, double alpha, double shift,
+                                     hm_operator* out);
+void hm_product_operator_destroy(hm_operator* op);
+
 /* Summary of the representation (ranks, black-box column counts, bytes M). */
 hm_status hm_info(const hm_handle* h, hm_info_t* out);
 /* Rank of the sibling block (node, node ^ 1) (HODLR) or of node's basis (HBS,

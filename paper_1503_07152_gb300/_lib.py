@@ -71,6 +71,11 @@ _sig = {
     "hm_destroy": ([_P], None),
     "hm_set_profiling": ([C.c_int32], C.c_int),
     "hm_profile": ([_P, C.POINTER(_Phase), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+    "hm_hodlr_factorize": ([_P, _P], C.c_int),
+    "hm_product_operator_create": ([C.c_int32, C.POINTER(_P), C.POINTER(C.c_int32), C.c_double,
+                                    C.c_double, C.POINTER(_Operator)], C.c_int),
+    "hm_product_operator_destroy": ([C.POINTER(_Operator)], None),
+    "hm_solve": ([_P, C.c_int, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
     "hm_skeleton": ([_P, C.c_int64, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)], C.c_int),
     "hm_hodlr_factored_apply": ([_P, C.c_int32, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
     "hm_hodlr_factored_apply_noalloc": ([_P, C.c_int32, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
@@ -156,12 +161,13 @@ def hm_tree_create(n: int, leaf_size: int) -> Tree:
 
 
 class Operator:
-    """A black box: the library's dense operator, or a Python callback."""
+    """A black box: the library's dense, matrix-free or product operator, or a Python callback."""
 
-    def __init__(self, op: _Operator, keep=None, dense: bool = False):
+    def __init__(self, op: _Operator, keep=None, dense: bool = False, product: bool = False):
         self.op = op
         self.keep = keep
         self.dense = dense
+        self.product = product
 
     @property
     def n(self):
@@ -170,6 +176,8 @@ class Operator:
     def __del__(self):
         if getattr(self, "dense", False) and self.op.ctx:
             lib.hm_dense_operator_destroy(C.byref(self.op))
+        if getattr(self, "product", False) and self.op.ctx:
+            lib.hm_product_operator_destroy(C.byref(self.op))
 
 
 def hm_dense_operator_create(A: torch.Tensor, fp64_blocks: bool = False,
@@ -341,6 +349,36 @@ def hm_node_rank(h: Handle, node: int) -> int:
     k = C.c_int32()
     _check(lib.hm_node_rank(h.ptr, node, C.byref(k)), "hm_node_rank")
     return k.value
+
+
+HM_FACTOR_APPLY, HM_FACTOR_TRANSPOSE, HM_FACTOR_SOLVE, HM_FACTOR_SOLVE_TRANSPOSE = 0, 1, 2, 3
+
+
+def hm_product_operator_create(handles: list, kinds: list, alpha: float = 1.0,
+                               shift: float = 0.0) -> Operator:
+    """Black box alpha F_0 ... F_{nf-1} X + shift X over compressed handles (kinds: HM_FACTOR_*)."""
+    nf = len(handles)
+    if len(kinds) != nf or nf < 1:
+        raise ValueError("one kind per handle, at least one handle")
+    arr = (_P * nf)(*[h.ptr for h in handles])
+    ks = (C.c_int32 * nf)(*kinds)
+    op = _Operator()
+    _check(lib.hm_product_operator_create(nf, arr, ks, float(alpha), float(shift), C.byref(op)),
+           "hm_product_operator_create")
+    return Operator(op, keep=list(handles), product=True)
+
+
+def hm_hodlr_factorize(h: Handle, stream=None) -> None:
+    """Factors of the fast direct solver of a HODLR handle (kept by the handle)."""
+    _check(lib.hm_hodlr_factorize(h.ptr, C.c_void_p(_stream(stream))), "hm_hodlr_factorize")
+
+
+def hm_solve(h: Handle, trans: int, B: torch.Tensor, X: torch.Tensor, stream=None) -> None:
+    """X = A_c^{-1} B (trans 0) or A_c^{-T} B; B, X as (ncols, ld) tensors (column-major blocks)."""
+    n = h.info["n"]
+    pb, ldb, ncols = _colmajor(B, n, "B")
+    px, ldx, _ = _colmajor(X, n, "X")
+    _check(lib.hm_solve(h.ptr, trans, ncols, pb, ldb, px, ldx, C.c_void_p(_stream(stream))), "hm_solve")
 
 
 def hm_set_profiling(on: bool) -> None:

@@ -228,6 +228,7 @@ hm_status hm_skeleton(const hm_handle* h, int64_t node, int32_t side, int64_t* i
 
 void hm_destroy(hm_handle* h) {
   if (!h) return;
+  if (h->solv) cudaFree(h->solv);
   if (h->U) cudaFree(h->U);
   if (h->V) cudaFree(h->V);
   if (h->D) cudaFree(h->D);

@@ -196,6 +196,20 @@ void launch_blockdiag_apply(const T* D, int nmax, int trans, const T* X, int64_t
 template <typename T>
 void launch_fill(T* p, int64_t count, T v, cudaStream_t st);
 
+// HODLR solver: inverses of a batch of n x n matrices held as [A | I] (n x 2n,
+// column-major) in `work`, by Gauss-Jordan with partial pivoting.
+template <typename T>
+void launch_gauss_jordan(T* work, int batch, int n, T* out, int* singular, cudaStream_t st);
+template <typename T>
+void launch_gj_load_leaves(const T* D, int nmax, const int64_t* d_size, int L, T* work,
+                           cudaStream_t st);
+template <typename T>
+void launch_gj_load_woodbury(const T* P, int r, int nparents, T* work, cudaStream_t st);
+// Y = alpha A + beta B (column-major n x ncols; B unread when beta == 0)
+template <typename T>
+void launch_axpby(T* Y, int64_t ldy, T alpha, const T* A, int64_t lda, T beta, const T* B,
+                  int64_t ldb, int64_t n, int64_t ncols, cudaStream_t st);
+
 template <typename T>
 void launch_copy_cols(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t rows,
                       int64_t cols, cudaStream_t st);
@@ -318,4 +332,8 @@ struct hm_handle {
   int64_t* skel = nullptr;                           // device skeleton indices
   hm_info_t info{};
   std::vector<hm_phase_t> prof;                      // phase profile (hm_profile)
+  // HODLR solver (hm_hodlr_factorize): leaf inverses, W_j = (A^(j))^{-1} U_j per
+  // level, Woodbury matrices M per parent; one device block
+  void* solv = nullptr;
+  int64_t solv_dinv = 0, solv_w = 0, solv_m = 0;  // element offsets
 };
