@@ -398,6 +398,20 @@ hm_status hm_product_operator_create(int32_t nf, const hm_handle* const* handles
                                      hm_operator* out);
 void hm_product_operator_destroy(hm_operator* op);
 
+/*
+ * Checkpoint of a compressed handle (HODLR or HBS-ID): hm_save writes the
+ * representation (its device arrays copied to the host, behind a header with
+ * the tree, rank and precision data and an FNV-1a checksum of the payload) to
+ * `path` (synchronizes the device); hm_load reads it back and builds an
+ * equivalent handle on the current device (the applies, reconstructions and
+ * infos of the loaded handle equal the saved one's bit for bit).  Solver
+ * factors are not stored: call hm_hodlr_factorize after loading.  hm_load
+ * returns HM_EINVAL for a file that is not a complete, uncorrupted checkpoint.
+ * The format is this build's: native byte order and struct layout.
+ */
+hm_status hm_save(const hm_handle* h, const char* path);
+hm_status hm_load(const char* path, void* stream, hm_handle** out);
+
 /* Summary of the representation (ranks, black-box column counts, bytes M). */
 hm_status hm_info(const hm_handle* h, hm_info_t* out);
 /* Rank of the sibling block (node, node ^ 1) (HODLR) or of node's basis (HBS,

@@ -72,6 +72,8 @@ _sig = {
     "hm_set_profiling": ([C.c_int32], C.c_int),
     "hm_profile": ([_P, C.POINTER(_Phase), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "hm_hodlr_factorize": ([_P, _P], C.c_int),
+    "hm_save": ([_P, C.c_char_p], C.c_int),
+    "hm_load": ([C.c_char_p, _P, C.POINTER(_P)], C.c_int),
     "hm_product_operator_create": ([C.c_int32, C.POINTER(_P), C.POINTER(C.c_int32), C.c_double,
                                     C.c_double, C.POINTER(_Operator)], C.c_int),
     "hm_product_operator_destroy": ([C.POINTER(_Operator)], None),
@@ -366,6 +368,18 @@ def hm_product_operator_create(handles: list, kinds: list, alpha: float = 1.0,
     _check(lib.hm_product_operator_create(nf, arr, ks, float(alpha), float(shift), C.byref(op)),
            "hm_product_operator_create")
     return Operator(op, keep=list(handles), product=True)
+
+
+def hm_save(h: Handle, path: str) -> None:
+    """Write the handle's representation to a checkpoint file."""
+    _check(lib.hm_save(h.ptr, os.fsencode(path)), "hm_save")
+
+
+def hm_load(path: str, stream=None) -> Handle:
+    """Rebuild a handle from a checkpoint file on the current device."""
+    h = C.c_void_p()
+    _check(lib.hm_load(os.fsencode(path), C.c_void_p(_stream(stream)), C.byref(h)), "hm_load")
+    return Handle(h)
 
 
 def hm_hodlr_factorize(h: Handle, stream=None) -> None:

@@ -56,3 +56,15 @@ def test_argument_errors_before_device_use():
     with pytest.raises(hm.HmError):
         hm.hm_compress_hodlr(op, t, tol=2.0, r=8, stream=0)
     assert hm.hm_version().startswith("hm")
+
+
+def test_load_rejects_garbage_without_a_device(tmp_path):
+    """hm_load validates the header and checksum before any device call."""
+    p = tmp_path / "junk.hm"
+    p.write_bytes(bytes(range(256)) * 4)
+    with pytest.raises(hm.HmError) as e:
+        hm.hm_load(str(p), stream=0)
+    assert e.value.status == 1
+    with pytest.raises(hm.HmError) as e:
+        hm.hm_load(str(tmp_path / "missing.hm"), stream=0)
+    assert e.value.status == 1
