@@ -209,7 +209,10 @@ def callback_operator(n: int, fn) -> Operator:
     def tramp(ctx, trans, nn, ncols, X, ldx, Y, ldy, stream):
         try:
             return int(fn(trans, X, ldx, Y, ldy, ncols, stream))
-        except Exception:  # an exception must not cross the C boundary
+        except Exception:  # an exception must not cross the C boundary: report it, fail the call
+            import sys
+            import traceback
+            traceback.print_exc(file=sys.stderr)
             return 99
     cb = APPLY_FN(tramp)
     op = _Operator(cb, None, n)

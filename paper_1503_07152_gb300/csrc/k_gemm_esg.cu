@@ -313,11 +313,12 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     // values of each table, staged in the (unused) raw stage: window entry e
     // holds S[|d|] for i - j = d = dbase + e, and P[m0 + k0 + e].
     int it = 0, xissued = 0;
-    constexpr int WN = TM + TK;  // window stride (TM + TK - 1 used)
-    float* swh = reinterpret_cast<float*>(sbase);
-    float* swl = swh + WN;
-    float* pwh = swl + WN;
-    float* pwl = pwh + WN;
+    // Four shifted copies of each window (copy q holds window entry x + q at x),
+    // so that every thread reads its four consecutive entries of a table as one
+    // aligned float4: for row m the P entries start at m + 4 k4 and the S entries
+    // (descending) at m - 4 k4 + 60, both congruent to m mod 4.
+    constexpr int WC = 196;  // floats per copy (16-byte multiple, covers index 193)
+    float* win = reinterpret_cast<float*>(sbase);  // [table (Sh, Sl, Ph, Pl)][q][WC]
     for (int kt = 0; kt < nkt; ++kt) {
       const int fl = active(kt);  // the same for every cutter
       if (!fl) continue;
@@ -338,13 +339,20 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       }
       const int64_t k0 = (int64_t)kt * TK;
       const int64_t dbase = m0 - k0 - (TK - 1);
-      for (int e = tid; e < TM + TK - 1; e += NCONV) {
-        const int64_t d = dbase + e, ad = d < 0 ? -d : d, sidx = m0 + k0 + e;
-        const bool sin_ = ad > 0 && ad < n, pin = sidx < 2 * n - 1;
-        swh[e] = sin_ ? tabS[ad] : 0.f;
-        swl[e] = sin_ ? tabS[n + ad] : 0.f;
-        pwh[e] = pin ? tabP[sidx] : 0.f;
-        pwl[e] = pin ? tabP[2 * n - 1 + sidx] : 0.f;
+      for (int e = tid; e < WC + 3; e += NCONV) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (e < TM + TK - 1) {
+          const int64_t d = dbase + e, ad = d < 0 ? -d : d, sidx = m0 + k0 + e;
+          if (ad > 0 && ad < n) { v[0] = tabS[ad]; v[1] = tabS[n + ad]; }
+          if (sidx < 2 * n - 1) { v[2] = tabP[sidx]; v[3] = tabP[2 * n - 1 + sidx]; }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int x = e - q;
+          if (x >= 0 && x < WC)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) win[(a * 4 + q) * WC + x] = v[a];
+        }
       }
       cutters_sync();
       // tiles that hold a diagonal entry or reach past n take the per-entry fixes
@@ -357,11 +365,19 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       for (int p = 0; p < 8; ++p) {
         const int f = p * NCONV + tid, m = f >> 4, k4 = f & 15;
         const float sc = srow[m];
-        const int ds = m - 4 * k4 + (TK - 1), ps = m + 4 * k4;
+        const int q = m & 3, ps = m + 4 * k4 - q, ds = m - 4 * k4 + (TK - 4) - q;
+        const float4 sh4 = *reinterpret_cast<const float4*>(win + (0 * 4 + q) * WC + ds);
+        const float4 sl4 = *reinterpret_cast<const float4*>(win + (1 * 4 + q) * WC + ds);
+        const float4 ph4 = *reinterpret_cast<const float4*>(win + (2 * 4 + q) * WC + ps);
+        const float4 pl4 = *reinterpret_cast<const float4*>(win + (3 * 4 + q) * WC + ps);
+        // entry e: S at window index m - 4 k4 + 63 - e (component 3 - e of the S
+        // float4), P at m + 4 k4 + e (component e)
+        const float shv[4] = {sh4.w, sh4.z, sh4.y, sh4.x}, slv[4] = {sl4.w, sl4.z, sl4.y, sl4.x};
+        const float phv[4] = {ph4.x, ph4.y, ph4.z, ph4.w}, plv[4] = {pl4.x, pl4.y, pl4.z, pl4.w};
         float a[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          float v = (swh[ds - e] + pwh[ps + e]) + (swl[ds - e] + pwl[ps + e]);
+          float v = (shv[e] + phv[e]) + (slv[e] + plv[e]);
           if (fix) {
             const int kk = 4 * k4 + e;
             if (m - kk == dk) v = 1.f;

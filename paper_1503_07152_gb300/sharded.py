@@ -82,7 +82,10 @@ class RowShardedOperator:
         def fn(trans, X, ldx, Y, ldy, ncols, stream):
             xs = torch.as_tensor(_DeviceBlock(X, ncols, ldx), device=dev)[:, :n]
             ys = torch.as_tensor(_DeviceBlock(Y, ncols, ldy), device=dev)[:, :n]
-            with torch.cuda.stream(torch.cuda.ExternalStream(stream, device=dev)):
+            # a null stream is the legacy default stream, torch's default stream
+            strm = (torch.cuda.ExternalStream(stream, device=dev) if stream
+                    else torch.cuda.default_stream(dev))
+            with torch.cuda.stream(strm):
                 ys.copy_(self.apply(xs, trans))
             return 0
         return _lib.callback_operator(n, fn)
