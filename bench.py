@@ -294,9 +294,14 @@ def adjoint_bench(hm, torch, dev, steps, warmup):
     ms = time_events(step, steps, torch)
     fbytes = 4.0 * (U.numel() + V.numel() + D.numel())
     moved = 2 * fbytes + fbytes + 4.0 * n * 8  # read factors twice, write gradients once
+    peak, kind = peaks()
     return {"value": round(1000.0 / ms, 2), "unit": "(forward + adjoint) applies/s",
             "ms_per_apply_pair": round(ms, 4), "config": {"n": n, "k": k, "leaf": m, "levels": L},
-            "bytes_per_pair": moved, "achieved_GBs": round(moved / (ms * 1e-3) / 1e9, 1)}
+            "bytes_per_pair": moved, "achieved_GBs": round(moved / (ms * 1e-3) / 1e9, 1),
+            "frac": round(moved / (ms * 1e-3) / 1e9 / peak, 4), "peak_GBs": peak,
+            "path": "hm_hodlr_factored_apply + hm_hodlr_factored_adjoint",
+            "bytes_definition": "factors U, V, D read by the forward apply and by the adjoint, "
+                                "their gradients written once, x / b / y / gx vectors"}
 
 
 def batched_bench(hm, torch, dev, count=64):

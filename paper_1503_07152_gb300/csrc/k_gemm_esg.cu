@@ -311,7 +311,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     // A(i, j) = (S[|i - j|] + P[i + j]) in float pairs: fl((Sh + Ph) + (Sl + Pl)),
     // 1 on the diagonal, 0 outside [0, n).  A tile's entries use TM + TK - 1
     // values of each table, staged in the (unused) raw stage: window entry e
-    // holds S[|d|] for i - j = d = dbase + e, and P[m0 + k0 + e].
+    // holds S[|d|] for i - j = d = m0 - k0 - (TK - 1) + e, and P[m0 + k0 + e].
     int it = 0, xissued = 0;
     // Four shifted copies of each window (copy q holds window entry x + q at x),
     // so that every thread reads its four consecutive entries of a table as one
@@ -319,6 +319,29 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     // (descending) at m - 4 k4 + 60, both congruent to m mod 4.
     constexpr int WC = 196;  // floats per copy (16-byte multiple, covers index 193)
     float* win = reinterpret_cast<float*>(sbase);  // [table (Sh, Sl, Ph, Pl)][q][WC]
+    // Thread e (< WC + 3 <= NCONV) owns window entry e.  The next active tile's
+    // entry is loaded from the (L2-resident) tables one tile ahead, so the load
+    // latency hides behind the current tile's cut.
+    float pv[4] = {0.f, 0.f, 0.f, 0.f};
+    auto load_win = [&](int ktn) {
+      pv[0] = pv[1] = pv[2] = pv[3] = 0.f;
+      const int e = tid;
+      if (e < TM + TK - 1) {
+        const int64_t kn = (int64_t)ktn * TK;
+        const int64_t d = m0 - kn - (TK - 1) + e, ad = d < 0 ? -d : d, sidx = m0 + kn + e;
+        if (ad > 0 && ad < n) { pv[0] = tabS[ad]; pv[1] = tabS[n + ad]; }
+        if (sidx < 2 * n - 1) { pv[2] = tabP[sidx]; pv[3] = tabP[2 * n - 1 + sidx]; }
+      }
+    };
+    auto next_active = [&](int from) {
+      int k = from;
+      while (k < nkt && !active(k)) ++k;
+      return k;
+    };
+    {
+      const int k1 = next_active(0);
+      if (k1 < nkt) load_win(k1);
+    }
     for (int kt = 0; kt < nkt; ++kt) {
       const int fl = active(kt);  // the same for every cutter
       if (!fl) continue;
@@ -338,21 +361,19 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
         xissued = it + 1;
       }
       const int64_t k0 = (int64_t)kt * TK;
-      const int64_t dbase = m0 - k0 - (TK - 1);
-      for (int e = tid; e < WC + 3; e += NCONV) {
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (e < TM + TK - 1) {
-          const int64_t d = dbase + e, ad = d < 0 ? -d : d, sidx = m0 + k0 + e;
-          if (ad > 0 && ad < n) { v[0] = tabS[ad]; v[1] = tabS[n + ad]; }
-          if (sidx < 2 * n - 1) { v[2] = tabP[sidx]; v[3] = tabP[2 * n - 1 + sidx]; }
-        }
+      {
+        const int e = tid;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int x = e - q;
           if (x >= 0 && x < WC)
 #pragma unroll
-            for (int a = 0; a < 4; ++a) win[(a * 4 + q) * WC + x] = v[a];
+            for (int a = 0; a < 4; ++a) win[(a * 4 + q) * WC + x] = pv[a];
         }
+      }
+      {
+        const int k1 = next_active(kt + 1);
+        if (k1 < nkt) load_win(k1);
       }
       cutters_sync();
       // tiles that hold a diagonal entry or reach past n take the per-entry fixes

@@ -272,3 +272,4 @@ def test_dense_apply_a32():
         A64 = A.astype(np.float64)
         want = (A64.T if trans else A64) @ X
         assert np.max(np.abs(Y.cpu().numpy().T - want)) <= 1e-13 * np.max(np.abs(want))
+
