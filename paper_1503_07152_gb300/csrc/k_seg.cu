@@ -19,16 +19,23 @@ namespace {
 constexpr int TN_ROWS = 32;   // rows staged per step
 constexpr int TN_MAX = 128;   // max ka, kb
 
-// Partial products of one chunk (<= 256 rows).  256 threads in a 16 x 16 grid,
-// 8 x 8 outputs each.
-template <typename T>
+// Per-thread tile for a product of ka x kb outputs: 256 threads in a 16 x 16
+// grid, thread (ti, tj) owning rows ti + 16 i (i < TI) and columns tj + 16 j
+// (j < TJ), so a warp reads 16 consecutive staged columns of B (no bank
+// conflicts) and only the 16 TI x 16 TJ outputs that cover ka x kb are computed.
+// Which thread owns an output changes nothing in how it is summed.
+constexpr int tn_tile(int k) { return k <= 32 ? 2 : (k <= 64 ? 4 : 8); }
+
+// Partial products of one chunk (<= 256 rows).
+template <typename T, int TI, int TJ>
 __global__ __launch_bounds__(256) void k_seg_tn_partial(
     const Chunk* __restrict__ chunks, const T* __restrict__ A, int64_t lda, int aoff_e,
     int aoff_o, int ka, const T* __restrict__ B, int64_t ldb, int boff_e, int boff_o, int kb,
     double* __restrict__ partial) {
+  constexpr int KA = 16 * TI, KB = 16 * TJ, LDA = KA + 1, LDB = KB + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* As = reinterpret_cast<T*>(smem_raw);          // [TN_ROWS][TN_MAX + 1]
-  T* Bs = As + TN_ROWS * (TN_MAX + 1);              // [TN_ROWS][TN_MAX + 1]
+  T* As = reinterpret_cast<T*>(smem_raw);  // [TN_ROWS][LDA]
+  T* Bs = As + TN_ROWS * LDA;              // [TN_ROWS][LDB]
   const Chunk ch = chunks[blockIdx.x];
   const int aoff = (ch.node & 1) ? aoff_o : aoff_e;
   const int boff = (ch.node & 1) ? boff_o : boff_e;
@@ -37,52 +44,53 @@ __global__ __launch_bounds__(256) void k_seg_tn_partial(
   // products summed in T over at most 16 rows, then added into FP64 sums: the
   // projections of the peel are differences of large sums, so a long FP32 sum
   // would cost far more than its unit roundoff
-  double acc[8][8];
+  double acc[TI][TJ];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < TI; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TJ; ++j) acc[i][j] = 0.0;
   for (int64_t r0 = ch.r0; r0 < ch.r1; r0 += TN_ROWS) {
     const int rows = (int)((ch.r1 - r0) < TN_ROWS ? (ch.r1 - r0) : TN_ROWS);
-    for (int idx = tid; idx < TN_ROWS * TN_MAX; idx += 256) {
+    for (int idx = tid; idx < TN_ROWS * KA; idx += 256) {
       const int rr = idx % TN_ROWS, c = idx / TN_ROWS;
-      As[rr * (TN_MAX + 1) + c] =
-          (rr < rows && c < ka) ? A[r0 + rr + (int64_t)(aoff + c) * lda] : (T)0;
-      Bs[rr * (TN_MAX + 1) + c] =
-          (rr < rows && c < kb) ? B[r0 + rr + (int64_t)(boff + c) * ldb] : (T)0;
+      As[rr * LDA + c] = (rr < rows && c < ka) ? A[r0 + rr + (int64_t)(aoff + c) * lda] : (T)0;
+    }
+    for (int idx = tid; idx < TN_ROWS * KB; idx += 256) {
+      const int rr = idx % TN_ROWS, c = idx / TN_ROWS;
+      Bs[rr * LDB + c] = (rr < rows && c < kb) ? B[r0 + rr + (int64_t)(boff + c) * ldb] : (T)0;
     }
     __syncthreads();
     for (int q0 = 0; q0 < rows; q0 += 16) {
       const int q1 = (q0 + 16 < rows) ? q0 + 16 : rows;
-      T tmp[8][8];
+      T tmp[TI][TJ];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < TI; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) tmp[i][j] = 0;
+        for (int j = 0; j < TJ; ++j) tmp[i][j] = 0;
       for (int rr = q0; rr < q1; ++rr) {
-        T a[8], b[8];
+        T a[TI], b[TJ];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = As[rr * (TN_MAX + 1) + ti * 8 + i];
+        for (int i = 0; i < TI; ++i) a[i] = As[rr * LDA + ti + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) b[j] = Bs[rr * (TN_MAX + 1) + tj * 8 + j];
+        for (int j = 0; j < TJ; ++j) b[j] = Bs[rr * LDB + tj + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < TI; ++i)
 #pragma unroll
-          for (int j = 0; j < 8; ++j) tmp[i][j] = fma(a[i], b[j], tmp[i][j]);
+          for (int j = 0; j < TJ; ++j) tmp[i][j] = fma(a[i], b[j], tmp[i][j]);
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < TI; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] += (double)tmp[i][j];
+        for (int j = 0; j < TJ; ++j) acc[i][j] += (double)tmp[i][j];
     }
     __syncthreads();
   }
   double* out = partial + (int64_t)blockIdx.x * ka * kb;
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < TI; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int ii = ti * 8 + i, jj = tj * 8 + j;
+    for (int j = 0; j < TJ; ++j) {
+      const int ii = ti + 16 * i, jj = tj + 16 * j;
       if (ii < ka && jj < kb) out[ii + jj * ka] = acc[i][j];
     }
 }
@@ -98,55 +106,60 @@ __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
   lo = (float)(x - (double)hi);
 }
 
+template <int TI, int TJ>
 __global__ __launch_bounds__(256) void k_seg_tn_partial_df(
     const Chunk* __restrict__ chunks, const double* __restrict__ A, int64_t lda, int aoff_e,
     int aoff_o, int ka, const double* __restrict__ B, int64_t ldb, int boff_e, int boff_o,
     int kb, double* __restrict__ partial) {
+  constexpr int KA = 16 * TI, KB = 16 * TJ, LDA = KA + 1, LDB = KB + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int LD = TN_MAX + 1;
-  float* Ah = reinterpret_cast<float*>(smem_raw);  // [TN_ROWS][LD] each
-  float* Al = Ah + TN_ROWS * LD;
-  float* Bh = Al + TN_ROWS * LD;
-  float* Bl = Bh + TN_ROWS * LD;
+  float* Ah = reinterpret_cast<float*>(smem_raw);  // [TN_ROWS][LDA] each
+  float* Al = Ah + TN_ROWS * LDA;
+  float* Bh = Al + TN_ROWS * LDA;                  // [TN_ROWS][LDB] each
+  float* Bl = Bh + TN_ROWS * LDB;
   const Chunk ch = chunks[blockIdx.x];
   const int aoff = (ch.node & 1) ? aoff_o : aoff_e;
   const int boff = (ch.node & 1) ? boff_o : boff_e;
   const int tid = threadIdx.x;
   const int ti = tid >> 4, tj = tid & 15;
-  float sh[8][8], sl[8][8];
+  float sh[TI][TJ], sl[TI][TJ];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < TI; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
+    for (int j = 0; j < TJ; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
   for (int64_t r0 = ch.r0; r0 < ch.r1; r0 += TN_ROWS) {
     const int rows = (int)((ch.r1 - r0) < TN_ROWS ? (ch.r1 - r0) : TN_ROWS);
-    for (int idx = tid; idx < TN_ROWS * TN_MAX; idx += 256) {
+    for (int idx = tid; idx < TN_ROWS * KA; idx += 256) {
       const int rr = idx % TN_ROWS, c = idx / TN_ROWS;
       float h, l;
       split_df((rr < rows && c < ka) ? A[r0 + rr + (int64_t)(aoff + c) * lda] : 0.0, h, l);
-      Ah[rr * LD + c] = h;
-      Al[rr * LD + c] = l;
+      Ah[rr * LDA + c] = h;
+      Al[rr * LDA + c] = l;
+    }
+    for (int idx = tid; idx < TN_ROWS * KB; idx += 256) {
+      const int rr = idx % TN_ROWS, c = idx / TN_ROWS;
+      float h, l;
       split_df((rr < rows && c < kb) ? B[r0 + rr + (int64_t)(boff + c) * ldb] : 0.0, h, l);
-      Bh[rr * LD + c] = h;
-      Bl[rr * LD + c] = l;
+      Bh[rr * LDB + c] = h;
+      Bl[rr * LDB + c] = l;
     }
     __syncthreads();
     for (int rr = 0; rr < rows; ++rr) {
-      float ah[8], al[8], bh[8], bl[8];
+      float ah[TI], al[TI], bh[TJ], bl[TJ];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        ah[i] = Ah[rr * LD + ti * 8 + i];
-        al[i] = Al[rr * LD + ti * 8 + i];
+      for (int i = 0; i < TI; ++i) {
+        ah[i] = Ah[rr * LDA + ti + 16 * i];
+        al[i] = Al[rr * LDA + ti + 16 * i];
       }
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        bh[j] = Bh[rr * LD + tj * 8 + j];
-        bl[j] = Bl[rr * LD + tj * 8 + j];
+      for (int j = 0; j < TJ; ++j) {
+        bh[j] = Bh[rr * LDB + tj + 16 * j];
+        bl[j] = Bl[rr * LDB + tj + 16 * j];
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < TI; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < TJ; ++j) {
           const float p = ah[i] * bh[j];
           const float e = fmaf(ah[i], bh[j], -p);               // hi hi - p, exact
           const float t = fmaf(ah[i], bl[j], fmaf(al[i], bh[j], e));
@@ -161,10 +174,10 @@ __global__ __launch_bounds__(256) void k_seg_tn_partial_df(
   }
   double* out = partial + (int64_t)blockIdx.x * ka * kb;
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < TI; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int ii = ti * 8 + i, jj = tj * 8 + j;
+    for (int j = 0; j < TJ; ++j) {
+      const int ii = ti + 16 * i, jj = tj + 16 * j;
       if (ii < ka && jj < kb) out[ii + jj * ka] = (double)sh[i][j] + (double)sl[i][j];
     }
 }
@@ -328,6 +341,48 @@ __global__ __launch_bounds__(256) void k_seg_nn_df(
 
 }  // namespace
 
+template <typename T, int TI, int TJ>
+void seg_tn_partial_tiled(const Chunk* chunks, int nchunks, const T* A, int64_t lda,
+                          int aoff_even, int aoff_odd, int ka, const T* B, int64_t ldb,
+                          int boff_even, int boff_odd, int kb, double* partial, cudaStream_t st,
+                          bool df) {
+  constexpr int LDA = 16 * TI + 1, LDB = 16 * TJ + 1;
+  if (sizeof(T) == 8 && df) {
+    const size_t smem = 2 * TN_ROWS * (LDA + LDB) * sizeof(float);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_seg_tn_partial_df<TI, TJ>, done);
+    k_seg_tn_partial_df<TI, TJ><<<nchunks, 256, smem, st>>>(
+        chunks, (const double*)A, lda, aoff_even, aoff_odd, ka, (const double*)B, ldb, boff_even,
+        boff_odd, kb, partial);
+  } else {
+    const size_t smem = TN_ROWS * (LDA + LDB) * sizeof(T);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_seg_tn_partial<T, TI, TJ>, done);
+    k_seg_tn_partial<T, TI, TJ><<<nchunks, 256, smem, st>>>(
+        chunks, A, lda, aoff_even, aoff_odd, ka, B, ldb, boff_even, boff_odd, kb, partial);
+  }
+}
+
+template <typename T, int TI>
+void seg_tn_partial_pick_j(const Chunk* chunks, int nchunks, const T* A, int64_t lda,
+                           int aoff_even, int aoff_odd, int ka, const T* B, int64_t ldb,
+                           int boff_even, int boff_odd, int kb, double* partial, cudaStream_t st,
+                           bool df) {
+  switch (tn_tile(kb)) {
+    case 2:
+      seg_tn_partial_tiled<T, TI, 2>(chunks, nchunks, A, lda, aoff_even, aoff_odd, ka, B, ldb,
+                                     boff_even, boff_odd, kb, partial, st, df);
+      break;
+    case 4:
+      seg_tn_partial_tiled<T, TI, 4>(chunks, nchunks, A, lda, aoff_even, aoff_odd, ka, B, ldb,
+                                     boff_even, boff_odd, kb, partial, st, df);
+      break;
+    default:
+      seg_tn_partial_tiled<T, TI, 8>(chunks, nchunks, A, lda, aoff_even, aoff_odd, ka, B, ldb,
+                                     boff_even, boff_odd, kb, partial, st, df);
+  }
+}
+
 template <typename T>
 void launch_seg_tn(const Chunk* chunks, int nchunks, const int32_t* chunk_begin, int nnodes,
                    int node0, const T* A, int64_t lda, int aoff_even, int aoff_odd, int ka,
@@ -335,18 +390,18 @@ void launch_seg_tn(const Chunk* chunks, int nchunks, const int32_t* chunk_begin,
                    T* out, cudaStream_t st, bool df) {
   count_launches(2);
   (void)node0;
-  const size_t smem = 2 * TN_ROWS * (TN_MAX + 1) * sizeof(T);  // the df form: 4 float planes
-  if (sizeof(T) == 8 && df) {
-    static std::atomic<uint32_t> done{0};
-    raise_smem_limit((const void*)k_seg_tn_partial_df, done);
-    k_seg_tn_partial_df<<<nchunks, 256, smem, st>>>(chunks, (const double*)A, lda, aoff_even,
-                                                    aoff_odd, ka, (const double*)B, ldb,
-                                                    boff_even, boff_odd, kb, partial);
-  } else {
-    static std::atomic<uint32_t> done{0};
-    raise_smem_limit((const void*)k_seg_tn_partial<T>, done);
-    k_seg_tn_partial<T><<<nchunks, 256, smem, st>>>(chunks, A, lda, aoff_even, aoff_odd, ka, B,
-                                                    ldb, boff_even, boff_odd, kb, partial);
+  switch (tn_tile(ka)) {
+    case 2:
+      seg_tn_partial_pick_j<T, 2>(chunks, nchunks, A, lda, aoff_even, aoff_odd, ka, B, ldb,
+                                  boff_even, boff_odd, kb, partial, st, df);
+      break;
+    case 4:
+      seg_tn_partial_pick_j<T, 4>(chunks, nchunks, A, lda, aoff_even, aoff_odd, ka, B, ldb,
+                                  boff_even, boff_odd, kb, partial, st, df);
+      break;
+    default:
+      seg_tn_partial_pick_j<T, 8>(chunks, nchunks, A, lda, aoff_even, aoff_odd, ka, B, ldb,
+                                  boff_even, boff_odd, kb, partial, st, df);
   }
   const int m = ka * kb;
   dim3 grid((unsigned)((m + 255) / 256), (unsigned)nnodes);
