@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-frob", action="store_true", help="skip the full Frobenius error check")
     ap.add_argument("--skip-mixed", action="store_true", help="skip the HM_MIXED comparison run")
+    ap.add_argument("--skip-fp64", action="store_true", help="skip the HM_FP64 comparison run")
     ap.add_argument("--skip-batched", action="store_true", help="skip the batched many-operator run")
     ap.add_argument("--skip-matrix-free", action="store_true",
                     help="skip the matrix-free log-kernel runs")
@@ -501,6 +502,31 @@ def run_gpu(args):
                  "t_blackbox_ms": round(hm_.info["t_blackbox_ms"], 3),
                  "ranks": [hm_.info["min_rank"], hm_.info["max_rank"]]}
         del hm_, opm
+    # the all-FP64 compression beside it: the same FP32 entries widened to an FP64
+    # operator (34 GB at N=65536), FP64 black box on the CUDA cores; one run
+    fp64 = None
+    if not args.skip_fp64:
+        A64 = A.double()
+        op64 = hm.hm_dense_operator_create(A64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h64 = hm.hm_compress_hbs(op64, tree, **dict(kw, prec=hm.HM_FP64))
+        e1.record()
+        torch.cuda.synchronize()
+        Yt64, Yc64 = torch.empty_like(Wv), torch.empty_like(Wv)
+        hm.hm_dense_apply(op64, 0, Wv, Yt64)
+        hm.hm_apply(h64, 0, Wv, Yc64)
+        torch.cuda.synchronize()
+        fp64 = {"ms": round(e0.elapsed_time(e1), 3),
+                "precision": "HM_FP64 (FP64 operator holding the same FP32 entries, FP64 black box "
+                             "on the CUDA cores, FP64 samples, bases and ID)",
+                "estimate_E": float(((Yt64 - Yc64).norm(dim=1) / Yt64.norm(dim=1)).max()),
+                "t_blackbox_ms": round(h64.info["t_blackbox_ms"], 3),
+                "ranks": [h64.info["min_rank"], h64.info["max_rank"]],
+                "note": "one run without warm-up, outside the timed region"}
+        del h64, op64, A64, Yt64, Yc64
+        torch.cuda.empty_cache()
     roof = gemm_roofline(hm, torch, A, op, tree, n, peak_gbs, peak_kind)
     info = infos[-1]
     # the whole compression against the HBM roofline: the two black-box calls of a
@@ -586,6 +612,7 @@ def run_gpu(args):
                     "note": "relative Frobenius error of this run's compressed matrix against the "
                             "FP32 operator over all N^2 entries; E: max over 10 unit vectors"},
         "mixed": mixed,
+        "fp64": fp64,
         "compress": {"t_compress_ms": round(info["t_compress_ms"], 3),
                      "t_blackbox_ms": round(info["t_blackbox_ms"], 3),
                      "blackbox_share": None if bb_share is None else round(bb_share, 3),

@@ -67,6 +67,24 @@ def test_hbsid_a32_n65536_sampled_rows():
     assert hm.hm_rel_frob_error(h, A) <= 1e-7
 
 
+@pytest.mark.parametrize("N,seed", [(65536, 3), (65536, 4), (49152, 2)])
+def test_hbsid_a32_tolerance_holds_at_other_seeds_and_sizes(N, seed):
+    """The ID threshold scale (0.004 tol times the level-1 sample scale) was set on
+    the measured N = 65536 workload with seed 2; the same configuration at other
+    test-matrix seeds and at another N must stay within the tolerance over all N^2
+    entries."""
+    m, tol, r = 256, 1e-7, 60
+    A = torch.empty((N, N), device=DEV, dtype=torch.float32)
+    hm.hm_gen_log_kernel(A)
+    op = hm.hm_dense_operator_create(A, fp64_blocks=True, tensor_cores=True)
+    h = hm.hm_compress_hbs(op, hm.Tree(N, m), tol=tol, r=r, seed=seed, prec=hm.HM_A32, hbs_id=1)
+    err = hm.hm_rel_frob_error(h, A)
+    print(f"HBS-ID N={N} seed={seed}: relative Frobenius error {err:.3e}, ranks "
+          f"{h.info['min_rank']}..{h.info['max_rank']}, saturated {h.info['saturated']}")
+    assert h.info["saturated"] == 0
+    assert err <= tol
+
+
 @pytest.mark.parametrize("prec,bound", [(2, 1e-7), (1, 1e-5)])
 def test_hodlr_log_kernel_n16384_full_error(prec, bound):
     N, m, tol, r = 16384, 128, 1e-7, 60
