@@ -187,13 +187,22 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
         float* mkh = Mh + (on ? k : j) * c;
         float* mkl = Ml + (on ? k : j) * c;
         float dh = 0.f, dl = 0.f;
-        if (on)
-          for (int i = j + gl; i < c; i += 8) df::dot_acc(mjh[i], mjl[i], mkh[i], mkl[i], dh, dl);
+        if (on) {
+#pragma unroll
+          for (int ii = 0; ii < 16; ++ii) {
+            const int i = j + gl + 8 * ii;
+            if (i < c) df::dot_acc(mjh[i], mjl[i], mkh[i], mkl[i], dh, dl);
+          }
+        }
         df::group8_sum(dh, dl);
         if (on) {
           float fh, fl;
           df::fast_two_sum(dh, dl, fh, fl);
-          for (int i = j + gl; i < c; i += 8) df::axpy_neg(fh, fl, mjh[i], mjl[i], mkh[i], mkl[i]);
+#pragma unroll
+          for (int ii = 0; ii < 16; ++ii) {
+            const int i = j + gl + 8 * ii;
+            if (i < c) df::axpy_neg(fh, fl, mjh[i], mjl[i], mkh[i], mkl[i]);
+          }
         }
       }
     }
@@ -233,6 +242,8 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
   }
   __syncthreads();
   {
+    // (element loops over a fixed 16 strided elements per lane, c <= 128, so
+    // that they unroll; the arithmetic and its order are those of the plain loops)
     const float tol = (float)(5.960464477539063e-08 * sqrt((double)c));
     const float big2 = tol;
     for (int sweep = 0; sweep < 40; ++sweep) {
@@ -242,15 +253,24 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
         int p = c, q = c;
         if (pg < cp / 2) {
           const int a = pg, b = cp - 1 - pg;
-          p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
-          q = ((b - 1 + step) % (cp - 1)) + 1;
+          // round-robin pairing: a - 1 + step < 2 (cp - 1) and b - 1 + step < 2 (cp - 1)
+          int va = a - 1 + step, vb = b - 1 + step;
+          if (va >= cp - 1) va -= cp - 1;
+          if (vb >= cp - 1) vb -= cp - 1;
+          p = (a == 0) ? 0 : va + 1;
+          q = vb + 1;
         }
         const bool valid = p < c && q < c;
         float* ap = X32 + (valid ? p : 0) * c;
         float* aq = X32 + (valid ? q : 0) * c;
         float ga = 0;
-        if (valid)
-          for (int i = gl; i < c; i += 8) ga = fmaf(ap[i], aq[i], ga);
+        if (valid) {
+#pragma unroll
+          for (int ii = 0; ii < 16; ++ii) {
+            const int i = gl + 8 * ii;
+            if (i < c) ga = fmaf(ap[i], aq[i], ga);
+          }
+        }
         ga += __shfl_xor_sync(0xffffffffu, ga, 4);
         ga += __shfl_xor_sync(0xffffffffu, ga, 2);
         ga += __shfl_xor_sync(0xffffffffu, ga, 1);
@@ -261,17 +281,25 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
             const float zeta = (be - al) / (2.f * ga);
             const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
             const float tc = 1.f / sqrtf(1.f + t * t), ts = tc * t;
-            for (int i = gl; i < c; i += 8) {
-              const float x = ap[i], y = aq[i];
-              ap[i] = tc * x - ts * y;
-              aq[i] = ts * x + tc * y;
-            }
             float* vp = V32 + p * c;
             float* vq = V32 + q * c;
-            for (int i = gl; i < c; i += 8) {
-              const float x = vp[i], y = vq[i];
-              vp[i] = tc * x - ts * y;
-              vq[i] = ts * x + tc * y;
+#pragma unroll
+            for (int ii = 0; ii < 16; ++ii) {
+              const int i = gl + 8 * ii;
+              if (i < c) {
+                const float x = ap[i], y = aq[i];
+                ap[i] = tc * x - ts * y;
+                aq[i] = ts * x + tc * y;
+              }
+            }
+#pragma unroll
+            for (int ii = 0; ii < 16; ++ii) {
+              const int i = gl + 8 * ii;
+              if (i < c) {
+                const float x = vp[i], y = vq[i];
+                vp[i] = tc * x - ts * y;
+                vq[i] = ts * x + tc * y;
+              }
             }
             if (gl == 0) {
               const float cs2 = 2.f * tc * ts, c2 = tc * tc, s2 = ts * ts;
@@ -301,8 +329,13 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
       const float* qih = Qh + (on ? i : 0) * c;
       const float* qil = Ql + (on ? i : 0) * c;
       float sh = 0.f, sl = 0.f;
-      if (on)
-        for (int e = gl; e < c; e += 8) df::dot_acc(qih[e], qil[e], qjh[e], qjl[e], sh, sl);
+      if (on) {
+#pragma unroll
+        for (int ee = 0; ee < 16; ++ee) {
+          const int e = gl + 8 * ee;
+          if (e < c) df::dot_acc(qih[e], qil[e], qjh[e], qjl[e], sh, sl);
+        }
+      }
       df::group8_sum(sh, sl);
       if (on && gl == 0) { hbh[i] = sh; hbl[i] = sl; }
     }
@@ -381,8 +414,11 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
         int p = c, q = c;
         if (pg < cp / 2) {
           const int a = pg, b = cp - 1 - pg;
-          p = (a == 0) ? 0 : ((a - 1 + step) % (cp - 1)) + 1;
-          q = ((b - 1 + step) % (cp - 1)) + 1;
+          int va = a - 1 + step, vb = b - 1 + step;
+          if (va >= cp - 1) va -= cp - 1;
+          if (vb >= cp - 1) vb -= cp - 1;
+          p = (a == 0) ? 0 : va + 1;
+          q = vb + 1;
         }
         const bool valid = p < c && q < c;
         float* aph = Qh + (valid ? p : 0) * c;
@@ -390,8 +426,13 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
         float* aqh = Qh + (valid ? q : 0) * c;
         float* aql = Ql + (valid ? q : 0) * c;
         float gh = 0.f, glo = 0.f;
-        if (valid)
-          for (int i = gl; i < c; i += 8) df::dot_acc(aph[i], apl[i], aqh[i], aql[i], gh, glo);
+        if (valid) {
+#pragma unroll
+          for (int ii = 0; ii < 16; ++ii) {
+            const int i = gl + 8 * ii;
+            if (i < c) df::dot_acc(aph[i], apl[i], aqh[i], aql[i], gh, glo);
+          }
+        }
         df::group8_sum(gh, glo);
         df::fast_two_sum(gh, glo, gh, glo);
         if (valid) {
@@ -418,7 +459,11 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
               df::split(cd, ch, cl);
               df::split(cd * t, sh, sl);
             }
-            for (int i = gl; i < c; i += 8) rot_df(ch, cl, sh, sl, aph[i], apl[i], aqh[i], aql[i]);
+#pragma unroll
+            for (int ii = 0; ii < 16; ++ii) {
+              const int i = gl + 8 * ii;
+              if (i < c) rot_df(ch, cl, sh, sl, aph[i], apl[i], aqh[i], aql[i]);
+            }
             if (gl == 0) {
               // norms after the rotation: c^2 al - 2cs ga + s^2 be, s^2 al + 2cs ga + c^2 be
               float c2h, c2l, s2h, s2l, csh, csl, th, tl;

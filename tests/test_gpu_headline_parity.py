@@ -2,13 +2,14 @@
 tol 1e-7, HM_A32) on the N = 8192 log kernel, where the FP64 oracle still runs
 in seconds (Sec. 4.2 compression, Sec. 4.3 HBS-ID conversion).
 
-* CUDA-core black box (exact FP64 products of the FP32 operator): the
-  reconstruction agrees with the oracle's element by element to 1e-11 of ||A||
-  (the double-float arithmetic of HM_A32, see the test), every node's skeleton
-  rank equals the oracle's, and every skeleton index set equals the oracle's bit
-  for bit, in pivot order.  At this size the leaf arcs are eight times longer
-  than at N = 65536 and some skeleton ranks reach r (counted, as on the oracle
-  side).
+* CUDA-core black box (exact FP64 products of the FP32 operator): every node's
+  skeleton rank equals the oracle's; where no saturated ID enters (see the
+  test) the skeleton index sets equal the oracle's bit for bit, in pivot order,
+  and the reconstruction agrees with the oracle's element by element to 1e-11
+  of ||A|| (the double-float arithmetic of HM_A32); elsewhere it is a valid
+  compression within the tolerance.  At this size the leaf arcs are eight times
+  longer than at N = 65536 and some skeleton ranks reach r (counted, as on the
+  oracle side).
 * Tensor-core black box (the split products the bench times): the
   reconstruction is within 1e-7 of the oracle's; the number of nodes whose rank
   differs from the oracle's is reported (the split products differ from exact
@@ -63,28 +64,51 @@ def test_headline_shapes_exact_products(oracle_result):
     e_par = np.linalg.norm(Ag - Ao) / nA
     e_gpu = np.linalg.norm(Ag - A64) / nA
     nodes, k_gpu, k_or = _ranks(h, g)
-    print(f"N={N} leaves {M} r={R}: GPU err {e_gpu:.3e}, vs oracle {e_par:.3e}, ranks "
-          f"{h.info['min_rank']}..{h.info['max_rank']}, saturated {h.info['saturated']}")
-    assert e_gpu <= TOL
-    # HM_A32 carries FP64 data through double-float arithmetic (products, QR and
-    # SVD at ~2^-46 relative); through five levels of peeling and the ID's
-    # interpolation matrices that is ~1e-12 of ||A||: the bound leaves a factor 10
-    assert e_par <= 1e-11
+    t = build_tree(N, M)
+    L = t.L
     # A node whose ID rank reached r on either side picks its last skeletons by
-    # pivots among columns of similar residual norm: a 1e-13 change of the input
-    # may reorder them (both choices are valid IDs), and its ancestors inherit
-    # the difference.  Skeletons are compared bit for bit on every node whose
-    # subtree is free of saturated IDs; ranks everywhere.
-    L = build_tree(N, M).L
+    # pivots among columns of similar residual norm (Sec. 4.3: the ID keeps r
+    # columns; which ones among near-equal pivots is not fixed): a rounding-level
+    # change of the input may reorder them, both choices are valid IDs, and its
+    # ancestors inherit the difference.  So the result is unique only where no
+    # saturated ID enters: skeletons are compared bit for bit on every node whose
+    # subtree is free of saturated IDs, and the reconstruction element by element
+    # on the blocks A(I_a, I_b) whose two paths up to the children of the lowest
+    # common ancestor are such clean subtrees, and on the leaf blocks D_a (the
+    # HBS stage, before any ID).  Elsewhere the result must be a valid
+    # compression: within the tolerance of A.
     sat = {tau for tau in nodes if len(g.Iin[tau]) == R or len(g.Iout[tau]) == R}
 
     def clean(tau):
         return tau not in sat and (tau >= 2 ** L or (clean(2 * tau) and clean(2 * tau + 1)))
+    mask = np.zeros((N, N), dtype=bool)
+    for a in t.leaves():
+        for b in t.leaves():
+            x, y = a, b
+            while x != y and x >> 1 != y >> 1:
+                x >>= 1
+                y >>= 1
+            if a == b or (clean(x) and clean(y)):
+                mask[t.rows(a), t.rows(b)] = True
+    e_unique = np.linalg.norm((Ag - Ao)[mask]) / nA
     checked = [tau for tau in nodes if clean(tau)]
     differ = [tau for tau in nodes if hm.hm_skeleton(h, tau, 0) != [int(v) for v in g.Iin[tau]]
               or hm.hm_skeleton(h, tau, 1) != [int(v) for v in g.Iout[tau]]]
-    print(f"saturated IDs on {len(sat)} nodes; skeletons compared on {len(checked)} nodes; "
+    print(f"N={N} leaves {M} r={R}: GPU err {e_gpu:.3e}, vs oracle {e_par:.3e} (on the "
+          f"{mask.mean():.0%} of entries free of saturated IDs {e_unique:.3e}), ranks "
+          f"{h.info['min_rank']}..{h.info['max_rank']}, saturated {h.info['saturated']}; "
+          f"saturated IDs on {len(sat)} nodes; skeletons compared on {len(checked)} nodes; "
           f"skeleton sets differing on {len(differ)} nodes: {differ}")
+    assert e_gpu <= TOL
+    assert e_par <= TOL
+    # HM_A32 carries FP64 data through double-float arithmetic (products, QR and
+    # SVD at ~2^-46 relative); through five levels of peeling and the ID's
+    # interpolation matrices that is ~1e-12 of ||A||: the bound leaves a factor 10
+    assert e_unique <= 1e-11
+    # at these shapes 12 of the 32 leaves saturate (the tips of the ellipse), so
+    # the unique part is the leaf blocks and the blocks between clean subtrees
+    # (8% of the entries)
+    assert mask.mean() >= 0.05
     assert np.array_equal(k_gpu, k_or)
     assert len(checked) >= len(nodes) // 2
     for tau in checked:
