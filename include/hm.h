@@ -179,7 +179,9 @@ void hm_dense_operator_destroy(hm_operator* op);
  * symmetric; its products are those of dtype 4 of hm_dense_operator_create
  * (FP64 blocks, exact-accumulation split on the tensor cores) on these
  * entries, with no operator bytes read from HBM (24 n bytes of tables).
- * Element type double (HM_A32).  Destroy with hm_dense_operator_destroy.
+ * Element type double (HM_A32).  2 <= n <= 524288 (HM_EINVAL otherwise: the
+ * GEMM tracks its K tiles in one shared-memory bitmask).  Destroy with
+ * hm_dense_operator_destroy.
  */
 hm_status hm_log_kernel_operator_create(int64_t n, hm_operator* out);
 

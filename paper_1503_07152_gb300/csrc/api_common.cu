@@ -379,7 +379,7 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
       launch_dense_gemm<double>((const double*)d->A, d->lda, trans, n, w,
                                 (const double*)X + c0 * ldx, ldx, (double*)Y + c0 * ldy, ldy,
                                 d->flags, st);
-    else if (d->dtype == 4 && gemm_tc_supported((const float*)d->A, d->lda, n)) {
+    else if (d->dtype == 4 && n <= 524288 && gemm_tc_supported((const float*)d->A, d->lda, n)) {
       const int64_t need = gemm_esg_work_bytes(n, w);
       if (need > d->xs_bytes) {
         if (d->xs) cudaFree(d->xs);
@@ -452,8 +452,8 @@ hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_
 
 hm_status hm_log_kernel_operator_create(int64_t n, hm_operator* out) {
   clear_error();
-  if (!out || n < 2) {
-    set_error("hm_log_kernel_operator_create: need n >= 2 and out");
+  if (!out || n < 2 || n > 524288) {
+    set_error("hm_log_kernel_operator_create: need 2 <= n <= 524288 and out");
     return HM_EINVAL;
   }
   // tables of the entries' two terms, S[m] = log|sin(pi m / n)| (m >= 1) and

@@ -1,13 +1,13 @@
 // Sampling GEMM of the FP32 dense operator with FP64 samples (HM_A32) on the
 // 5th-generation tensor cores: Y = op(A) X, A FP32, X and Y FP64, to about
-// 2^-40 relative accuracy per product term (the FP64 black-box products
+// 2^-32 of (max slice)^2 relative per product term (the FP64 black-box products
 // A Omega / A^* Omega of the compression figures, without FP64 arithmetic in
 // the contraction).
 //
 // Exact-accumulation split: every row of op(A) (over all of K; the exponents
 // are recorded once per operator) and every column of X inside a window of
-// four 64-wide K tiles is scaled by a power of two so that its largest entry
-// lies in [64, 128), and cut into four 8-bit integer slices
+// 256 K values is scaled by a power of two so that its largest entry lies in
+// [64, 128), and cut into four 8-bit integer slices
 // (a = sum_s a_s 2^(-8(s-1)) up to the scale, |a_s| <= 128, each exact in BF16).
 // A BF16 x BF16 product of slices is an integer of magnitude <= 2^14, and the
 // products of one order d = s + t (d = 2..5, at most four of them) summed over
@@ -18,24 +18,26 @@
 // (L, M, C, D: the exact sums of orders 2..5) into an FP32 double-float
 // (hi, lo), every term through an error-free TwoSum.  Y = hi + lo in FP64.
 //
+// MMA form: one chain of same-shape MMAs per K tile.  A stage holds the four A
+// slices and the X slices stacked as seven 64-row blocks [0 0 0 x1 x2 x3 x4]
+// (three zero blocks written once).  A slice s times the 256 rows starting at
+// block 4 - s is [0 ... x1 .. x(5-s)], so its N = 256 product lands, column
+// block j, in the accumulator of order j + 2 for every s: all sixteen MMAs of
+// a 32-wide K tile (4 slices x 2 K steps) have the same accumulator and shape
+// and are ordered by the tensor pipe without waits.  The zero blocks cost 6 of
+// 16 products' worth of tensor work; the MMAs are large enough (128 x 256 x 16)
+// that one thread's issue keeps the pipe fed.
+//
 // Block: 128 rows of op(A) x 64 columns of X, eighteen warps:
-//   warp 17 (one lane): TMA loads of the FP32 tile of A into one raw stage;
-//   warps 0-7: move the raw tile to registers (releasing the stage), scale and
-//     cut the slices into two operand stages (K-major, 128-byte swizzle); one
-//     lane loads the pre-cut X slices by TMA.  An entry that does not fit its
-//     recorded row scale (the operator changed after the scales were taken)
+//   warp 17 (one lane): TMA loads of the FP32 tiles of A (128 x 32) into four
+//     raw stages;
+//   warps 0-7: move a raw tile to registers (releasing the stage), scale and
+//     cut the slices into one of two operand stages (K-major, 64-byte swizzle);
+//     one lane loads the pre-cut X slices by TMA.  An entry that does not fit
+//     its recorded row scale (the operator changed after the scales were taken)
 //     aborts the block, whose outputs are then NaN;
-//   warp 8: allocates 512 TMEM columns; one lane issues the MMAs into the four
-//     order accumulators.  The four X slices of a stage lie one after the other
-//     as one 256-row K-major operand, so one MMA takes A slice s times X slices
-//     1 .. 5 - s (N = 64 (5 - s)) into the accumulators from column 64 (s - 1)
-//     on: product (s, t) lands in the accumulator of order s + t, and the ten
-//     products of orders 2..5 take four instructions per 16-wide K step.  MMAs
-//     are ordered back to back only for the same accumulator and shape, so the
-//     four K steps of one s form a chain, and before a chain of another shape
-//     the issuing lane waits for the previous one to complete (commit to a
-//     private mbarrier).  Successive tiles run the chains in alternate order,
-//     so that a tile's first chain has the shape of the previous tile's last;
+//   warp 8: allocates 512 TMEM columns (two windows x four orders x 64
+//     columns); one lane issues the MMAs;
 //   warps 9-16: drain once per window (two warps per TMEM lane quarter, 32
 //     columns each) and write Y.
 // All-zero K tiles of X are skipped; the four X slices of an active tile are
@@ -45,6 +47,7 @@
 // its issued MMAs complete (waits of the full limit) and leaves; TMEM is
 // released unless even the full-limit wait for its MMAs ran out.
 #include <algorithm>
+#include <cstring>
 #include <atomic>
 
 #include "tc_util.cuh"
@@ -54,19 +57,44 @@ namespace {
 
 using namespace tc;
 
-constexpr int TM = 128, TN = 64, TK = 64;
+constexpr int TM = 128, TN = 64, TK = 32;  // TK: the K extent of a stage
 constexpr int NSL = 4;                  // slices of A and of X
-constexpr int A_SLICE = TM * TK * 2;    // 16 KB
-constexpr int B_SLICE = TN * TK * 2;    // 8 KB
-constexpr int RAW_BYTES = TM * TK * 4;  // 32 KB
-constexpr int STAGE_BYTES = NSL * A_SLICE + NSL * B_SLICE;  // 96 KB
-constexpr int SSTAGES = 2;
-constexpr int LAYOUT_BYTES = RAW_BYTES + SSTAGES * STAGE_BYTES;  // 224 KB
-constexpr int NCONV = 256, NDRAIN = 256, NTHREADS = 576;
-constexpr int W_MMA = 8, W_DRAIN0 = 9, W_TMA = 17;
+constexpr int A_SLICE = TM * TK * 2;    // 8 KB: 128 rows x 64 bytes
+constexpr int XB = TN * TK * 2;         // 4 KB: one X slice, 64 rows x 64 bytes
+constexpr int XZ = 3;                   // zero blocks before x1
+constexpr int X_BYTES = (XZ + NSL) * XB;                 // 28 KB
+constexpr int STAGE_BYTES = NSL * A_SLICE + X_BYTES;     // 60 KB
+constexpr int SSTAGES = 3;
+constexpr int RAW_BYTES = TM * TK * 4;  // 16 KB
+constexpr int RSTAGES = 2;
+constexpr int RAW_REGION = RSTAGES * RAW_BYTES;          // 32 KB
+constexpr int LAYOUT_BYTES = RAW_REGION + SSTAGES * STAGE_BYTES;  // 212 KB
+constexpr int NCONV = 256, NDRAIN = 256, NTHREADS = 608;
+constexpr int W_MMA = 8, W_DRAIN0 = 9, W_TMA = 17, W_XTMA = 18;
 constexpr uint32_t TMEM_COLS = 512;  // 2 buffers x 4 orders x 64 columns
-constexpr int WIN_TILES = 4;         // K tiles per exact accumulation window
-constexpr int WIN_ROWS = WIN_TILES * TK;
+constexpr int WIN_ROWS = 256;        // K values per exact accumulation window
+constexpr int WIN_TILES = WIN_ROWS / TK;
+constexpr int KPAD = 64;             // K padding of the pre-cut X (k_split_x64's rows)
+constexpr int MAX_KT = 16384;        // K tiles a call may have (n <= 524288)
+
+static_assert(STAGE_BYTES % 1024 == 0 && RAW_BYTES % 1024 == 0, "1 KB aligned stages");
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle (16-byte chunk c of
+// row r at chunk c ^ ((r >> 1) & 3)), 8-row groups 512 bytes apart; start
+// address and offsets in 16-byte units.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset between 8-row groups
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)4 << 61;            // 64-byte swizzle
+  return d;
+}
+// byte offset of 16-byte chunk q (0..3) of row m in a 64-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw64_off(int m, int q) {
+  return (uint32_t)((m >> 3) * 512 + (m & 7) * 64 + ((q ^ ((m >> 1) & 3)) << 4));
+}
 
 __device__ __forceinline__ float pow2f(int k) {  // 2^k for k in [-126, 127]
   return __int_as_float((k + 127) << 23);
@@ -80,20 +108,32 @@ __device__ __forceinline__ int exp_above(float x) {
   return e;
 }
 
-// Cut v (|v| < 128, a multiple of 2^-24 of the scale) into four 8-bit integers.
-__device__ __forceinline__ void cut4(float v, float& s1, float& s2, float& s3, float& s4) {
-  s1 = rintf(v);
-  float r = (v - s1) * 256.f;
-  s2 = rintf(r);
-  r = (r - s2) * 256.f;
-  s3 = rintf(r);
-  r = (r - s3) * 256.f;
-  s4 = rintf(r);
+// Round to the nearest integer, ties to even, for |x| < 2^22: adding 1.5 * 2^23
+// lands in [2^23, 2^24), where the FP32 spacing is 1, so the add rounds x and
+// the subtraction is exact.  Two adds on the FMA pipe instead of one rounding
+// instruction on the slower conversion pipe; the compiler does not reassociate
+// the pair (no fast-math).
+__device__ __forceinline__ float round_int(float x) {
+  return (x + 12582912.f) - 12582912.f;
 }
 
+// Cut v (|v| < 128, a multiple of 2^-24 of the scale) into four 8-bit integers
+// (the digits of v rounded to a multiple of 2^-24, each in [-128, 128]).
+__device__ __forceinline__ void cut4(float v, float& s1, float& s2, float& s3, float& s4) {
+  s1 = round_int(v);
+  float r = (v - s1) * 256.f;
+  s2 = round_int(r);
+  r = (r - s2) * 256.f;
+  s3 = round_int(r);
+  r = (r - s3) * 256.f;
+  s4 = round_int(r);
+}
+
+// Two digits as a BF16 pair (lo in the low half).  A digit is an integer of at
+// most 8 significant bits, so its FP32 pattern ends in 16 zero bits and its BF16
+// pattern is the FP32 pattern's upper half: one byte permute, no rounding.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&h);
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
 // Row exponents of A (e with max_j |A(i, j)| < 2^e, clamped to >= -120): one
@@ -122,23 +162,28 @@ __global__ __launch_bounds__(256) void k_col_exp(const float* __restrict__ A, in
 }
 
 // X (FP64, column-major n x ncols) -> per (window, column) exponents and four
-// BF16 integer slices, layout Xs[((ct * 4 + t) * 64 + c) * kpad + k]; flags bit t
-// of (kt, ct) set when slice t of that K tile has a nonzero entry.  Block: one
-// window (four K tiles) x 64 columns; thread (c, q) covers K tile q of the window.
+// BF16 integer slices, laid out as the GEMM's shared memory wants them: per
+// (column tile ct, K tile kt) one contiguous 16 KB block of 256 rows
+// (row t * 64 + c: slice t of column c) x 32 K values, each row's four 16-byte
+// chunks in 64-byte-swizzle order, so one 1-D bulk copy lands a tile in place.
+// Flags of (kt, ct) nonzero when that K tile has a nonzero slice.  Block: one
+// window (256 rows) x 64 columns; thread (c, q) covers rows 64 q .. 64 q + 63
+// of the window (kpad is a multiple of 64).
 __global__ __launch_bounds__(256) void k_split_x64(const double* __restrict__ X, int64_t ldx,
                                                    int64_t n, int64_t ncols, int64_t kpad,
                                                    int nct, __nv_bfloat16* __restrict__ Xs,
                                                    int* __restrict__ ex,
                                                    uint8_t* __restrict__ flags) {
+  constexpr int QR = WIN_ROWS / 4;  // rows per thread
   const int win = blockIdx.x, ct = blockIdx.y;
   const int tid = threadIdx.x;
   const int c = tid >> 2, q = tid & 3;
   const int64_t col = (int64_t)ct * TN + c;
-  const int64_t r0 = (int64_t)win * WIN_ROWS + q * TK;
+  const int64_t r0 = (int64_t)win * WIN_ROWS + q * QR;
   __shared__ int fl[WIN_TILES];
   if (tid < WIN_TILES) fl[tid] = 0;
   double mx = 0.0;
-  for (int i = 0; i < TK; ++i) {
+  for (int i = 0; i < QR; ++i) {
     const int64_t row = r0 + i;
     if (row < n && col < ncols) mx = fmax(mx, fabs(X[row + col * ldx]));
   }
@@ -147,22 +192,26 @@ __global__ __launch_bounds__(256) void k_split_x64(const double* __restrict__ X,
   int e = 0;
   if (mx > 0.0) frexp(mx, &e);
   __syncthreads();
-  int bits = 0;
-  const int64_t base = (int64_t)ct * NSL * TN;
+  int bits[QR / TK] = {};
   if (r0 < kpad) {
-    for (int i = 0; i < TK; ++i) {
+    for (int i = 0; i < QR; ++i) {
       const int64_t row = r0 + i;
       double r = (row < n && col < ncols) ? ldexp(X[row + col * ldx], 7 - e) : 0.0;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const double st = rint(r);
         r = (r - st) * 256.0;
-        bits |= (st != 0.0) ? (1 << t) : 0;
-        Xs[(base + t * TN + c) * kpad + row] = __float2bfloat16_rn((float)st);
+        bits[i / TK] |= (st != 0.0) ? (1 << t) : 0;
+        const int rr = t * TN + c, kk = (int)(row % TK);
+        const int64_t tile = (int64_t)ct * (kpad / TK) + row / TK;
+        Xs[(tile * (NSL * TN) + rr) * TK + ((((kk >> 3) ^ ((rr >> 1) & 3))) << 3) + (kk & 7)] =
+            __float2bfloat16_rn((float)st);
       }
     }
   }
-  if (bits) atomicOr(&fl[q], bits);
+#pragma unroll
+  for (int h = 0; h < QR / TK; ++h)
+    if (bits[h]) atomicOr(&fl[q * (QR / TK) + h], bits[h]);
   if (q == 0) ex[((int64_t)win * nct + ct) * TN + c] = e;
   __syncthreads();
   if (tid < WIN_TILES) {
@@ -192,17 +241,18 @@ __device__ __forceinline__ bool cutters_all(bool v) {
 // operator is symmetric, so only TRANS = 0 is instantiated.
 template <int TRANS, int GEN>
 __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int64_t n,
+    const __grid_constant__ CUtensorMap tmA, const __nv_bfloat16* __restrict__ Xs, int64_t n,
     int64_t ncols, const uint8_t* __restrict__ flags, const int* __restrict__ ex,
     const int* __restrict__ e_rows, double* __restrict__ Y, int64_t ldy, int* __restrict__ err,
     long long poll_limit, const float* __restrict__ tabS, const float* __restrict__ tabP) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t raw_full, raw_empty, st_full[SSTAGES], x_full[SSTAGES],
-      st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final, bar_chain;
+  __shared__ __align__(8) uint64_t raw_full[RSTAGES], raw_empty[RSTAGES], st_full[SSTAGES],
+      x_full[SSTAGES], st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final;
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
   __shared__ float srow[TM];  // 2^(7 - e), e the exponent of the row of op(A)
   __shared__ int win_lo, win_hi;  // this block's share of the windows (split over K)
+  __shared__ uint32_t act_bits[MAX_KT / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ct = blockIdx.x, mt = blockIdx.y, nct = gridDim.x;
   const int64_t m0 = (int64_t)mt * TM;
@@ -211,12 +261,14 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sbase = smem_raw + (base - raw);
-  const uint32_t raw_addr = base, stage_addr0 = base + RAW_BYTES;
+  const uint32_t raw_addr = base, stage_addr0 = base + RAW_REGION;
 
   if (tid == 0) {
     abort_flag = 0;
-    mbar_init(smem_u32(&raw_full), 1);
-    mbar_init(smem_u32(&raw_empty), NCONV);
+    for (int i = 0; i < RSTAGES; ++i) {
+      mbar_init(smem_u32(&raw_full[i]), 1);
+      mbar_init(smem_u32(&raw_empty[i]), NCONV);
+    }
     for (int i = 0; i < SSTAGES; ++i) {
       mbar_init(smem_u32(&st_full[i]), NCONV);
       mbar_init(smem_u32(&x_full[i]), 1);
@@ -227,13 +279,20 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       mbar_init(smem_u32(&acc_empty[b]), NDRAIN);
     }
     mbar_init(smem_u32(&bar_final), 1);
-    mbar_init(smem_u32(&bar_chain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < TM) {
     const int e = (m0 + tid < n) ? e_rows[m0 + tid] : 0;
     srow[tid] = pow2f(7 - e);
   }
+  // the zero blocks in front of each stage's X slices, written once; the MMAs
+  // read them through the async proxy
+  for (int i = tid; i < SSTAGES * XZ * XB / 16; i += NTHREADS) {
+    const int sidx = i / (XZ * XB / 16), o = i % (XZ * XB / 16);
+    *reinterpret_cast<uint4*>(sbase + RAW_REGION + sidx * STAGE_BYTES + NSL * A_SLICE + o * 16) =
+        make_uint4(0u, 0u, 0u, 0u);
+  }
+  fence_proxy_async();
   if (warp == W_TMA) {
     // blocks z = 0 .. gridDim.z - 1 of a row block share its active windows
     // (those with a nonzero K tile of X) in equal counts, in window order
@@ -285,43 +344,71 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
   const int wlo = win_lo, whi = win_hi;
-  auto active = [&](int kt) -> int {
-    const int w = kt / WIN_TILES;
-    return (w >= wlo && w < whi) ? flags[(int64_t)kt * nct + ct] : 0;
+  // one bit per K tile: nonzero X and inside this block's share of the windows
+  // (every role walks the tiles; a shared-memory bit instead of a global load
+  // per tile and role)
+  for (int wd = tid; wd < (nkt + 31) / 32; wd += NTHREADS) {
+    uint32_t b = 0;
+    for (int i = 0; i < 32; ++i) {
+      const int kt = wd * 32 + i, w = kt / WIN_TILES;
+      if (kt < nkt && w >= wlo && w < whi && flags[(int64_t)kt * nct + ct]) b |= 1u << i;
+    }
+    act_bits[wd] = b;
+  }
+  __syncthreads();
+  auto active = [&](int kt) -> int { return (act_bits[kt >> 5] >> (kt & 31)) & 1; };
+  // the first active K tile at or after `from` (nkt if none)
+  const int nwords = (nkt + 31) / 32;
+  auto next_active = [&](int from) -> int {
+    int wd = from >> 5;
+    if (wd >= nwords) return nkt;
+    uint32_t b = act_bits[wd] & (~0u << (from & 31));
+    while (!b) {
+      if (++wd >= nwords) return nkt;
+      b = act_bits[wd];
+    }
+    return (wd << 5) + __ffs(b) - 1;
   };
 
   if (warp == W_TMA) {
     // ---------------------------------------------------------- TMA of A
     if (!GEN && lane == 0) {
       int it = 0;
-      for (int kt = 0; kt < nkt; ++kt) {
-        if (!active(kt)) continue;
-        if (!mbar_wait(smem_u32(&raw_empty), (it & 1) ^ 1, &abort_flag, poll_limit)) break;
-        mbar_arrive_tx(smem_u32(&raw_full), RAW_BYTES);
+      const uint64_t pol = l2_policy_evict_first();  // A is read once per call
+      for (int kt = next_active(0); kt < nkt; kt = next_active(kt + 1)) {
+        const int r = it % RSTAGES;
+        if (!mbar_wait(smem_u32(&raw_empty[r]), ((it / RSTAGES) & 1) ^ 1, &abort_flag,
+                       poll_limit))
+          break;
+        mbar_arrive_tx(smem_u32(&raw_full[r]), RAW_BYTES);
         if (!TRANS)
-          tma_load_2d(raw_addr, &tmA, kt * TK, (int)m0, smem_u32(&raw_full));
+          tma_load_2d_hint(raw_addr + r * RAW_BYTES, &tmA, kt * TK, (int)m0,
+                           smem_u32(&raw_full[r]), pol);
         else
-          tma_load_2d(raw_addr, &tmA, (int)m0, kt * TK, smem_u32(&raw_full));
+          tma_load_2d_hint(raw_addr + r * RAW_BYTES, &tmA, (int)m0, kt * TK,
+                           smem_u32(&raw_full[r]), pol);
         ++it;
       }
-      if (it > 0) mbar_wait_drain(smem_u32(&raw_full), (it - 1) & 1);
+      // the copies in flight land before the block's shared memory is given up
+      for (int j = (it > RSTAGES ? it - RSTAGES : 0); j < it; ++j)
+        mbar_wait_drain(smem_u32(&raw_full[j % RSTAGES]), (j / RSTAGES) & 1);
     }
   } else if (GEN && warp < 8) {
     // ---------------------------------------------------------- generate A, cut, TMA of X
     // A(i, j) = (S[|i - j|] + P[i + j]) in float pairs: fl((Sh + Ph) + (Sl + Pl)),
     // 1 on the diagonal, 0 outside [0, n).  A tile's entries use TM + TK - 1
-    // values of each table, staged in the (unused) raw stage: window entry e
+    // values of each table, staged in the (unused) raw region: window entry e
     // holds S[|d|] for i - j = d = m0 - k0 - (TK - 1) + e, and P[m0 + k0 + e].
-    int it = 0, xissued = 0;
+    int it = 0;
     // Four shifted copies of each window (copy q holds window entry x + q at x),
     // so that every thread reads its four consecutive entries of a table as one
     // aligned float4: for row m the P entries start at m + 4 k4 and the S entries
-    // (descending) at m - 4 k4 + 60, both congruent to m mod 4.
-    constexpr int WC = 196;  // floats per copy (16-byte multiple, covers index 193)
+    // (descending) at m - 4 k4 + TK - 4, both congruent to m mod 4.
+    constexpr int WC = 164;  // floats per copy (16-byte multiple, covers index 161)
     float* win = reinterpret_cast<float*>(sbase);  // [table (Sh, Sl, Ph, Pl)][q][WC]
-    // Thread e (< WC + 3 <= NCONV) owns window entry e.  The next active tile's
-    // entry is loaded from the (L2-resident) tables one tile ahead, so the load
-    // latency hides behind the current tile's cut.
+    // Thread e (< TM + TK - 1 <= NCONV) owns window entry e.  The next active
+    // tile's entry is loaded from the (L2-resident) tables one tile ahead, so the
+    // load latency hides behind the current tile's cut.
     float pv[4] = {0.f, 0.f, 0.f, 0.f};
     auto load_win = [&](int ktn) {
       pv[0] = pv[1] = pv[2] = pv[3] = 0.f;
@@ -333,18 +420,11 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
         if (sidx < 2 * n - 1) { pv[2] = tabP[sidx]; pv[3] = tabP[2 * n - 1 + sidx]; }
       }
     };
-    auto next_active = [&](int from) {
-      int k = from;
-      while (k < nkt && !active(k)) ++k;
-      return k;
-    };
     {
       const int k1 = next_active(0);
       if (k1 < nkt) load_win(k1);
     }
-    for (int kt = 0; kt < nkt; ++kt) {
-      const int fl = active(kt);  // the same for every cutter
-      if (!fl) continue;
+    for (int kt = next_active(0); kt < nkt; kt = next_active(kt + 1)) {
       const int s = it % SSTAGES;
       const bool ok = !abort_flag &&
                       mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag,
@@ -353,13 +433,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       // also orders the previous tile's window reads before the new writes
       if (!cutters_all(ok)) break;
       const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
-      if (tid == 0) {
-        mbar_arrive_tx(smem_u32(&x_full[s]), (uint32_t)(NSL * B_SLICE));
-        for (int t = 0; t < NSL; ++t)
-          tma_load_2d(st + NSL * A_SLICE + t * B_SLICE, &tmX, kt * TK, (ct * NSL + t) * TN,
-                      smem_u32(&x_full[s]));
-        xissued = it + 1;
-      }
       const int64_t k0 = (int64_t)kt * TK;
       {
         const int e = tid;
@@ -383,16 +456,16 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       unsigned char* sp = sbase + (st - base);
       int bad = 0;
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        const int f = p * NCONV + tid, m = f >> 4, k4 = f & 15;
+      for (int p = 0; p < TM * TK / 4 / NCONV; ++p) {
+        const int f = p * NCONV + tid, m = f >> 3, k4 = f & 7;
         const float sc = srow[m];
         const int q = m & 3, ps = m + 4 * k4 - q, ds = m - 4 * k4 + (TK - 4) - q;
         const float4 sh4 = *reinterpret_cast<const float4*>(win + (0 * 4 + q) * WC + ds);
         const float4 sl4 = *reinterpret_cast<const float4*>(win + (1 * 4 + q) * WC + ds);
         const float4 ph4 = *reinterpret_cast<const float4*>(win + (2 * 4 + q) * WC + ps);
         const float4 pl4 = *reinterpret_cast<const float4*>(win + (3 * 4 + q) * WC + ps);
-        // entry e: S at window index m - 4 k4 + 63 - e (component 3 - e of the S
-        // float4), P at m + 4 k4 + e (component e)
+        // entry e: S at window index m - 4 k4 + TK - 1 - e (component 3 - e of the
+        // S float4), P at m + 4 k4 + e (component e)
         const float shv[4] = {sh4.w, sh4.z, sh4.y, sh4.x}, slv[4] = {sl4.w, sl4.z, sl4.y, sl4.x};
         const float phv[4] = {ph4.x, ph4.y, ph4.z, ph4.w}, plv[4] = {pl4.x, pl4.y, pl4.z, pl4.w};
         float a[4];
@@ -412,7 +485,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
           bad |= !(fabsf(a[e]) < 128.f);
           cut4(a[e], sl[0][e], sl[1][e], sl[2][e], sl[3][e]);
         }
-        const uint32_t off = sw_off(m, k4 >> 1) + (uint32_t)((k4 & 1) * 8);
+        const uint32_t off = sw64_off(m, k4 >> 1) + (uint32_t)((k4 & 1) * 8);
 #pragma unroll
         for (int t = 0; t < NSL; ++t)
           *reinterpret_cast<uint2*>(sp + t * A_SLICE + off) =
@@ -423,43 +496,33 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       mbar_arrive(smem_u32(&st_full[s]));
       ++it;
     }
-    if (tid == 0)
-      for (int j = (xissued > SSTAGES ? xissued - SSTAGES : 0); j < xissued; ++j)
-        mbar_wait_drain(smem_u32(&x_full[j % SSTAGES]), (j / SSTAGES) & 1);
   } else if (warp < 8) {
     // ---------------------------------------------------------- cut A, TMA of X
-    int it = 0, xissued = 0;
-    for (int kt = 0; kt < nkt && !abort_flag; ++kt) {
-      const int fl = active(kt);
-      if (!fl) continue;
-      const int s = it % SSTAGES;
-      if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag, poll_limit)) break;
+    int it = 0;
+    for (int kt = next_active(0); kt < nkt && !abort_flag; kt = next_active(kt + 1)) {
+      const int s = it % SSTAGES, r = it % RSTAGES;
+      if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag, poll_limit))
+        break;
       const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
-      if (tid == 0) {
-        mbar_arrive_tx(smem_u32(&x_full[s]), (uint32_t)(NSL * B_SLICE));
-        for (int t = 0; t < NSL; ++t)
-          tma_load_2d(st + NSL * A_SLICE + t * B_SLICE, &tmX, kt * TK, (ct * NSL + t) * TN,
-                      smem_u32(&x_full[s]));
-        xissued = it + 1;
-      }
-      if (!mbar_wait(smem_u32(&raw_full), it & 1, &abort_flag, poll_limit)) break;
-      const unsigned char* rw = sbase;  // the raw stage sits at the aligned base
+      if (!mbar_wait(smem_u32(&raw_full[r]), (it / RSTAGES) & 1, &abort_flag, poll_limit)) break;
+      const unsigned char* rw = sbase + r * RAW_BYTES;
       unsigned char* sp = sbase + (st - base);
       int bad = 0;
       if (!TRANS) {
-        // raw [128 rows][64 k]; pass p: rows 16p .. 16p+15, 16 threads per row
-        float4 v[8];
+        // raw [128 rows][32 k]; pass p: rows 32p .. 32p+31, 8 threads per row
+        constexpr int NP = TM * TK / 4 / NCONV;  // 4
+        float4 v[NP];
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const int f = p * NCONV + tid, m = f >> 4, k4 = f & 15;
-          v[p] = *reinterpret_cast<const float4*>(rw + m * 256 + k4 * 16);
+        for (int p = 0; p < NP; ++p) {
+          const int f = p * NCONV + tid, m = f >> 3, k4 = f & 7;
+          v[p] = *reinterpret_cast<const float4*>(rw + m * (TK * 4) + k4 * 16);
         }
         // the next TMA write (async proxy) must follow these generic reads
         fence_proxy_async();
-        mbar_arrive(smem_u32(&raw_empty));  // the raw stage is free for the next tile
+        mbar_arrive(smem_u32(&raw_empty[r]));  // the raw stage is free for a later tile
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const int f = p * NCONV + tid, m = f >> 4, k4 = f & 15;
+        for (int p = 0; p < NP; ++p) {
+          const int f = p * NCONV + tid, m = f >> 3, k4 = f & 7;
           const float sc = srow[m];
           float a[4] = {v[p].x * sc, v[p].y * sc, v[p].z * sc, v[p].w * sc};
           float sl[4][4];
@@ -468,24 +531,24 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
             bad |= !(fabsf(a[i]) < 128.f);
             cut4(a[i], sl[0][i], sl[1][i], sl[2][i], sl[3][i]);
           }
-          const uint32_t off = sw_off(m, k4 >> 1) + (uint32_t)((k4 & 1) * 8);
+          const uint32_t off = sw64_off(m, k4 >> 1) + (uint32_t)((k4 & 1) * 8);
 #pragma unroll
           for (int t = 0; t < NSL; ++t)
             *reinterpret_cast<uint2*>(sp + t * A_SLICE + off) =
                 make_uint2(pack_bf16(sl[t][0], sl[t][1]), pack_bf16(sl[t][2], sl[t][3]));
         }
       } else {
-        // raw [64 k][128 m]; thread (m, half) takes k = 32 half .. 32 half + 31
+        // raw [32 k][128 m]; thread (m, half) takes k = 16 half .. 16 half + 15
         const int m = tid & (TM - 1), h = tid >> 7;
-        float v[32];
+        float v[16];
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          v[i] = *reinterpret_cast<const float*>(rw + ((h * 32 + i) * TM + m) * 4);
+        for (int i = 0; i < 16; ++i)
+          v[i] = *reinterpret_cast<const float*>(rw + ((h * 16 + i) * TM + m) * 4);
         fence_proxy_async();
-        mbar_arrive(smem_u32(&raw_empty));
+        mbar_arrive(smem_u32(&raw_empty[r]));
         const float sc = srow[m];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {  // 16-byte chunk q of this half: k = 32 h + 8 q ..
+        for (int q = 0; q < 2; ++q) {  // 16-byte chunk 2 h + q: k = 16 h + 8 q ..
           float sl[4][8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -493,7 +556,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
             bad |= !(fabsf(a) < 128.f);
             cut4(a, sl[0][i], sl[1][i], sl[2][i], sl[3][i]);
           }
-          const uint32_t off = sw_off(m, h * 4 + q);
+          const uint32_t off = sw64_off(m, h * 2 + q);
 #pragma unroll
           for (int t = 0; t < NSL; ++t)
             *reinterpret_cast<uint4*>(sp + t * A_SLICE + off) =
@@ -506,18 +569,42 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       mbar_arrive(smem_u32(&st_full[s]));
       ++it;
     }
-    if (tid == 0)
-      for (int j = (xissued > SSTAGES ? xissued - SSTAGES : 0); j < xissued; ++j)
+  } else if (warp == W_XTMA) {
+    // ---------------------------------------------------------- bulk copies of the X slices
+    // the four pre-cut slices of a K tile are one contiguous 16 KB block of Xs,
+    // already in the stage's swizzled order
+    if (lane == 0) {
+      const int64_t nkt_pad = 2 * ((n + KPAD - 1) / KPAD);  // K tiles of the padded Xs
+      int it = 0;
+      const uint64_t pol = l2_policy_evict_last();  // every row block re-reads X
+      for (int kt = next_active(0); kt < nkt; kt = next_active(kt + 1)) {
+        const int s = it % SSTAGES;
+        if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag, poll_limit))
+          break;
+        const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
+        mbar_arrive_tx(smem_u32(&x_full[s]), (uint32_t)(NSL * XB));
+        const int64_t tile = (int64_t)ct * nkt_pad + kt;
+        bulk_load_hint(st + NSL * A_SLICE + XZ * XB, Xs + tile * (NSL * TN * TK),
+                       (uint32_t)(NSL * XB), smem_u32(&x_full[s]), pol);
+        // the tile SSTAGES active tiles ahead, into L2 while this stage turns over
+        int kp = kt;
+        for (int i = 0; i < SSTAGES && kp < nkt; ++i) kp = next_active(kp + 1);
+        if (kp < nkt)
+          bulk_prefetch_l2(Xs + ((int64_t)ct * nkt_pad + kp) * (NSL * TN * TK),
+                           (uint32_t)(NSL * XB));
+        ++it;
+      }
+      for (int j = (it > SSTAGES ? it - SSTAGES : 0); j < it; ++j)
         mbar_wait_drain(smem_u32(&x_full[j % SSTAGES]), (j / SSTAGES) & 1);
+    }
   } else if (warp == W_MMA) {
     // ---------------------------------------------------------- MMA issue
     if (lane == 0) {
-      int it = 0, wc = 0, cur = -1, pos = 0;  // pos: active tiles so far in the window
-      uint32_t started = 0, dbase = 0, chain_ph = 0;
+      int it = 0, wc = 0, cur = -1;
+      uint32_t started = 0, dbase = 0;
       bool ok = true;
-      for (int kt = 0; kt < nkt && ok; ++kt) {
-        const int fl = active(kt);
-        if (!fl) continue;
+      const uint32_t id = idesc_bf16_f32_n(NSL * TN);  // M = 128, N = 256
+      for (int kt = next_active(0); kt < nkt && ok; kt = next_active(kt + 1)) {
         const int w = kt / WIN_TILES;
         if (w != cur) {
           if (cur >= 0) {
@@ -529,7 +616,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
           if (!ok) break;
           dbase = tmem + (uint32_t)((wc & 1) * 4 * TN);
           started = 0;
-          pos = 0;
         }
         const int s = it % SSTAGES;
         ok = mbar_wait(smem_u32(&st_full[s]), (it / SSTAGES) & 1, &abort_flag, poll_limit) &&
@@ -537,27 +623,20 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
         if (!ok) break;
         tc_fence_after();
         const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
-        // chains s = 1..4 on even positions, 4..1 on odd ones: the window's first
-        // MMA (s = 1, N = 256) overwrites all four accumulators
-        for (int c = 0; c < NSL && ok; ++c) {
-          const int sa = (pos & 1) ? NSL - 1 - c : c;
-          if (c > 0) {  // the previous chain had another shape: let it complete
-            mma_commit(smem_u32(&bar_chain));
-            ok = mbar_wait(smem_u32(&bar_chain), chain_ph, &abort_flag, poll_limit);
-            chain_ph ^= 1;
-            if (!ok) break;
-          }
+        // descriptors of the stage's operands: the address field holds addr / 16
+        // (the stage lies below 256 KB, so offsets add without carry)
+        const uint64_t d0 = sw64_desc(st);
 #pragma unroll
-          for (int kk = 0; kk < TK / 16; ++kk) {
-            const uint64_t ad = sw128_desc(st + sa * A_SLICE + kk * 32);
-            const uint64_t bd = sw128_desc(st + NSL * A_SLICE + kk * 32);
-            // A slice sa + 1 times X slices 1 .. NSL - sa
-            mma_bf16(dbase + (uint32_t)(sa * TN), ad, bd, idesc_bf16_f32_n((NSL - sa) * TN),
-                     started);
+        for (int sa = 0; sa < NSL; ++sa) {
+          // A slice sa + 1 times [0 .. x1 .. x(4 - sa)]: the 256 rows from block 3 - sa
+          const uint64_t ad = d0 + (uint64_t)((sa * A_SLICE) >> 4);
+          const uint64_t bd = d0 + (uint64_t)((NSL * A_SLICE + (XZ - sa) * XB) >> 4);
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk) {  // K step kk is 32 bytes on
+            mma_bf16(dbase, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), id, started);
             started = 1;
           }
         }
-        ++pos;
         mma_commit(smem_u32(&st_empty[s]));
         ++it;
       }
@@ -655,7 +734,7 @@ size_t gemm_esg_smem_bytes() { return (size_t)LAYOUT_BYTES + 1024; }
 // bytes of the pre-cut X workspace: four BF16 slices per padded column tile,
 // then one int exponent per (window, column) (sized per K tile, which is more)
 int64_t gemm_esg_work_bytes(int64_t n, int64_t ncols) {
-  const int64_t kpad = ((n + TK - 1) / TK) * TK;
+  const int64_t kpad = ((n + KPAD - 1) / KPAD) * KPAD;
   const int64_t nct = (ncols + TN - 1) / TN;
   const int64_t xs = nct * NSL * TN * kpad * 2;
   return ((xs + 255) / 256) * 256 + (kpad / TK) * nct * TN * 4;
@@ -672,13 +751,14 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
                     const int* aexp, uint8_t* flags, int* err, cudaStream_t st) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tc::encode_fn();
   if (!enc || !gemm_tc_supported(A, lda, n)) return 1;
-  const int64_t kpad = ((n + TK - 1) / TK) * TK;
+  const int64_t kpad = ((n + KPAD - 1) / KPAD) * KPAD;
   const int nct = (int)((ncols + TN - 1) / TN);
   const int nkt = (int)(kpad / TK);
+  if (nkt > MAX_KT) return 1;
   __nv_bfloat16* Xs = (__nv_bfloat16*)work;
   const int64_t xs_bytes = (int64_t)nct * NSL * TN * kpad * 2;
   int* ex = (int*)((unsigned char*)work + ((xs_bytes + 255) / 256) * 256);
-  CUtensorMap tmA, tmX;
+  CUtensorMap tmA;
   const cuuint64_t adim[2] = {(cuuint64_t)n, (cuuint64_t)n};
   const cuuint64_t astr[1] = {(cuuint64_t)lda * 4};
   const cuuint32_t abox[2] = {trans ? (cuuint32_t)TM : (cuuint32_t)TK,
@@ -686,13 +766,6 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
   const cuuint32_t one[2] = {1, 1};
   if (enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)A, adim, astr, abox, one,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return 2;
-  const cuuint64_t xdim[2] = {(cuuint64_t)kpad, (cuuint64_t)NSL * TN * nct};
-  const cuuint64_t xstr[1] = {(cuuint64_t)kpad * 2};
-  const cuuint32_t xbox[2] = {(cuuint32_t)TK, (cuuint32_t)TN};
-  if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Xs, xdim, xstr, xbox, one,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return 2;
   count_launches(2);
@@ -726,11 +799,11 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
   dim3 grid((unsigned)nct, (unsigned)nrb, (unsigned)ks);
   if (trans) {
     raise_smem_limit((const void*)k_gemm_esg<1, 0>, done[1]);
-    k_gemm_esg<1, 0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
+    k_gemm_esg<1, 0><<<grid, NTHREADS, smem, st>>>(tmA, Xs, n, ncols, flags, ex, e_rows, Y, ldy,
                                                    err, wait_limit(), nullptr, nullptr);
   } else {
     raise_smem_limit((const void*)k_gemm_esg<0, 0>, done[0]);
-    k_gemm_esg<0, 0><<<grid, NTHREADS, smem, st>>>(tmA, tmX, n, ncols, flags, ex, e_rows, Y, ldy,
+    k_gemm_esg<0, 0><<<grid, NTHREADS, smem, st>>>(tmA, Xs, n, ncols, flags, ex, e_rows, Y, ldy,
                                                    err, wait_limit(), nullptr, nullptr);
   }
   return 0;
@@ -798,23 +871,16 @@ void launch_logtab_block(const float* S, const float* P, int64_t n, int64_t r0, 
 int launch_gemm_esg_gen(const float* S, const float* P, const int* rowexp, int64_t n,
                         int64_t ncols, const double* X, int64_t ldx, double* Y, int64_t ldy,
                         void* work, uint8_t* flags, int* err, cudaStream_t st) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tc::encode_fn();
-  if (!enc) return 1;
-  const int64_t kpad = ((n + TK - 1) / TK) * TK;
+  const int64_t kpad = ((n + KPAD - 1) / KPAD) * KPAD;
   const int nct = (int)((ncols + TN - 1) / TN);
   const int nkt = (int)(kpad / TK);
+  if (nkt > MAX_KT) return 1;
   __nv_bfloat16* Xs = (__nv_bfloat16*)work;
   const int64_t xs_bytes = (int64_t)nct * NSL * TN * kpad * 2;
   int* ex = (int*)((unsigned char*)work + ((xs_bytes + 255) / 256) * 256);
-  CUtensorMap tmX;
-  const cuuint32_t one[2] = {1, 1};
-  const cuuint64_t xdim[2] = {(cuuint64_t)kpad, (cuuint64_t)NSL * TN * nct};
-  const cuuint64_t xstr[1] = {(cuuint64_t)kpad * 2};
-  const cuuint32_t xbox[2] = {(cuuint32_t)TK, (cuuint32_t)TN};
-  if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Xs, xdim, xstr, xbox, one,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return 2;
+  // the kernel takes no TMA map of A in this form: a zeroed map fills the slot
+  CUtensorMap tm0;
+  memset(&tm0, 0, sizeof(tm0));
   count_launches(2);
   const int nwin = (nkt + WIN_TILES - 1) / WIN_TILES;
   k_split_x64<<<dim3(nwin, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, ex, flags);
@@ -841,8 +907,7 @@ int launch_gemm_esg_gen(const float* S, const float* P, const int* rowexp, int64
     return 2;
   dim3 grid((unsigned)nct, (unsigned)nrb, (unsigned)ks);
   raise_smem_limit((const void*)k_gemm_esg<0, 1>, done);
-  // the kernel takes no TMA map of A in this form; the X map fills the slot
-  k_gemm_esg<0, 1><<<grid, NTHREADS, smem, st>>>(tmX, tmX, n, ncols, flags, ex, rowexp, Y, ldy,
+  k_gemm_esg<0, 1><<<grid, NTHREADS, smem, st>>>(tm0, Xs, n, ncols, flags, ex, rowexp, Y, ldy,
                                                  err, wait_limit(), S, P);
   return 0;
 }
