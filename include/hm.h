@@ -504,6 +504,26 @@ hm_status hm_hodlr_factored_adjoint(const hm_tree* tree, int32_t k, const float*
                                     const float* r, float scale, float* gx, float* gU,
                                     float* gV, float* gD, void* stream);
 
+/*
+ * One training step of the factored HODLR form: the forward product, the
+ * residual and the adjoint above at it, in one call,
+ *   y = H x,  r = y - b,  then gx, gU, gV, gD exactly as hm_hodlr_factored_adjoint
+ *   with this r (scale = 2: the gradients of ||H x - b||^2).
+ * The forward's projections V_j(I_b)^T x(I_b) are the ones the adjoint needs, so
+ * they are computed once: every factor is read twice per call (U, V and D by
+ * the forward and by the adjoint), where the two separate calls read V three
+ * times.  b: device, length N.  y, r: device outputs of length N, or NULL (then
+ * kept in scratch).  Gradient outputs as in hm_hodlr_factored_adjoint (any may
+ * be NULL).  Scratch of O(k * (N / 256 * L + 2^(L+1)) + 2 N) floats is taken
+ * from the stream's CUDA memory pool and released in order.  Results equal the
+ * two separate calls up to the summation order of the node projections
+ * (FP32 rounding).  Errors as hm_hodlr_factored_adjoint.
+ */
+hm_status hm_hodlr_factored_loss_grad(const hm_tree* tree, int32_t k, const float* U,
+                                      const float* V, const float* D, const float* x,
+                                      const float* b, float scale, float* y, float* r,
+                                      float* gx, float* gU, float* gV, float* gD, void* stream);
+
 /* ------------------------------------------------------ workload helpers --- */
 
 /*

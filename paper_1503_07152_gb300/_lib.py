@@ -83,6 +83,8 @@ _sig = {
     "hm_hodlr_factored_apply_noalloc": ([_P, C.c_int32, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
     "hm_hodlr_factored_adjoint": ([_P, C.c_int32, _P, _P, _P, _P, _P, C.c_float, _P, _P, _P, _P, _P],
                                   C.c_int),
+    "hm_hodlr_factored_loss_grad": ([_P, C.c_int32, _P, _P, _P, _P, _P, C.c_float, _P, _P, _P, _P,
+                                     _P, _P, _P], C.c_int),
     "hm_gen_log_kernel": ([_P, C.c_int64, C.c_int64, _P], C.c_int),
     "hm_hodlr_export_level": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "hm_gaussian_test_matrix": ([_P, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, _P, C.c_int64, _P],
@@ -439,6 +441,16 @@ def hm_hodlr_factored_adjoint(tree: Tree, k: int, U, V, D, x, r, scale=1.0, gx=N
     _check(lib.hm_hodlr_factored_adjoint(tree.ptr, k, _ptr(U), _ptr(V), _ptr(D), _ptr(x), _ptr(r),
                                          float(scale), _ptr(gx), _ptr(gU), _ptr(gV), _ptr(gD),
                                          C.c_void_p(_stream(stream))), "hm_hodlr_factored_adjoint")
+
+
+def hm_hodlr_factored_loss_grad(tree: Tree, k: int, U, V, D, x, b, scale=2.0, y=None, r=None,
+                                gx=None, gU=None, gV=None, gD=None, stream=None) -> None:
+    """y = H x, r = y - b and the adjoint at r (gradients of ||H x - b||^2 at scale 2)."""
+    _check(lib.hm_hodlr_factored_loss_grad(tree.ptr, k, _ptr(U), _ptr(V), _ptr(D), _ptr(x),
+                                           _ptr(b), float(scale), _ptr(y), _ptr(r), _ptr(gx),
+                                           _ptr(gU), _ptr(gV), _ptr(gD),
+                                           C.c_void_p(_stream(stream))),
+           "hm_hodlr_factored_loss_grad")
 
 
 def hm_gen_log_kernel(A: torch.Tensor, stream=None) -> None:

@@ -278,6 +278,27 @@ hm_status hm_hodlr_factored_adjoint(const hm_tree* tree, int32_t k, const float*
   return check_launch("hm_hodlr_factored_adjoint");
 }
 
+hm_status hm_hodlr_factored_loss_grad(const hm_tree* tree, int32_t k, const float* U,
+                                      const float* V, const float* D, const float* x,
+                                      const float* b, float scale, float* y, float* res,
+                                      float* gx, float* gU, float* gV, float* gD, void* stream) {
+  clear_error();
+  if (!tree || k < 1 || k > 64 || !U || !V || !D || !x || !b || tree->L < 1) {
+    set_error("hm_hodlr_factored_loss_grad: need tree (L >= 1), 1 <= k <= 64, U, V, D, x, b");
+    return HM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  HM_TRY(factored_check(tree, false));
+  HM_TRY(factored_check(tree, true));
+  HM_TRY(tree_device(const_cast<hm_tree*>(tree), st));
+  float* scratch = nullptr;
+  const size_t sbytes = factored_loss_grad_scratch_bytes(tree, k);
+  HM_CUDA_TRY(cudaMallocAsync((void**)&scratch, sbytes, st));
+  launch_factored_loss_grad(tree, k, U, V, D, x, b, scale, y, res, gx, gU, gV, gD, scratch, st);
+  cudaFreeAsync(scratch, st);
+  return check_launch("hm_hodlr_factored_loss_grad");
+}
+
 }  // extern "C"
 
 extern "C" hm_status hm_gaussian_test_matrix(const hm_tree* tree, int32_t level, int32_t r,

@@ -252,6 +252,11 @@ void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const floa
                              const float* D, const float* x, const float* res, float scale,
                              float* gx, float* gU, float* gV, float* gD, float* scratch,
                              cudaStream_t st);
+size_t factored_loss_grad_scratch_bytes(const hm_tree* t, int k);
+void launch_factored_loss_grad(const hm_tree* t, int k, const float* U, const float* V,
+                               const float* D, const float* x, const float* b, float scale,
+                               float* y, float* res, float* gx, float* gU, float* gV, float* gD,
+                               float* scratch, cudaStream_t st);
 
 }  // namespace hm
 

@@ -87,7 +87,8 @@ __global__ __launch_bounds__(256) void k_fact_reduce(const float* __restrict__ p
   }
 }
 
-// y(I_leaf) = sum_j Uex_j(I_leaf) coef[sib(anc_j)] + op(D_leaf) x(I_leaf)
+// y(I_leaf) = sum_j Uex_j(I_leaf) coef[sib(anc_j)] + op(D_leaf) x(I_leaf); with
+// b, also res = y - b
 __global__ __launch_bounds__(256) void k_fact_expand(const int64_t* __restrict__ start,
                                                      const int64_t* __restrict__ size, int L,
                                                      int64_t n, int k, int nmax, int width,
@@ -95,7 +96,9 @@ __global__ __launch_bounds__(256) void k_fact_expand(const int64_t* __restrict__
                                                      const float* __restrict__ coef,
                                                      const float* __restrict__ D, int trans,
                                                      const float* __restrict__ x,
-                                                     float* __restrict__ y) {
+                                                     float* __restrict__ y,
+                                                     const float* __restrict__ b,
+                                                     float* __restrict__ res) {
   extern __shared__ float sm[];
   float* cs = sm;                  // L * k coefficients
   float* xs = sm + L * kMaxK;      // leaf slice of x
@@ -134,16 +137,18 @@ __global__ __launch_bounds__(256) void k_fact_expand(const int64_t* __restrict__
     } else {
       for (int m = 0; m < ns; ++m) acc = fmaf(Dl[i + (int64_t)m * nmax], xs[m], acc);
     }
-    y[row] = acc;
+    if (y) y[row] = acc;
+    if (b) res[row] = acc - b[row];
   }
 }
 
-// Adjoint rows of one leaf.  coef holds [t | s] per node (width 2k):
-// t_node = V_j(I_node)^T x, s_node = U_j(I_node)^T res.
+// Adjoint rows of one leaf.  Per node, coef_t holds t_node = V_j(I_node)^T x and
+// coef_s holds s_node = U_j(I_node)^T res, at node * cw (+ the k entries).
 __global__ __launch_bounds__(256) void k_fact_adjoint(
     const int64_t* __restrict__ start, const int64_t* __restrict__ size, int L, int64_t n, int k,
     int nmax, const float* __restrict__ U, const float* __restrict__ V,
-    const float* __restrict__ D, const float* __restrict__ coef, const float* __restrict__ x,
+    const float* __restrict__ D, const float* __restrict__ coef_t,
+    const float* __restrict__ coef_s, int cw, const float* __restrict__ x,
     const float* __restrict__ res, float scale, float* __restrict__ gx, float* __restrict__ gU,
     float* __restrict__ gV, float* __restrict__ gD) {
   extern __shared__ float sm[];
@@ -159,8 +164,8 @@ __global__ __launch_bounds__(256) void k_fact_adjoint(
   for (int e = tid; e < L * k; e += blockDim.x) {
     const int j = 1 + e / k, col = e % k;
     const int sib = (leaf >> (L - j)) ^ 1;
-    ts[(j - 1) * kMaxK + col] = coef[(int64_t)sib * 2 * k + col];
-    ss[(j - 1) * kMaxK + col] = coef[(int64_t)sib * 2 * k + k + col];
+    ts[(j - 1) * kMaxK + col] = coef_t[(int64_t)sib * cw + col];
+    ss[(j - 1) * kMaxK + col] = coef_s[(int64_t)sib * cw + col];
   }
   for (int m = tid; m < ns; m += blockDim.x) {
     xs[m] = x[s0 + m];
@@ -261,7 +266,8 @@ void launch_factored_apply(const hm_tree* t, int k, const float* U, const float*
   const int nmax = (int)t->nmax;
   const size_t smem = fact_leaf_smem(t, false);
   k_fact_expand<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, k,
-                                           trans ? V : U, coef, D, trans, x, y);
+                                           trans ? V : U, coef, D, trans, x, y, nullptr,
+                                           nullptr);
 }
 
 void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const float* V,
@@ -278,7 +284,43 @@ void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const floa
   const int nmax = (int)t->nmax;
   const size_t smem = fact_leaf_smem(t, true);
   k_fact_adjoint<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, U, V, D,
-                                            coef, x, res, scale, gx, gU, gV, gD);
+                                            coef, coef + k, 2 * k, x, res, scale, gx, gU, gV,
+                                            gD);
+}
+
+size_t factored_loss_grad_scratch_bytes(const hm_tree* t, int k) {
+  const size_t nodes = (size_t)1 << (t->L + 1);
+  return sizeof(float) * ((size_t)t->n_fchunks * k + 2 * nodes * k + 2 * (size_t)t->n) + 512;
+}
+
+// y = H x, res = y - b and the adjoint at res, with every factor read twice: the
+// forward's projections t = V^T x are the adjoint's too, so the adjoint's first
+// pass reads U only, and V is read again only for gx.
+void launch_factored_loss_grad(const hm_tree* t, int k, const float* U, const float* V,
+                               const float* D, const float* x, const float* b, float scale,
+                               float* y, float* res, float* gx, float* gU, float* gV, float* gD,
+                               float* scratch, cudaStream_t st) {
+  count_launches(6);
+  const int L = t->L;
+  const int nodes = 1 << (L + 1);
+  const int nmax = (int)t->nmax;
+  float* partial = scratch;
+  float* coef_t = partial + (size_t)t->n_fchunks * k;
+  float* coef_s = coef_t + (size_t)nodes * k;
+  float* tmp = coef_s + (size_t)nodes * k;
+  float* yy = y ? y : tmp;
+  float* rr = res ? res : tmp + t->n;
+  k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, V, x,
+                                                                   nullptr, nullptr, partial);
+  k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, k, nodes, coef_t);
+  k_fact_expand<<<1 << L, 256, fact_leaf_smem(t, false), st>>>(
+      t->d_start, t->d_size, L, t->n, k, nmax, k, U, coef_t, D, 0, x, yy, b, rr);
+  k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, U, rr,
+                                                                   nullptr, nullptr, partial);
+  k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, k, nodes, coef_s);
+  k_fact_adjoint<<<1 << L, 256, fact_leaf_smem(t, true), st>>>(
+      t->d_start, t->d_size, L, t->n, k, nmax, U, V, D, coef_t, coef_s, k, x, rr, scale, gx, gU,
+      gV, gD);
 }
 
 }  // namespace hm

@@ -139,6 +139,20 @@ def test_factored_apply_adjoint_n262144():
     num = sum(float(np.sum((gDh[i].T - d) ** 2)) for i, d in enumerate(dD))
     den = sum(float(np.sum(d ** 2)) for d in dD)
     assert (num / den) ** 0.5 < 1e-5
+    # the fused training step the bench times, against the same oracle values
+    y2 = torch.empty_like(xd)
+    g2 = [torch.empty_like(a) for a in (xd, U, V, D)]
+    hm.hm_hodlr_factored_loss_grad(t, k, U, V, D, xd, torch.from_numpy(b).to(DEV), 2.0, y2, None,
+                                   *g2)
+    torch.cuda.synchronize()
+    assert rel(y2.cpu().numpy(), ograd.apply(f, x64)) < 1e-5
+    assert rel(g2[0].cpu().numpy(), dx) < 1e-5
+    gUh, gVh, gDh = g2[1].cpu().numpy(), g2[2].cpu().numpy(), g2[3].cpu().numpy()
+    for j in range(1, L + 1):
+        assert rel(gUh[j - 1].T, dU[j]) < 1e-5, j
+        assert rel(gVh[j - 1].T, dV[j]) < 1e-5, j
+    num = sum(float(np.sum((gDh[i].T - d) ** 2)) for i, d in enumerate(dD))
+    assert (num / den) ** 0.5 < 1e-5
 
 
 def test_batched_64_operators_against_factors():

@@ -205,6 +205,29 @@ def test_factored_apply_and_adjoint(N, m, k):
         assert rel(gDh[i, :n, :n].T, d) < 1e-5
         # the padding of a leaf smaller than n_max is written as zero (uneven leaves at N=3000)
         assert np.all(gDh[i, n:, :] == 0.0) and np.all(gDh[i, :, n:] == 0.0)
+    # the fused training step (forward, residual, adjoint in one call, the forward's
+    # projections reused) against the same oracle values
+    bd = torch.from_numpy(b).to(DEV)
+    y2, r2 = torch.full_like(xd, float("nan")), torch.full_like(xd, float("nan"))
+    g2 = [torch.full_like(a, float("nan")) for a in (xd, U, V, D)]
+    hm.hm_hodlr_factored_loss_grad(t, k, U, V, D, xd, bd, 2.0, y2, r2, *g2)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(y2.cpu().numpy() - want) <= 1e-5 * np.linalg.norm(want)
+    assert rel(r2.cpu().numpy(), want - b) < 1e-5
+    assert rel(g2[0].cpu().numpy(), dx) < 1e-5
+    for j in range(1, L + 1):
+        assert rel(g2[1][j - 1].cpu().numpy().T, dU[j]) < 1e-5
+        assert rel(g2[2][j - 1].cpu().numpy().T, dV[j]) < 1e-5
+    gDh2 = g2[3].cpu().numpy()
+    for i, d in enumerate(dD):
+        n = d.shape[0]
+        assert rel(gDh2[i, :n, :n].T, d) < 1e-5
+        assert np.all(gDh2[i, n:, :] == 0.0) and np.all(gDh2[i, :, n:] == 0.0)
+    # y and r may stay in scratch
+    g3 = torch.full_like(xd, float("nan"))
+    hm.hm_hodlr_factored_loss_grad(t, k, U, V, D, xd, bd, 2.0, None, None, g3)
+    torch.cuda.synchronize()
+    assert torch.equal(g3, g2[0])
 
 
 def test_autograd_function_matches_adjoint():
