@@ -389,7 +389,8 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
         d->xs_bytes = need;
       }
       if (!d->aexp) {
-        if (cudaMalloc(&d->aexp, sizeof(int) * 2 * (size_t)n) != cudaSuccess) return 3;
+        if (cudaMalloc(&d->aexp, sizeof(int) * 2 * (size_t)gemm_esg_exp_count(n)) != cudaSuccess)
+          return 3;
         launch_esg_scales((const float*)d->A, d->lda, n, d->aexp, st);
       }
       if (launch_gemm_esg((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
@@ -483,7 +484,7 @@ hm_status hm_log_kernel_operator_create(int64_t n, hm_operator* out) {
   if (s == HM_OK) s = device_alloc((void**)&d->err, sizeof(int));
   if (s == HM_OK) s = device_alloc((void**)&d->tabS, sizeof(float) * hs.size());
   if (s == HM_OK) s = device_alloc((void**)&d->tabP, sizeof(float) * hp.size());
-  if (s == HM_OK) s = device_alloc((void**)&d->aexp, sizeof(int) * (size_t)n);
+  if (s == HM_OK) s = device_alloc((void**)&d->aexp, sizeof(int) * (size_t)gemm_esg_exp_count(n));
   if (s == HM_OK &&
       (cudaMemcpy(d->tabS, hs.data(), sizeof(float) * hs.size(), cudaMemcpyHostToDevice) !=
            cudaSuccess ||

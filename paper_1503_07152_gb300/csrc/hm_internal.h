@@ -96,6 +96,10 @@ bool gemm_tc_supported(const float* A, int64_t lda, int64_t n);
 size_t gemm_esg_smem_bytes();
 int64_t gemm_esg_work_bytes(int64_t n, int64_t ncols);
 // row exponents then column exponents of A (2 n ints), taken once per operator
+// Exponents of A per row and per column, each per window of 256 (n * nw ints
+// each, nw = ceil(n / 256)): gemm_esg_exp_count(n) row entries, then as many
+// column entries.
+int64_t gemm_esg_exp_count(int64_t n);
 void launch_esg_scales(const float* A, int64_t lda, int64_t n, int* aexp, cudaStream_t st);
 int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
                     const double* X, int64_t ldx, double* Y, int64_t ldy, void* work,
@@ -311,7 +315,7 @@ struct hm_dense_ctx {
   void* xs = nullptr;        // split copy of X for the tensor-core engine
   int64_t xs_bytes = 0;
   int* err = nullptr;        // device flag raised by a kernel that gave up waiting
-  int* aexp = nullptr;       // dtype 4: row then column exponents of A (taken at first use)
+  int* aexp = nullptr;       // dtype 4 / 5: row (then column) exponents of A per 256-wide window
   float* tabS = nullptr;     // dtype 5 (matrix-free log kernel): S[|i - j|] and P[i + j]
   float* tabP = nullptr;
 };

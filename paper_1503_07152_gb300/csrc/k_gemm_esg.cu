@@ -4,10 +4,10 @@
 // A Omega / A^* Omega of the compression figures, without FP64 arithmetic in
 // the contraction).
 //
-// Exact-accumulation split: every row of op(A) (over all of K; the exponents
-// are recorded once per operator) and every column of X inside a window of
-// 256 K values is scaled by a power of two so that its largest entry lies in
-// [64, 128), and cut into four 8-bit integer slices
+// Exact-accumulation split: every row of op(A) and every column of X inside a
+// window of 256 K values (the A exponents are recorded once per operator) is
+// scaled by a power of two so that its largest entry lies in [64, 128), and cut
+// into four 8-bit integer slices
 // (a = sum_s a_s 2^(-8(s-1)) up to the scale, |a_s| <= 128, each exact in BF16).
 // A BF16 x BF16 product of slices is an integer of magnitude <= 2^14, and the
 // products of one order d = s + t (d = 2..5, at most four of them) summed over
@@ -136,29 +136,38 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-// Row exponents of A (e with max_j |A(i, j)| < 2^e, clamped to >= -120): one
-// warp per row.
+// Exponents of A per row and window of 256 columns: e_row[i * nw + w] = e with
+// max over the window of |A(i, j)| < 2^e (clamped to >= -120).  One warp per
+// row, eight entries per lane and window.
 __global__ __launch_bounds__(256) void k_row_exp(const float* __restrict__ A, int64_t lda,
-                                                 int64_t n, int* __restrict__ e_row) {
+                                                 int64_t n, int nw, int* __restrict__ e_row) {
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const float* a = A + row * lda;
-  float mx = 0.f;
-  for (int64_t j = lane; j < n; j += 32) mx = fmaxf(mx, fabsf(a[j]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) e_row[row] = max(exp_above(mx), -120);
+  for (int w = 0; w < nw; ++w) {
+    float mx = 0.f;
+    for (int64_t j = (int64_t)w * WIN_ROWS + lane; j < n && j < (int64_t)(w + 1) * WIN_ROWS;
+         j += 32)
+      mx = fmaxf(mx, fabsf(a[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) e_row[row * nw + w] = max(exp_above(mx), -120);
+  }
 }
 
-// Column exponents of A: one thread per column, rows streamed.
+// The same per column and window of 256 rows (the rows of op(A) = A^T): one
+// thread per column, rows streamed.
 __global__ __launch_bounds__(256) void k_col_exp(const float* __restrict__ A, int64_t lda,
-                                                 int64_t n, int* __restrict__ e_col) {
+                                                 int64_t n, int nw, int* __restrict__ e_col) {
   const int64_t col = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (col >= n) return;
-  float mx = 0.f;
+  for (int w = 0; w < nw; ++w) {
+    float mx = 0.f;
+    const int64_t i1 = (n < (int64_t)(w + 1) * WIN_ROWS) ? n : (int64_t)(w + 1) * WIN_ROWS;
 #pragma unroll 8
-  for (int64_t i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(A[i * lda + col]));
-  e_col[col] = max(exp_above(mx), -120);
+    for (int64_t i = (int64_t)w * WIN_ROWS; i < i1; ++i) mx = fmaxf(mx, fabsf(A[i * lda + col]));
+    e_col[col * nw + w] = max(exp_above(mx), -120);
+  }
 }
 
 // X (FP64, column-major n x ncols) -> per (window, column) exponents and four
@@ -250,7 +259,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       x_full[SSTAGES], st_empty[SSTAGES], acc_full[2], acc_empty[2], bar_final;
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
-  __shared__ float srow[TM];  // 2^(7 - e), e the exponent of the row of op(A)
   __shared__ int win_lo, win_hi;  // this block's share of the windows (split over K)
   __shared__ uint32_t act_bits[MAX_KT / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -262,6 +270,10 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* sbase = smem_raw + (base - raw);
   const uint32_t raw_addr = base, stage_addr0 = base + RAW_REGION;
+  // 2^(7 - e), e the exponent of row m of this block in window w (1 past n)
+  auto row_scale = [&](int m, int w) -> float {
+    return pow2f(7 - ((m0 + m < n) ? e_rows[(m0 + m) * nwin + w] : 0));
+  };
 
   if (tid == 0) {
     abort_flag = 0;
@@ -280,10 +292,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
     }
     mbar_init(smem_u32(&bar_final), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (tid < TM) {
-    const int e = (m0 + tid < n) ? e_rows[m0 + tid] : 0;
-    srow[tid] = pow2f(7 - e);
   }
   // the zero blocks in front of each stage's X slices, written once; the MMAs
   // read them through the async proxy
@@ -424,6 +432,9 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       const int k1 = next_active(0);
       if (k1 < nkt) load_win(k1);
     }
+    constexpr int NP = TM * TK / 4 / NCONV;  // 4 passes: rows 32 p + tid / 8
+    float scs[NP];                           // this thread's row scales in window scw
+    int scw = -1;
     for (int kt = next_active(0); kt < nkt; kt = next_active(kt + 1)) {
       const int s = it % SSTAGES;
       const bool ok = !abort_flag &&
@@ -455,10 +466,15 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       const int mrow = (int)(n - m0 < TM ? n - m0 : TM), kcol = (int)(n - k0 < TK ? n - k0 : TK);
       unsigned char* sp = sbase + (st - base);
       int bad = 0;
+      if (kt / WIN_TILES != scw) {
+        scw = kt / WIN_TILES;
 #pragma unroll
-      for (int p = 0; p < TM * TK / 4 / NCONV; ++p) {
+        for (int p = 0; p < NP; ++p) scs[p] = row_scale((p * NCONV + tid) >> 3, scw);
+      }
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
         const int f = p * NCONV + tid, m = f >> 3, k4 = f & 7;
-        const float sc = srow[m];
+        const float sc = scs[p];
         const int q = m & 3, ps = m + 4 * k4 - q, ds = m - 4 * k4 + (TK - 4) - q;
         const float4 sh4 = *reinterpret_cast<const float4*>(win + (0 * 4 + q) * WC + ds);
         const float4 sl4 = *reinterpret_cast<const float4*>(win + (1 * 4 + q) * WC + ds);
@@ -499,8 +515,20 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
   } else if (warp < 8) {
     // ---------------------------------------------------------- cut A, TMA of X
     int it = 0;
+    constexpr int NP = TM * TK / 4 / NCONV;  // 4 passes: rows 32 p + tid / 8 (not TRANS)
+    float scs[NP];                           // this thread's row scales in window scw
+    int scw = -1;
     for (int kt = next_active(0); kt < nkt && !abort_flag; kt = next_active(kt + 1)) {
       const int s = it % SSTAGES, r = it % RSTAGES;
+      if (kt / WIN_TILES != scw) {  // (issued before the raw wait: the loads overlap it)
+        scw = kt / WIN_TILES;
+        if (!TRANS) {
+#pragma unroll
+          for (int p = 0; p < NP; ++p) scs[p] = row_scale((p * NCONV + tid) >> 3, scw);
+        } else {
+          scs[0] = row_scale(tid & (TM - 1), scw);
+        }
+      }
       if (!mbar_wait(smem_u32(&st_empty[s]), ((it / SSTAGES) & 1) ^ 1, &abort_flag, poll_limit))
         break;
       const uint32_t st = stage_addr0 + (uint32_t)s * STAGE_BYTES;
@@ -510,7 +538,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       int bad = 0;
       if (!TRANS) {
         // raw [128 rows][32 k]; pass p: rows 32p .. 32p+31, 8 threads per row
-        constexpr int NP = TM * TK / 4 / NCONV;  // 4
         float4 v[NP];
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
@@ -523,7 +550,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
           const int f = p * NCONV + tid, m = f >> 3, k4 = f & 7;
-          const float sc = srow[m];
+          const float sc = scs[p];
           float a[4] = {v[p].x * sc, v[p].y * sc, v[p].z * sc, v[p].w * sc};
           float sl[4][4];
 #pragma unroll
@@ -546,7 +573,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
           v[i] = *reinterpret_cast<const float*>(rw + ((h * 16 + i) * TM + m) * 4);
         fence_proxy_async();
         mbar_arrive(smem_u32(&raw_empty[r]));
-        const float sc = srow[m];
+        const float sc = scs[0];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {  // 16-byte chunk 2 h + q: k = 16 h + 8 q ..
           float sl[4][8];
@@ -657,7 +684,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
 #pragma unroll
     for (int j = 0; j < 32; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
     const int64_t colbase = (int64_t)ct * TN + half * 32;
-    const int ea = 7 - (((__float_as_int(srow[r]) >> 23) & 0xFF) - 127);  // row exponent
     int wc = 0;
     for (int w = 0; w < nwin; ++w) {
       int any = 0;
@@ -665,6 +691,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void k_gemm_esg(
       if (!any) continue;
       const int b = wc & 1;
       const int exl = ex[((int64_t)w * nct + ct) * TN + half * 32 + lane];  // column lane
+      const int ea = (m0 + r < n) ? e_rows[(m0 + r) * nwin + w] : 0;      // row, window
       if (!mbar_wait(smem_u32(&acc_full[b]), (wc >> 1) & 1, &abort_flag, poll_limit)) break;
       tc_fence_after();
       const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 4 * TN + half * 32);
@@ -740,10 +767,13 @@ int64_t gemm_esg_work_bytes(int64_t n, int64_t ncols) {
   return ((xs + 255) / 256) * 256 + (kpad / TK) * nct * TN * 4;
 }
 
+int64_t gemm_esg_exp_count(int64_t n) { return n * ((n + WIN_ROWS - 1) / WIN_ROWS); }
+
 void launch_esg_scales(const float* A, int64_t lda, int64_t n, int* aexp, cudaStream_t st) {
   count_launches(2);
-  k_row_exp<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(A, lda, n, aexp);
-  k_col_exp<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, n, aexp + n);
+  const int nw = (int)((n + WIN_ROWS - 1) / WIN_ROWS);
+  k_row_exp<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(A, lda, n, nw, aexp);
+  k_col_exp<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A, lda, n, nw, aexp + gemm_esg_exp_count(n));
 }
 
 int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t ncols,
@@ -771,7 +801,7 @@ int launch_gemm_esg(const float* A, int64_t lda, int trans, int64_t n, int64_t n
   count_launches(2);
   const int nwin = (nkt + WIN_TILES - 1) / WIN_TILES;
   k_split_x64<<<dim3(nwin, nct), 256, 0, st>>>(X, ldx, n, ncols, kpad, nct, Xs, ex, flags);
-  const int* e_rows = trans ? aexp + n : aexp;
+  const int* e_rows = trans ? aexp + gemm_esg_exp_count(n) : aexp;
   const size_t smem = gemm_esg_smem_bytes();
   static std::atomic<uint32_t> done[2] = {{0}, {0}};
   // Split over K when the row blocks alone leave the last wave of blocks
@@ -816,24 +846,27 @@ namespace {
 
 // The tables hold float pairs: S[0 .. n) high parts then S[n .. 2n) low parts,
 // P[0 .. 2n - 1) high parts then P[2n - 1 .. 4n - 2) low parts.
-// Row exponents of the matrix-free log kernel: e with max_j |A(i, j)| < 2^e
-// (clamped to >= -120), the entries formed exactly as the generating cutters
-// form them.  One warp per row.  The operator is symmetric: these are also the
-// column exponents.
+// Exponents of the matrix-free log kernel per row and window of 256 columns: e
+// with max |A(i, j)| < 2^e over the window (clamped to >= -120), the entries
+// formed exactly as the generating cutters form them.  One warp per row.  The
+// operator is symmetric: these are also the column exponents.
 __global__ __launch_bounds__(256) void k_row_exp_logtab(const float* __restrict__ S,
                                                         const float* __restrict__ P, int64_t n,
-                                                        int* __restrict__ e_row) {
+                                                        int nw, int* __restrict__ e_row) {
   const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  float mx = 0.f;
-  for (int64_t j = lane; j < n; j += 32) {
-    const int64_t d = row > j ? row - j : j - row;
-    const float v = (d == 0) ? 1.f : (S[d] + P[row + j]) + (S[n + d] + P[2 * n - 1 + row + j]);
-    mx = fmaxf(mx, fabsf(v));
+  for (int w = 0; w < nw; ++w) {
+    float mx = 0.f;
+    for (int64_t j = (int64_t)w * WIN_ROWS + lane; j < n && j < (int64_t)(w + 1) * WIN_ROWS;
+         j += 32) {
+      const int64_t d = row > j ? row - j : j - row;
+      const float v = (d == 0) ? 1.f : (S[d] + P[row + j]) + (S[n + d] + P[2 * n - 1 + row + j]);
+      mx = fmaxf(mx, fabsf(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) e_row[row * nw + w] = max(exp_above(mx), -120);
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0) e_row[row] = max(exp_above(mx), -120);
 }
 
 // out[(i - r0) * ld + (j - c0)] = A(i, j) of the matrix-free log kernel.
@@ -853,7 +886,8 @@ __global__ void k_logtab_block(const float* __restrict__ S, const float* __restr
 
 void launch_logtab_rowexp(const float* S, const float* P, int64_t n, int* e_row, cudaStream_t st) {
   count_launches(1);
-  k_row_exp_logtab<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(S, P, n, e_row);
+  k_row_exp_logtab<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(
+      S, P, n, (int)((n + WIN_ROWS - 1) / WIN_ROWS), e_row);
 }
 
 void launch_logtab_block(const float* S, const float* P, int64_t n, int64_t r0, int64_t r1,
