@@ -114,9 +114,14 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
     return HM_EUNSUPPORTED;
   }
   mark(c, lv - 1, c.side, HM_PHASE_TSQR);
-  for (size_t rd = 0; rd < lp.d_rounds.size(); ++rd)
-    launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rd > 0 ? 1 : 0, P, N, pc,
-                   c.Rw, c.st);
+  for (size_t rd = 0; rd < lp.d_rounds.size(); ++rd) {
+    if (sizeof(T) == 8 && c.bf16)  // HM_A32: the Householder work in double-float
+      launch_tsqr_df(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rd > 0 ? 1 : 0,
+                     (const double*)P, N, pc, (double*)c.Rw, c.st);
+    else
+      launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rd > 0 ? 1 : 0, P, N, pc,
+                     c.Rw, c.st);
+  }
   mark(c, lv - 1, c.side, HM_PHASE_SVD);
   if (sizeof(T) == 8 && c.bf16)  // HM_A32: the FP64 phases in double-float
     launch_jacobi_df(lp.d_final_slot, lp.nnodes, (const double*)c.Rw, pc, (double*)c.W,

@@ -69,6 +69,37 @@ __device__ __forceinline__ void axpy_neg(float fh, float fl, float vh, float vl,
   fast_two_sum(s, err, mh, ml);
 }
 
+// (h, l) = x - y
+__device__ __forceinline__ void sub(float xh, float xl, float yh, float yl, float& h, float& l) {
+  float s, e;
+  two_sum(xh, -yh, s, e);
+  e += xl - yl;
+  fast_two_sum(s, e, h, l);
+}
+
+// (h, l) = sqrt(x) for x >= 0: the FP32 root s, then one Newton correction
+// s + (x - s^2) / (2 s) with s^2 formed exactly (TwoProduct); about 2^-46
+// relative (Karp and Markstein's form of the correction).
+__device__ __forceinline__ void sqrt_df(float xh, float xl, float& h, float& l) {
+  if (!(xh > 0.f)) { h = 0.f; l = 0.f; return; }
+  const float s = sqrtf(xh);
+  const float p = s * s;
+  const float e = fmaf(s, s, -p);
+  const float r = ((xh - p) - e) + xl;
+  fast_two_sum(s, r * (0.5f / s), h, l);
+}
+
+// (h, l) = x / y (y != 0): the FP32 quotient q, then one correction with the
+// exact remainder x - q y (TwoProduct); about 2^-46 relative.
+__device__ __forceinline__ void div_df(float xh, float xl, float yh, float yl, float& h,
+                                       float& l) {
+  const float q = xh / yh;
+  const float p = q * yh;
+  const float e = fmaf(q, yh, -p);
+  const float r = (((xh - p) - e) + xl) - q * yl;
+  fast_two_sum(q, r / yh, h, l);
+}
+
 // DF sum over a warp (xor butterfly): every lane ends with the total
 __device__ __forceinline__ void warp_sum(float& h, float& l) {
 #pragma unroll

@@ -156,6 +156,10 @@ void launch_jacobi(const int32_t* node_slot, int nnodes, const T* R, int c, T* W
 
 // The FP64-accurate SVD of k_jacobi_mp with its FP64 phases in double-float
 // (HM_A32): same outputs, ~2^-46 relative accuracy.
+// A TSQR round of an FP64 panel in double-float arithmetic (HM_A32): the row
+// blocks (merge = 0) or the pairwise merges of the R factors (merge = 1).
+void launch_tsqr_df(const TsqrTask* tasks, int ntasks, int merge, const double* P, int64_t ldp,
+                    int c, double* R, cudaStream_t st);
 void launch_jacobi_df(const int32_t* node_slot, int nnodes, const double* R, int c, double* W,
                       double* sigma, cudaStream_t st);
 

@@ -547,6 +547,219 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
     sigma[(int64_t)node * c + j] = sv[order[j]] > 0.0 ? ldexp(sv[order[j]], ex) : 0.0;
 }
 
+
+// Householder QR of one row block of a panel (the first TSQR round, <= 128 rows,
+// FP64 data) in double-float: the steps of k_tsqr with every operation (the
+// norms, the reflector's scalars, the dot products and updates of the trailing
+// columns) carried by float pairs on the FP32 pipe.  v^T v is formed as
+// 2 nrm (nrm + |x0|), the cancellation-free form of |x|^2 - x0^2 + v0^2.
+// Writes the c x c R (row-major, upper triangle) in FP64.
+__global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ tasks,
+                                                 const double* __restrict__ P, int64_t ldp,
+                                                 int c, double* __restrict__ R, int ldm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Mh = reinterpret_cast<float*>(smem_raw);  // column-major, ld = ldm, high parts
+  float* Ml = Mh + (size_t)ldm * c;                 // low parts
+  __shared__ float red_h[8], red_l[8];
+  __shared__ float sh_ah, sh_al, sh_bh, sh_bl;
+  const TsqrTask tk = tasks[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int m = 0;
+  for (int s = 0; s < tk.nsrc; ++s) {
+    if (tk.kind[s] == 0) {
+      const int rows = (int)(tk.r1[s] - tk.r0[s]);
+      for (int idx = tid; idx < rows * c; idx += 256) {
+        const int rr = idx % rows, col = idx / rows;
+        df::split(P[tk.r0[s] + rr + (int64_t)col * ldp], Mh[col * ldm + m + rr],
+                  Ml[col * ldm + m + rr]);
+      }
+      m += rows;
+    } else {
+      const double* Rs = R + (int64_t)tk.slot[s] * c * c;
+      for (int idx = tid; idx < c * c; idx += 256) {
+        const int rr = idx / c, col = idx % c;
+        df::split(Rs[rr * c + col], Mh[col * ldm + m + rr], Ml[col * ldm + m + rr]);
+      }
+      m += c;
+    }
+  }
+  __syncthreads();
+  const int steps = m < c ? m : c;
+  for (int j = 0; j < steps; ++j) {
+    float* mjh = Mh + j * ldm;
+    float* mjl = Ml + j * ldm;
+    float sh = 0.f, sl = 0.f;
+    for (int i = j + tid; i < m; i += 256) df::dot_acc(mjh[i], mjl[i], mjh[i], mjl[i], sh, sl);
+    df::warp_sum(sh, sl);
+    if (lane == 0) { red_h[warp] = sh; red_l[warp] = sl; }
+    __syncthreads();
+    if (tid == 0) {
+      // the reflector's scalars in double-float too (an FP64 square root or
+      // division is a long dependent chain on the FP64 pipe)
+      float th = red_h[0], tl = red_l[0];
+      for (int w = 1; w < 8; ++w) df::add_to(th, tl, red_h[w], red_l[w]);
+      const float xh = mjh[j], xl = mjl[j];
+      float nh, nl;
+      df::sqrt_df(th, tl, nh, nl);
+      const float ah = (xh > 0.f) ? -nh : nh, al = (xh > 0.f) ? -nl : nl;
+      float vh, vl, wh = nh, wl = nl, qh, ql;
+      df::sub(xh, xl, ah, al, vh, vl);                                 // v0 = x0 - alpha
+      df::add_to(wh, wl, fabsf(xh), xh < 0.f ? -xl : xl);               // nrm + |x0|
+      df::mul(nh, nl, wh, wl, qh, ql);                                  // v^T v / 2
+      sh_ah = ah;
+      sh_al = al;
+      if (qh > 0.f) {
+        df::div_df(1.f, 0.f, qh, ql, sh_bh, sh_bl);                     // beta = 2 / v^T v
+      } else {
+        sh_bh = 0.f;
+        sh_bl = 0.f;
+      }
+      mjh[j] = vh;
+      mjl[j] = vl;
+    }
+    __syncthreads();
+    const float bh = sh_bh, bl = sh_bl;
+    if (bh != 0.f) {
+      // one aligned 8-lane group per trailing column, 32 columns per round
+      for (int k0 = j + 1; k0 < c; k0 += 32) {
+        const int k = k0 + (tid >> 3), gl = tid & 7;
+        const bool on = k < c;
+        float* mkh = Mh + (on ? k : j) * ldm;
+        float* mkl = Ml + (on ? k : j) * ldm;
+        float dh = 0.f, dl = 0.f;
+        if (on) {
+#pragma unroll
+          for (int ii = 0; ii < 17; ++ii) {  // rows j .. m - 1, m <= 136
+            const int i = j + gl + 8 * ii;
+            if (i < m) df::dot_acc(mjh[i], mjl[i], mkh[i], mkl[i], dh, dl);
+          }
+        }
+        df::group8_sum(dh, dl);
+        if (on) {
+          float fh, fl;
+          df::fast_two_sum(dh, dl, dh, dl);
+          df::mul(bh, bl, dh, dl, fh, fl);
+#pragma unroll
+          for (int ii = 0; ii < 17; ++ii) {
+            const int i = j + gl + 8 * ii;
+            if (i < m) df::axpy_neg(fh, fl, mjh[i], mjl[i], mkh[i], mkl[i]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) { mjh[j] = sh_ah; mjl[j] = sh_al; }
+    __syncthreads();
+  }
+  double* Ro = R + (int64_t)tk.out_slot * c * c;
+  for (int idx = tid; idx < c * c; idx += 256) {
+    const int rr = idx / c, col = idx % c;
+    Ro[idx] = (rr <= col && rr < steps) ? df::join(Mh[col * ldm + rr], Ml[col * ldm + rr]) : 0.0;
+  }
+}
+
+// The merge of two c x c triangles R = qr([R1; R2]) of k_tsqr_merge (packed
+// triangles, the j-th reflector touching row j of R1 and rows 0..j of R2) in
+// double-float; FP64 in and out.
+__global__ __launch_bounds__(256) void k_tsqr_merge_df(const TsqrTask* __restrict__ tasks, int c,
+                                                       double* __restrict__ R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int pk = c * (c + 1) / 2;
+  float* Ah = reinterpret_cast<float*>(smem_raw);  // R1, packed upper
+  float* Al = Ah + pk;
+  float* Bh = Al + pk;                              // R2, packed upper
+  float* Bl = Bh + pk;
+  __shared__ float red_h[8], red_l[8];
+  __shared__ float sh_ah, sh_al, sh_bh, sh_bl, sh_vh, sh_vl;
+  const TsqrTask tk = tasks[blockIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* R1 = R + (int64_t)tk.slot[0] * c * c;
+  const double* R2 = R + (int64_t)tk.slot[1] * c * c;
+  for (int idx = tid; idx < c * c; idx += 256) {
+    const int rr = idx / c, col = idx % c;
+    if (rr <= col) {
+      const int o = col * (col + 1) / 2 + rr;
+      df::split(R1[idx], Ah[o], Al[o]);
+      df::split(R2[idx], Bh[o], Bl[o]);
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < c; ++j) {
+    const int oj = j * (j + 1) / 2;  // rows 0..j of column j of R2
+    float sh = 0.f, sl = 0.f;
+    for (int i = tid; i <= j; i += 256) df::dot_acc(Bh[oj + i], Bl[oj + i], Bh[oj + i], Bl[oj + i], sh, sl);
+    df::warp_sum(sh, sl);
+    if (lane == 0) { red_h[warp] = sh; red_l[warp] = sl; }
+    __syncthreads();
+    if (tid == 0) {
+      // the reflector's scalars in double-float (see k_tsqr_df)
+      float th = red_h[0], tl = red_l[0];
+      for (int w = 1; w < 8; ++w) df::add_to(th, tl, red_h[w], red_l[w]);
+      const float xh = Ah[oj + j], xl = Al[oj + j];
+      float sh2, sl2, nh, nl;
+      df::mul(xh, xl, xh, xl, sh2, sl2);
+      df::add_to(sh2, sl2, th, tl);                                     // x0^2 + tail
+      df::sqrt_df(sh2, sl2, nh, nl);
+      const float ah = (xh > 0.f) ? -nh : nh, al = (xh > 0.f) ? -nl : nl;
+      float vh, vl, wh = nh, wl = nl, qh, ql;
+      df::sub(xh, xl, ah, al, vh, vl);                                 // v0 = x0 - alpha
+      df::add_to(wh, wl, fabsf(xh), xh < 0.f ? -xl : xl);               // nrm + |x0|
+      df::mul(nh, nl, wh, wl, qh, ql);                                  // v^T v / 2
+      sh_ah = ah;
+      sh_al = al;
+      sh_vh = vh;
+      sh_vl = vl;
+      if (qh > 0.f) {
+        df::div_df(1.f, 0.f, qh, ql, sh_bh, sh_bl);                     // beta = 2 / v^T v
+      } else {
+        sh_bh = 0.f;
+        sh_bl = 0.f;
+      }
+    }
+    __syncthreads();
+    const float bh = sh_bh, bl = sh_bl, vh = sh_vh, vl = sh_vl;
+    if (bh != 0.f) {
+      // one aligned 8-lane group per trailing column, 32 columns per round
+      for (int k0 = j + 1; k0 < c; k0 += 32) {
+        const int k = k0 + (tid >> 3), gl = tid & 7;
+        const bool on = k < c;
+        const int kk = on ? k : j;
+        const int ok = kk * (kk + 1) / 2;
+        float dh = 0.f, dl = 0.f;
+        if (on) {
+#pragma unroll
+          for (int ii = 0; ii < 16; ++ii) {  // rows 0 .. j, j < c <= 128
+            const int i = gl + 8 * ii;
+            if (i <= j) df::dot_acc(Bh[oj + i], Bl[oj + i], Bh[ok + i], Bl[ok + i], dh, dl);
+          }
+        }
+        df::group8_sum(dh, dl);
+        if (on) {
+          // f = beta (dot + v0 A(j, k))
+          df::dot_acc(vh, vl, Ah[ok + j], Al[ok + j], dh, dl);
+          float fh, fl;
+          df::fast_two_sum(dh, dl, dh, dl);
+          df::mul(bh, bl, dh, dl, fh, fl);
+#pragma unroll
+          for (int ii = 0; ii < 16; ++ii) {
+            const int i = gl + 8 * ii;
+            if (i <= j) df::axpy_neg(fh, fl, Bh[oj + i], Bl[oj + i], Bh[ok + i], Bl[ok + i]);
+          }
+          if (gl == 0) df::axpy_neg(fh, fl, vh, vl, Ah[ok + j], Al[ok + j]);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && bh != 0.f) { Ah[oj + j] = sh_ah; Al[oj + j] = sh_al; }
+    __syncthreads();
+  }
+  double* Ro = R + (int64_t)tk.out_slot * c * c;
+  for (int idx = tid; idx < c * c; idx += 256) {
+    const int rr = idx / c, col = idx % c;
+    const int o = col * (col + 1) / 2 + rr;
+    Ro[idx] = (rr <= col) ? df::join(Ah[o], Al[o]) : 0.0;
+  }
+}
 }  // namespace
 
 void launch_jacobi_df(const int32_t* node_slot, int nnodes, const double* R, int c, double* W,
@@ -556,6 +769,23 @@ void launch_jacobi_df(const int32_t* node_slot, int nnodes, const double* R, int
   static std::atomic<uint32_t> done{0};
   raise_smem_limit((const void*)k_jacobi_df, done);
   k_jacobi_df<<<nnodes, 512, smem, st>>>(node_slot, R, c, W, sigma);
+}
+
+void launch_tsqr_df(const TsqrTask* tasks, int ntasks, int merge, const double* P, int64_t ldp,
+                    int c, double* R, cudaStream_t st) {
+  count_launches(1);
+  if (!merge) {
+    const int ldm = kTsqrRows + 8;
+    const size_t smem = (size_t)2 * ldm * c * sizeof(float);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_tsqr_df, done);
+    k_tsqr_df<<<ntasks, 256, smem, st>>>(tasks, P, ldp, c, R, ldm);
+  } else {
+    const size_t smem = (size_t)2 * c * (c + 1) * sizeof(float);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_tsqr_merge_df, done);
+    k_tsqr_merge_df<<<ntasks, 256, smem, st>>>(tasks, c, R);
+  }
 }
 
 }  // namespace hm
