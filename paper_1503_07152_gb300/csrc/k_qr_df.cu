@@ -71,15 +71,15 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
   float* Qh = reg1;   // C - F
   float* Ql = reg2;
   __shared__ int rotated, large;
-  __shared__ double sv[128], cn[128], hb[128];
+  __shared__ double sv[128], hb[128];
   __shared__ float cnh[128], cnl[128], hbh[128], hbl[128];
   __shared__ float psh[4][128], psl[4][128];
   __shared__ int perm[128], order[128];
   __shared__ signed char sgn[128];
   __shared__ double red_v[16];
   __shared__ int red_i[16];
-  __shared__ double sh_alpha;
-  __shared__ float sh_sh, sh_sl;
+  __shared__ float pnh[128], pnl[128], ph0[128];  // A: pivoting norms
+  __shared__ float sh_ah, sh_al, sh_sh, sh_sl;
   __shared__ int sh_exp;
   const int node = blockIdx.x;
   const double* Rs = R + (int64_t)node_slot[node] * cc;
@@ -111,33 +111,39 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
   }
   for (int j = tid; j < c; j += nthr) perm[j] = j;
   __syncthreads();
+  // Squared column norms for the pivoting, kept as double-float pairs (pnh, pnl)
+  // and downdated per step; ph0 holds the value at the last exact recompute.
+  // Every scalar of this phase is double-float: a dependent chain of FP64
+  // instructions (a square root, a division) is very long on GB300's FP64 pipe.
   for (int k = warp; k < c; k += nwarps) {
     float sh = 0.f, sl = 0.f;
     for (int i = lane; i < c; i += 32) df::dot_acc(Mh[k * c + i], Ml[k * c + i], Mh[k * c + i], Ml[k * c + i], sh, sl);
     df::warp_sum(sh, sl);
-    if (lane == 0) { cn[k] = df::join(sh, sl); hb[k] = cn[k]; }
+    if (lane == 0) { df::fast_two_sum(sh, sl, pnh[k], pnl[k]); ph0[k] = pnh[k]; }
   }
   __syncthreads();
   for (int j = 0; j < c; ++j) {
+    // recompute the norms that downdating has left with few correct digits
     for (int k = j + warp; k < c; k += nwarps) {
-      if (!(cn[k] > 1.4901161193847656e-08 * hb[k])) {
+      if (!(pnh[k] > 5.9604644775390625e-08f * ph0[k])) {
         float sh = 0.f, sl = 0.f;
         for (int i = j + lane; i < c; i += 32)
           df::dot_acc(Mh[k * c + i], Ml[k * c + i], Mh[k * c + i], Ml[k * c + i], sh, sl);
         df::warp_sum(sh, sl);
-        if (lane == 0) { cn[k] = df::join(sh, sl); hb[k] = cn[k]; }
+        if (lane == 0) { df::fast_two_sum(sh, sl, pnh[k], pnl[k]); ph0[k] = pnh[k]; }
       }
     }
     __syncthreads();
-    if (warp == 0) {
-      double best = -1.0;
+    if (warp == 0) {  // the largest remaining norm, the first on ties
+      float bh = -1.f, bl = 0.f;
       int bi = c;
       for (int k = j + lane; k < c; k += 32)
-        if (cn[k] > best) { best = cn[k]; bi = k; }
+        if (pnh[k] > bh || (pnh[k] == bh && pnl[k] > bl)) { bh = pnh[k]; bl = pnl[k]; bi = k; }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const float oh = __shfl_xor_sync(0xffffffffu, bh, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, bl, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        if (oh > bh || (oh == bh && (ol > bl || (ol == bl && oi < bi)))) { bh = oh; bl = ol; bi = oi; }
       }
       if (lane == 0) red_i[0] = bi;
     }
@@ -150,8 +156,9 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
       }
       if (tid == 0) {
         const int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
-        double u = cn[j]; cn[j] = cn[p]; cn[p] = u;
-        u = hb[j]; hb[j] = hb[p]; hb[p] = u;
+        float u = pnh[j]; pnh[j] = pnh[p]; pnh[p] = u;
+        u = pnl[j]; pnl[j] = pnl[p]; pnl[p] = u;
+        u = ph0[j]; ph0[j] = ph0[p]; ph0[p] = u;
       }
     }
     __syncthreads();
@@ -161,20 +168,27 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
       float sh = 0.f, sl = 0.f;
       for (int i = j + lane; i < c; i += 32) df::dot_acc(mjh[i], mjl[i], mjh[i], mjl[i], sh, sl);
       df::warp_sum(sh, sl);
-      if (lane == 0) red_v[0] = df::join(sh, sl);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      const double tot = red_v[0] > 0.0 ? red_v[0] : 0.0;
-      const double x0 = df::join(mjh[j], mjl[j]);
-      const double nrm = sqrt(tot);
-      const double alpha = (x0 > 0.0) ? -nrm : nrm;
-      const double v0 = x0 - alpha;
-      const double vtv = 2.0 * nrm * (nrm + fabs(x0));
-      const double sc = (vtv > 0.0) ? sqrt(2.0 / vtv) : 0.0;
-      sh_alpha = alpha;
-      df::split(sc, sh_sh, sh_sl);
-      df::split(v0 * sc, mjh[j], mjl[j]);
+      if (lane == 0) {
+        // x0 and the reflector scale sqrt(2 / v^T v), v^T v = 2 nrm (nrm + |x0|)
+        const float xh = mjh[j], xl = mjl[j];
+        float nh, nl;
+        df::sqrt_df(sh, sl, nh, nl);
+        const float ah = (xh > 0.f) ? -nh : nh, al = (xh > 0.f) ? -nl : nl;
+        float vh, vl, wh = nh, wl = nl, qh, ql, sch = 0.f, scl = 0.f;
+        df::sub(xh, xl, ah, al, vh, vl);                        // v0 = x0 - alpha
+        df::add_to(wh, wl, fabsf(xh), xh < 0.f ? -xl : xl);      // nrm + |x0|
+        df::mul(nh, nl, wh, wl, qh, ql);                         // v^T v / 2
+        if (qh > 0.f) {
+          float ih, il;
+          df::div_df(1.f, 0.f, qh, ql, ih, il);
+          df::sqrt_df(ih, il, sch, scl);
+        }
+        sh_ah = ah;
+        sh_al = al;
+        sh_sh = sch;
+        sh_sl = scl;
+        df::mul(vh, vl, sch, scl, mjh[j], mjl[j]);
+      }
     }
     __syncthreads();
     const float sch = sh_sh, scl = sh_sl;
@@ -207,10 +221,11 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
       }
     }
     __syncthreads();
-    if (tid == 0 && sch != 0.f) df::split(sh_alpha, mjh[j], mjl[j]);
-    for (int k = j + 1 + tid; k < c; k += nthr) {
-      const double r = df::join(Mh[k * c + j], Ml[k * c + j]);
-      cn[k] -= r * r;
+    if (tid == 0 && sch != 0.f) { mjh[j] = sh_ah; mjl[j] = sh_al; }
+    for (int k = j + 1 + tid; k < c; k += nthr) {  // downdate: |col k|^2 -= R(j, k)^2
+      float rh, rl;
+      df::mul(Mh[k * c + j], Ml[k * c + j], Mh[k * c + j], Ml[k * c + j], rh, rl);
+      df::sub(pnh[k], pnl[k], rh, rl, pnh[k], pnl[k]);
     }
     __syncthreads();
   }
@@ -451,13 +466,21 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
               cl = t2 * fmaf(t2, 0.375f, -0.5f);            // cos - 1 = -t^2/2 + 3t^4/8
               sh = t;
               sl = t * cl;                                  // sin = t cos
-            } else {
-              const double zeta = ((double)be - (double)al + ((double)cnl[q] - (double)cnl[p])) /
-                                  (2.0 * df::join(gh, glo));
-              const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-              const double cd = 1.0 / sqrt(1.0 + t * t);
-              df::split(cd, ch, cl);
-              df::split(cd * t, sh, sl);
+            } else {  // |zeta| <= 2^10 here: zeta^2 stays in float range
+              float zh, zl, th, tl, uh, ul;
+              df::sub(be, cnl[q], al, cnl[p], uh, ul);             // |a_q|^2 - |a_p|^2
+              df::div_df(uh, ul, 2.f * gh, 2.f * glo, zh, zl);     // zeta
+              df::mul(zh, zl, zh, zl, th, tl);
+              df::add_to(th, tl, 1.f, 0.f);
+              df::sqrt_df(th, tl, uh, ul);                         // sqrt(1 + zeta^2)
+              df::add_to(uh, ul, fabsf(zh), zh < 0.f ? -zl : zl);
+              df::div_df(zh >= 0.f ? 1.f : -1.f, 0.f, uh, ul, th, tl);  // t = tan(theta)
+              df::mul(th, tl, th, tl, uh, ul);
+              df::add_to(uh, ul, 1.f, 0.f);
+              float rh, rl;
+              df::sqrt_df(uh, ul, rh, rl);
+              df::div_df(1.f, 0.f, rh, rl, ch, cl);               // cos = 1 / sqrt(1 + t^2)
+              df::mul(ch, cl, th, tl, sh, sl);                     // sin = t cos
             }
 #pragma unroll
             for (int ii = 0; ii < 16; ++ii) {
