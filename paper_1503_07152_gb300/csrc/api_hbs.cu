@@ -39,7 +39,7 @@ struct Items {
     it.ta = ta; it.tb = tb;
     v.push_back(it);
   }
-  hm_status run(GemmItem* dev, size_t cap, T alpha, T beta, cudaStream_t st) {
+  hm_status run(GemmItem* dev, size_t cap, T alpha, T beta, cudaStream_t st, bool df = false) {
     if (v.empty()) return HM_OK;
     if (v.size() > cap) {
       set_error("internal: too many batched GEMM items");
@@ -53,7 +53,7 @@ struct Items {
       max_n = std::max(max_n, (int)g.n);
       max_k = std::max(max_k, (int)g.k);
     }
-    launch_batched_gemm<T>(dev, (int)v.size(), alpha, beta, st, max_m, max_n, max_k);
+    launch_batched_gemm<T>(dev, (int)v.size(), alpha, beta, st, max_m, max_n, max_k, df);
     v.clear();
     // the pageable source was staged by the copy call; the next batch may reuse dev only
     // after this launch has read it, which stream order guarantees
@@ -105,11 +105,11 @@ hm_status hbs_partial_apply(HbsState<T>& s, int m, const T* X, int64_t ldx, T* S
     for (int lev = m - 1; lev >= 1; --lev) {
       for (int tau = 1 << lev; tau < (2 << lev); ++tau)
         it.add(Sout + (2 * tau) * rr, r, 1, qh + (2 * tau) * rw, r, 0, qh + tau * rw, r, r, w, r);
-      HM_TRY(it.run(s.items, s.items_cap, (T)1, (T)0, st));
+      HM_TRY(it.run(s.items, s.items_cap, (T)1, (T)0, st, s.df));
       for (int tau = 1 << lev; tau < (2 << lev); ++tau)
         it.add(Sout + (2 * tau + 1) * rr, r, 1, qh + (2 * tau + 1) * rw, r, 0, qh + tau * rw, r, r,
                w, r);
-      HM_TRY(it.run(s.items, s.items_cap, (T)1, (T)1, st));
+      HM_TRY(it.run(s.items, s.items_cap, (T)1, (T)1, st, s.df));
     }
     // incoming expansions of the root's children and the downward pass
     for (int lev = 1; lev <= m; ++lev) {
@@ -117,11 +117,11 @@ hm_status hbs_partial_apply(HbsState<T>& s, int m, const T* X, int64_t ldx, T* S
         if (!trans) it.add(s.Bm + a * rr, r, 0, qh + (a ^ 1) * rw, r, 0, uh + a * rw, r, r, w, r);
         else it.add(s.Bm + (a ^ 1) * rr, r, 1, qh + (a ^ 1) * rw, r, 0, uh + a * rw, r, r, w, r);
       }
-      HM_TRY(it.run(s.items, s.items_cap, (T)1, (T)0, st));
+      HM_TRY(it.run(s.items, s.items_cap, (T)1, (T)0, st, s.df));
       if (lev >= 2) {
         for (int a = 1 << lev; a < (2 << lev); ++a)
           it.add(Sin + a * rr, r, 0, uh + (a >> 1) * rw, r, 0, uh + a * rw, r, r, w, r);
-        HM_TRY(it.run(s.items, s.items_cap, (T)1, (T)1, st));
+        HM_TRY(it.run(s.items, s.items_cap, (T)1, (T)1, st, s.df));
       }
     }
     launch_seg_nn<T>(pm.d_nn, pm.n_nn, pm.node0, Uin, s.N, 0, 0, r, uh + pm.node0 * rw, rw, r, 0,
@@ -304,7 +304,7 @@ hm_status hbsid_sweep(Ctx<T>& c, HbsState<T>& s, const T* D, hm_handle* h) {
         it.add(Samp + (2 * t) * rr, r, 0, Sh + (2 * t) * rr, r, 0, Ut, 2 * r, r, r, r);
         it.add(Samp + (2 * t + 1) * rr, r, 0, Sh + (2 * t + 1) * rr, r, 0, Ut + r, 2 * r, r, r, r);
       }
-      HM_TRY(it.run((GemmItem*)s.items, s.items_cap, 1.0, 0.0, st));
+      HM_TRY(it.run((GemmItem*)s.items, s.items_cap, 1.0, 0.0, st, s.df));
       launch_id_prep_parent<T>(nn, n0, Utmp, w, r, Yt, st);
       launch_pivqr_id(nn, Yt, r, 2 * r, eps, kcap, kk, J, Tid, st);
       launch_usamp_parent(nn, n0, Utmp, J, r, Samp, skel, st);
@@ -322,11 +322,11 @@ hm_status hbsid_sweep(Ctx<T>& c, HbsState<T>& s, const T* D, hm_handle* h) {
     // tmp = Usamp_a B_ab for the level, then Bsk = tmp Vsamp_b^T
     for (int x = n0; x < 2 * n0; ++x)
       it.add(Us + x * rr, r, 0, Bm + x * rr, r, 0, tmp + (int64_t)(x - n0) * rr, r, r, r, r);
-    HM_TRY(it.run((GemmItem*)s.items, s.items_cap, 1.0, 0.0, st));
+    HM_TRY(it.run((GemmItem*)s.items, s.items_cap, 1.0, 0.0, st, s.df));
     for (int x = n0; x < 2 * n0; ++x)
       it.add(tmp + (int64_t)(x - n0) * rr, r, 0, Vs + (x ^ 1) * rr, r, 1, Tid + (int64_t)(x - n0) * rr,
              r, r, r, r);
-    HM_TRY(it.run((GemmItem*)s.items, s.items_cap, 1.0, 0.0, st));
+    HM_TRY(it.run((GemmItem*)s.items, s.items_cap, 1.0, 0.0, st, s.df));
     launch_node_copy<double, T>(n0, n0, Tid, rr, r, store_in + lay.bsk, rr, r, r, r, 0, st);
   }
   cudaMemcpyAsync(store_in + lay.d, D, sizeof(T) * (size_t)nleaf * nmax * nmax,

@@ -21,9 +21,10 @@ void launch_gather_parent_scaled(const T* U, int64_t ldu, T* P, int64_t ldp, int
                                  cudaStream_t st);
 template <typename T>
 // max_m, max_n, max_k: the largest m, n and k of the items (the tiled form is used
-// when its staging fits, else the plain one; the results are the same)
+// when its staging fits, else the plain one; the results are the same).  df: FP64
+// items in double-float on the FP32 pipe (HM_A32).
 void launch_batched_gemm(const GemmItem* items, int count, T alpha, T beta, cudaStream_t st,
-                         int max_m, int max_n, int max_k);
+                         int max_m, int max_n, int max_k, bool df = false);
 template <typename TS, typename TD>
 void launch_node_copy(int nnodes, int node0, const TS* src, int64_t sstride, int sld, TD* dst,
                       int64_t dstride, int dld, int rows, int cols, int flip, cudaStream_t st);

@@ -10,6 +10,7 @@
 //    T = R11^{-1} [R11 R12] in FP64, one block per node.
 #include <atomic>
 
+#include "df.cuh"
 #include "hm_internal.h"
 #include "hm_hbs.h"
 
@@ -107,6 +108,58 @@ __global__ __launch_bounds__(256) void k_batched_gemm_tiled(const GemmItem* __re
       if (i < m) {
         T* c = Cm + i + (int64_t)col * it.ldc;
         *c = (beta == (T)0) ? alpha * acc[q] : alpha * acc[q] + beta * (*c);
+      }
+    }
+  }
+}
+
+// The FP64 form of k_batched_gemm_tiled in double-float on the FP32 pipe
+// (HM_A32): every input cut once, when staged, into hi + lo floats; each output
+// summed as a float pair (TwoProduct of the high parts, the cross terms, TwoSum).
+__global__ __launch_bounds__(256) void k_batched_gemm_tiled_df(const GemmItem* __restrict__ items,
+                                                               double alpha, double beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const GemmItem it = items[blockIdx.x];
+  const int m = it.m, n = it.n, k = it.k;
+  const int j0 = blockIdx.y * 32, m0 = blockIdx.z * 32;
+  if (j0 >= n || m0 >= m) return;  // uniform over the block
+  const double* A = (const double*)it.A;
+  const double* B = (const double*)it.B;
+  double* Cm = (double*)it.C;
+  float* Ah = reinterpret_cast<float*>(smem_raw);  // [32][k]: rows m0 .. m0 + 31 of op(A)
+  float* Al = Ah + 32 * k;
+  float* Bh = Al + 32 * k;                         // [k][32]: columns j0 .. j0 + 31 of op(B)
+  float* Bl = Bh + 32 * k;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 32 * k; e += 256) {
+    const int ii = e / k, p = e % k, i = m0 + ii;
+    const double v = (i < m) ? (it.ta ? A[p + (int64_t)i * it.lda] : A[i + (int64_t)p * it.lda]) : 0.0;
+    df::split(v, Ah[e], Al[e]);
+  }
+  for (int e = tid; e < k * 32; e += 256) {
+    const int p = e >> 5, col = j0 + (e & 31);
+    const double v = (col < n) ? (it.tb ? B[col + (int64_t)p * it.ldb] : B[p + (int64_t)col * it.ldb])
+                               : 0.0;
+    df::split(v, Bh[e], Bl[e]);
+  }
+  __syncthreads();
+  const int j = tid & 31, i0 = tid >> 5;
+  float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int p = 0; p < k; ++p) {
+    const float bh = Bh[p * 32 + j], bl = Bl[p * 32 + j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      df::dot_acc(Ah[(i0 + 8 * q) * k + p], Al[(i0 + 8 * q) * k + p], bh, bl, sh[q], sl[q]);
+  }
+  const int col = j0 + j;
+  if (col < n) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = m0 + i0 + 8 * q;
+      if (i < m) {
+        double* c = Cm + i + (int64_t)col * it.ldc;
+        const double a = df::join(sh[q], sl[q]);
+        *c = (beta == 0.0) ? alpha * a : alpha * a + beta * (*c);
       }
     }
   }
@@ -326,12 +379,18 @@ void launch_gather_parent_scaled(const T* U, int64_t ldu, T* P, int64_t ldp, int
 
 template <typename T>
 void launch_batched_gemm(const GemmItem* items, int count, T alpha, T beta, cudaStream_t st,
-                         int max_m, int max_n, int max_k) {
+                         int max_m, int max_n, int max_k, bool df) {
   if (count <= 0) return;
   count_launches(1);
   const size_t smem = (size_t)64 * max_k * sizeof(T);
   if (max_m >= 1 && max_n >= 1 && max_k >= 1 && smem <= 96 * 1024 && max_n <= 32 * 65535 &&
-      max_m <= 32 * 65535) {
+      max_m <= 32 * 65535 && sizeof(T) == 8 && df) {
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_batched_gemm_tiled_df, done);
+    dim3 grid((unsigned)count, (unsigned)((max_n + 31) / 32), (unsigned)((max_m + 31) / 32));
+    k_batched_gemm_tiled_df<<<grid, 256, smem, st>>>(items, (double)alpha, (double)beta);
+  } else if (max_m >= 1 && max_n >= 1 && max_k >= 1 && smem <= 96 * 1024 &&
+             max_n <= 32 * 65535 && max_m <= 32 * 65535) {
     static std::atomic<uint32_t> done{0};
     raise_smem_limit((const void*)k_batched_gemm_tiled<T>, done);
     dim3 grid((unsigned)count, (unsigned)((max_n + 31) / 32), (unsigned)((max_m + 31) / 32));
@@ -390,7 +449,8 @@ void launch_usamp_parent(int nnodes, int node0, const double* Utmp, const int32_
   template void launch_gather_parent_scaled<T>(const T*, int64_t, T*, int64_t, int64_t, int,   \
                                                int, const int64_t*, const T*, int,             \
                                                cudaStream_t);                                  \
-  template void launch_batched_gemm<T>(const GemmItem*, int, T, T, cudaStream_t, int, int, int);              \
+  template void launch_batched_gemm<T>(const GemmItem*, int, T, T, cudaStream_t, int, int, int, \
+                                       bool);              \
   template void launch_id_prep_leaf<T>(const T*, int64_t, const int64_t*, const int64_t*, int, \
                                        const T*, int, double*, int, cudaStream_t);             \
   template void launch_id_prep_parent<T>(int, int, const double*, const T*, int, double*,      \
