@@ -289,7 +289,7 @@ hm_status hbsid_sweep(Ctx<T>& c, HbsState<T>& s, const T* D, hm_handle* h) {
     auto& kall = side == 0 ? kin_all : kout_all;
     // leaves
     launch_id_prep_leaf<T>(Bl, N, c.tree->d_start, c.tree->d_size, L, w, r, Yt, nmax, st);
-    launch_pivqr_id(nleaf, Yt, r, nmax, eps, kcap, kk, J, Tid, st);
+    launch_pivqr_id(nleaf, Yt, r, nmax, eps, kcap, kk, J, Tid, st, s.df);
     launch_usamp_leaf<T>(Bl, N, c.tree->d_start, L, J, r, Samp, skel, st);
     launch_node_copy<double, T>(nleaf, 0, Tid, (int64_t)r * nmax, r, store + lay.tin_leaf,
                                 (int64_t)r * nmax, r, r, nmax, 0, st);
@@ -306,7 +306,7 @@ hm_status hbsid_sweep(Ctx<T>& c, HbsState<T>& s, const T* D, hm_handle* h) {
       }
       HM_TRY(it.run((GemmItem*)s.items, s.items_cap, 1.0, 0.0, st, s.df));
       launch_id_prep_parent<T>(nn, n0, Utmp, w, r, Yt, st);
-      launch_pivqr_id(nn, Yt, r, 2 * r, eps, kcap, kk, J, Tid, st);
+      launch_pivqr_id(nn, Yt, r, 2 * r, eps, kcap, kk, J, Tid, st, s.df);
       launch_usamp_parent(nn, n0, Utmp, J, r, Samp, skel, st);
       launch_node_copy<double, T>(nn, 0, Tid, (int64_t)r * 2 * r, r,
                                   store + lay.tin_par + (int64_t)(n0 - 1) * 2 * rr, 2 * rr, r, r,

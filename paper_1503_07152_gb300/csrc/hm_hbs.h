@@ -34,8 +34,9 @@ void launch_id_prep_leaf(const T* U, int64_t ldu, const int64_t* d_start, const 
 template <typename T>
 void launch_id_prep_parent(int nnodes, int node0, const double* Utmp, const T* y, int r,
                            double* Yt, cudaStream_t st);
+// df: the pivoted QR and the substitution in double-float (HM_A32)
 void launch_pivqr_id(int nnodes, const double* Yt, int r, int nc, double eps, int kcap,
-                     int32_t* k, int32_t* J, double* T, cudaStream_t st);
+                     int32_t* k, int32_t* J, double* T, cudaStream_t st, bool df = false);
 template <typename T>
 void launch_usamp_leaf(const T* U, int64_t ldu, const int64_t* d_start, int L, const int32_t* J,
                        int r, double* Us, int64_t* skel, cudaStream_t st);

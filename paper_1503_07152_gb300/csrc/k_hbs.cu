@@ -327,6 +327,148 @@ __global__ __launch_bounds__(256) void k_pivqr_id(const double* __restrict__ Yt,
   if (tid == 0) kout[blockIdx.x] = k;
 }
 
+// k_pivqr_id in double-float (HM_A32): the same column-pivoted Householder QR
+// with the exact pivot rule (norms recomputed each step, the largest first,
+// the first index on ties) and T = R11^{-1} R12 by back substitution, with every
+// operation carried by float pairs on the FP32 pipe (FP64 in and out).  The
+// columns of R12 are overwritten by T in place during the substitution.
+__global__ __launch_bounds__(256) void k_pivqr_id_df(const double* __restrict__ Yt, int r, int nc,
+                                                     double eps, int kcap,
+                                                     int32_t* __restrict__ kout,
+                                                     int32_t* __restrict__ Jout,
+                                                     double* __restrict__ Tout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Mh = reinterpret_cast<float*>(smem_raw);  // r x nc, column-major
+  float* Ml = Mh + (size_t)r * nc;
+  float* nh = Ml + (size_t)r * nc;                 // nc: squared norms (pairs)
+  float* nl = nh + nc;
+  int* perm = reinterpret_cast<int*>(nl + nc);     // nc
+  __shared__ float redh[8], redl[8], sh_a[2], sh_b[2];
+  __shared__ int redi[8];
+  __shared__ int sk;
+  const double* Y = Yt + (int64_t)blockIdx.x * r * nc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < r * nc; e += blockDim.x) df::split(Y[e], Mh[e], Ml[e]);
+  for (int j = tid; j < nc; j += blockDim.x) perm[j] = j;
+  // eps^2 as a pair, for the rank test |col|^2 > eps^2
+  float e2h, e2l;
+  df::split(eps * eps, e2h, e2l);
+  __syncthreads();
+  const int steps = min(r, nc);
+  int k = 0;
+  for (int j = 0; j < steps; ++j) {
+    for (int c = j + warp; c < nc; c += 8) {
+      float s = 0.f, t = 0.f;
+      for (int i = j + lane; i < r; i += 32)
+        df::dot_acc(Mh[i + c * r], Ml[i + c * r], Mh[i + c * r], Ml[i + c * r], s, t);
+      df::warp_sum(s, t);
+      if (lane == 0) df::fast_two_sum(s, t, nh[c], nl[c]);
+    }
+    __syncthreads();
+    float bh = -1.f, bl = 0.f;
+    int bi = nc;
+    for (int c = j + tid; c < nc; c += blockDim.x)
+      if (nh[c] > bh || (nh[c] == bh && nl[c] > bl)) { bh = nh[c]; bl = nl[c]; bi = c; }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, bh, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oh > bh || (oh == bh && (ol > bl || (ol == bl && oi < bi)))) { bh = oh; bl = ol; bi = oi; }
+    }
+    if (lane == 0) { redh[warp] = bh; redl[warp] = bl; redi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      float b = redh[0], bb = redl[0];
+      int i0 = redi[0];
+      for (int w = 1; w < 8; ++w)
+        if (redh[w] > b || (redh[w] == b && (redl[w] > bb || (redl[w] == bb && redi[w] < i0)))) {
+          b = redh[w]; bb = redl[w]; i0 = redi[w];
+        }
+      const bool above = b > e2h || (b == e2h && bb > e2l);
+      sk = (above && j < kcap) ? i0 : -1;
+    }
+    __syncthreads();
+    const int p = sk;
+    if (p < 0) break;
+    if (p != j) {
+      for (int i = tid; i < r; i += blockDim.x) {
+        float t = Mh[i + j * r]; Mh[i + j * r] = Mh[i + p * r]; Mh[i + p * r] = t;
+        t = Ml[i + j * r]; Ml[i + j * r] = Ml[i + p * r]; Ml[i + p * r] = t;
+      }
+      if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+    }
+    __syncthreads();
+    // Householder on column j (rows j..r-1)
+    if (warp == 0) {
+      float s = 0.f, t = 0.f;
+      for (int i = j + lane; i < r; i += 32)
+        df::dot_acc(Mh[i + j * r], Ml[i + j * r], Mh[i + j * r], Ml[i + j * r], s, t);
+      df::warp_sum(s, t);
+      if (lane == 0) {
+        const float xh = Mh[j + j * r], xl = Ml[j + j * r];
+        float nxh, nxl;
+        df::sqrt_df(s, t, nxh, nxl);
+        const float ah = (xh > 0.f) ? -nxh : nxh, al = (xh > 0.f) ? -nxl : nxl;
+        float vh, vl, wh = nxh, wl = nxl, qh, ql;
+        df::sub(xh, xl, ah, al, vh, vl);                    // v0 = x0 - alpha
+        df::add_to(wh, wl, fabsf(xh), xh < 0.f ? -xl : xl);  // nrm + |x0|
+        df::mul(nxh, nxl, wh, wl, qh, ql);                   // v^T v / 2
+        sh_a[0] = ah;
+        sh_a[1] = al;
+        if (qh > 0.f) {
+          df::div_df(1.f, 0.f, qh, ql, sh_b[0], sh_b[1]);   // beta = 2 / v^T v
+        } else {
+          sh_b[0] = 0.f;
+          sh_b[1] = 0.f;
+        }
+        Mh[j + j * r] = vh;
+        Ml[j + j * r] = vl;
+      }
+    }
+    __syncthreads();
+    const float beh = sh_b[0], bel = sh_b[1];
+    for (int c = j + 1 + warp; c < nc; c += 8) {
+      float dh = 0.f, dl = 0.f;
+      for (int i = j + lane; i < r; i += 32)
+        df::dot_acc(Mh[i + j * r], Ml[i + j * r], Mh[i + c * r], Ml[i + c * r], dh, dl);
+      df::warp_sum(dh, dl);
+      float fh, fl;
+      df::mul(dh, dl, beh, bel, fh, fl);
+      for (int i = j + lane; i < r; i += 32)
+        df::axpy_neg(fh, fl, Mh[i + j * r], Ml[i + j * r], Mh[i + c * r], Ml[i + c * r]);
+    }
+    __syncthreads();
+    if (tid == 0) { Mh[j + j * r] = sh_a[0]; Ml[j + j * r] = sh_a[1]; }
+    for (int i = j + 1 + tid; i < r; i += blockDim.x) { Mh[i + j * r] = 0.f; Ml[i + j * r] = 0.f; }
+    __syncthreads();
+    k = j + 1;
+  }
+  // inverse diagonal of R11, then T(:, perm) = [I, R11^{-1} R12] column by column
+  // (back substitution; column c's T overwrites its R12 entries as they are used)
+  for (int i = tid; i < k; i += blockDim.x) df::div_df(1.f, 0.f, Mh[i + i * r], Ml[i + i * r], nh[i], nl[i]);
+  __syncthreads();
+  double* T = Tout + (int64_t)blockIdx.x * r * nc;
+  for (int e = tid; e < r * nc; e += blockDim.x) T[e] = 0.0;
+  __syncthreads();
+  for (int c = tid; c < nc; c += blockDim.x) {
+    const int oc = perm[c];
+    if (c < k) {
+      T[c + (int64_t)oc * r] = 1.0;
+    } else {
+      for (int i = k - 1; i >= 0; --i) {
+        float sh = Mh[i + c * r], sl = Ml[i + c * r];
+        for (int q = i + 1; q < k; ++q)
+          df::axpy_neg(Mh[q + c * r], Ml[q + c * r], Mh[i + q * r], Ml[i + q * r], sh, sl);
+        df::mul(sh, sl, nh[i], nl[i], Mh[i + c * r], Ml[i + c * r]);
+      }
+      for (int i = 0; i < k; ++i) T[i + (int64_t)oc * r] = df::join(Mh[i + c * r], Ml[i + c * r]);
+    }
+  }
+  int32_t* J = Jout + (int64_t)blockIdx.x * r;
+  for (int a = tid; a < r; a += blockDim.x) J[a] = (a < k) ? perm[a] : -1;
+  if (tid == 0) kout[blockIdx.x] = k;
+}
+
 // Usamp (r x r, row a = skeleton row a, zero rows past k) from a leaf basis.
 template <typename T>
 __global__ void k_usamp_leaf(const T* __restrict__ U, int64_t ldu, const int64_t* __restrict__ start,
@@ -424,9 +566,15 @@ void launch_id_prep_parent(int nnodes, int node0, const double* Utmp, const T* y
 }
 
 void launch_pivqr_id(int nnodes, const double* Yt, int r, int nc, double eps, int kcap,
-                     int32_t* k, int32_t* J, double* T, cudaStream_t st) {
+                     int32_t* k, int32_t* J, double* T, cudaStream_t st, bool df) {
   count_launches(1);
   const size_t smem = sizeof(double) * ((size_t)r * nc + nc) + sizeof(int) * nc;
+  if (df) {  // the same layout size: float pairs in place of doubles
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_pivqr_id_df, done);
+    k_pivqr_id_df<<<nnodes, 256, smem, st>>>(Yt, r, nc, eps, kcap, k, J, T);
+    return;
+  }
   static std::atomic<uint32_t> done{0};
   raise_smem_limit((const void*)k_pivqr_id, done);
   k_pivqr_id<<<nnodes, 256, smem, st>>>(Yt, r, nc, eps, kcap, k, J, T);

@@ -269,15 +269,19 @@ __global__ __launch_bounds__(256) void k_seg_nn(
 
 // The FP64 expansion in double-float arithmetic (HM_A32), as k_seg_tn_partial_df:
 // inputs cut to hi + lo floats when staged, products by TwoProduct, sums by TwoSum.
+// Warp w owns output columns [CJ w, CJ w + CJ) (CJ = 4, 8 or 16 as kout needs), so
+// only the columns that cover kout are staged and computed.
+template <int CJ>
 __global__ __launch_bounds__(256) void k_seg_nn_df(
     const Chunk* __restrict__ chunks, int node0, const double* P, int64_t ldp, int poff_e,
     int poff_o, int kin, const double* __restrict__ C, int64_t cstride, int cld, int cflip,
     double* Y, int64_t ldy, int yoff_e, int yoff_o, int kout, double alpha, double beta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int CW = 8 * CJ;                      // staged columns of C
   float* Ph = reinterpret_cast<float*>(smem_raw);  // [NN_MAX][NN_ROWS] each
   float* Pl = Ph + NN_MAX * NN_ROWS;
-  float* Ch = Pl + NN_MAX * NN_ROWS;              // [NN_MAX][NN_MAX] each
-  float* Cl = Ch + NN_MAX * NN_MAX;
+  float* Ch = Pl + NN_MAX * NN_ROWS;              // [NN_MAX][CW] each
+  float* Cl = Ch + NN_MAX * CW;
   const Chunk ch = chunks[blockIdx.x];
   const int rows = (int)(ch.r1 - ch.r0);
   const int poff = (ch.node & 1) ? poff_o : poff_e;
@@ -291,26 +295,26 @@ __global__ __launch_bounds__(256) void k_seg_nn_df(
     Ph[k * NN_ROWS + rr] = h;
     Pl[k * NN_ROWS + rr] = l;
   }
-  for (int idx = tid; idx < kin * NN_MAX; idx += 256) {
-    const int j = idx % NN_MAX, k = idx / NN_MAX;
+  for (int idx = tid; idx < kin * CW; idx += 256) {
+    const int j = idx % CW, k = idx / CW;
     float h, l;
     split_df((j < kout) ? Cn[k + (int64_t)j * cld] : 0.0, h, l);
-    Ch[k * NN_MAX + j] = h;
-    Cl[k * NN_MAX + j] = l;
+    Ch[k * CW + j] = h;
+    Cl[k * CW + j] = l;
   }
   __syncthreads();
   const int lane = tid & 31, w = tid >> 5;
-  float sh[2][16], sl[2][16];
+  float sh[2][CJ], sl[2][CJ];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
+    for (int j = 0; j < CJ; ++j) { sh[i][j] = 0.f; sl[i][j] = 0.f; }
   for (int k = 0; k < kin; ++k) {
     const float ah[2] = {Ph[k * NN_ROWS + lane], Ph[k * NN_ROWS + lane + 32]};
     const float al[2] = {Pl[k * NN_ROWS + lane], Pl[k * NN_ROWS + lane + 32]};
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float chj = Ch[k * NN_MAX + w * 16 + j], clj = Cl[k * NN_MAX + w * 16 + j];
+    for (int j = 0; j < CJ; ++j) {
+      const float chj = Ch[k * CW + w * CJ + j], clj = Cl[k * CW + w * CJ + j];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const float p = ah[i] * chj;
@@ -325,8 +329,8 @@ __global__ __launch_bounds__(256) void k_seg_nn_df(
     }
   }
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int col = w * 16 + j;
+  for (int j = 0; j < CJ; ++j) {
+    const int col = w * CJ + j;
     if (col >= kout) continue;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -416,12 +420,23 @@ void launch_seg_nn(const Chunk* chunks, int nchunks, int node0, const T* P, int6
   count_launches(1);
   const size_t smem = (size_t)(NN_MAX * NN_ROWS + NN_MAX * NN_MAX) * sizeof(T);
   if (sizeof(T) == 8 && df) {
-    static std::atomic<uint32_t> done{0};
-    raise_smem_limit((const void*)k_seg_nn_df, done);
-    k_seg_nn_df<<<nchunks, 256, smem, st>>>(chunks, node0, (const double*)P, ldp, poff_even,
-                                            poff_odd, kin, (const double*)C, cstride, cld, cflip,
-                                            (double*)Y, ldy, yoff_even, yoff_odd, kout,
-                                            (double)alpha, (double)beta);
+    auto run = [&](auto kern, int cw) {
+      const size_t sm = (size_t)2 * (NN_MAX * NN_ROWS + NN_MAX * cw) * sizeof(float);
+      kern<<<nchunks, 256, sm, st>>>(chunks, node0, (const double*)P, ldp, poff_even, poff_odd,
+                                     kin, (const double*)C, cstride, cld, cflip, (double*)Y, ldy,
+                                     yoff_even, yoff_odd, kout, (double)alpha, (double)beta);
+    };
+    static std::atomic<uint32_t> d4{0}, d8{0}, d16{0};
+    if (kout <= 32) {
+      raise_smem_limit((const void*)k_seg_nn_df<4>, d4);
+      run(k_seg_nn_df<4>, 32);
+    } else if (kout <= 64) {
+      raise_smem_limit((const void*)k_seg_nn_df<8>, d8);
+      run(k_seg_nn_df<8>, 64);
+    } else {
+      raise_smem_limit((const void*)k_seg_nn_df<16>, d16);
+      run(k_seg_nn_df<16>, 128);
+    }
     return;
   }
   static std::atomic<uint32_t> done{0};
