@@ -571,19 +571,21 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
 }
 
 
+constexpr int TQ_THREADS = 512;  // threads of the double-float TSQR kernels
+
 // Householder QR of one row block of a panel (the first TSQR round, <= 128 rows,
 // FP64 data) in double-float: the steps of k_tsqr with every operation (the
 // norms, the reflector's scalars, the dot products and updates of the trailing
 // columns) carried by float pairs on the FP32 pipe.  v^T v is formed as
 // 2 nrm (nrm + |x0|), the cancellation-free form of |x|^2 - x0^2 + v0^2.
 // Writes the c x c R (row-major, upper triangle) in FP64.
-__global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ tasks,
+__global__ __launch_bounds__(TQ_THREADS) void k_tsqr_df(const TsqrTask* __restrict__ tasks,
                                                  const double* __restrict__ P, int64_t ldp,
                                                  int c, double* __restrict__ R, int ldm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Mh = reinterpret_cast<float*>(smem_raw);  // column-major, ld = ldm, high parts
   float* Ml = Mh + (size_t)ldm * c;                 // low parts
-  __shared__ float red_h[8], red_l[8];
+  __shared__ float red_h[TQ_THREADS / 32], red_l[TQ_THREADS / 32];
   __shared__ float sh_ah, sh_al, sh_bh, sh_bl;
   const TsqrTask tk = tasks[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -591,7 +593,7 @@ __global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ ta
   for (int s = 0; s < tk.nsrc; ++s) {
     if (tk.kind[s] == 0) {
       const int rows = (int)(tk.r1[s] - tk.r0[s]);
-      for (int idx = tid; idx < rows * c; idx += 256) {
+      for (int idx = tid; idx < rows * c; idx += TQ_THREADS) {
         const int rr = idx % rows, col = idx / rows;
         df::split(P[tk.r0[s] + rr + (int64_t)col * ldp], Mh[col * ldm + m + rr],
                   Ml[col * ldm + m + rr]);
@@ -599,7 +601,7 @@ __global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ ta
       m += rows;
     } else {
       const double* Rs = R + (int64_t)tk.slot[s] * c * c;
-      for (int idx = tid; idx < c * c; idx += 256) {
+      for (int idx = tid; idx < c * c; idx += TQ_THREADS) {
         const int rr = idx / c, col = idx % c;
         df::split(Rs[rr * c + col], Mh[col * ldm + m + rr], Ml[col * ldm + m + rr]);
       }
@@ -612,7 +614,7 @@ __global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ ta
     float* mjh = Mh + j * ldm;
     float* mjl = Ml + j * ldm;
     float sh = 0.f, sl = 0.f;
-    for (int i = j + tid; i < m; i += 256) df::dot_acc(mjh[i], mjl[i], mjh[i], mjl[i], sh, sl);
+    for (int i = j + tid; i < m; i += TQ_THREADS) df::dot_acc(mjh[i], mjl[i], mjh[i], mjl[i], sh, sl);
     df::warp_sum(sh, sl);
     if (lane == 0) { red_h[warp] = sh; red_l[warp] = sl; }
     __syncthreads();
@@ -620,7 +622,7 @@ __global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ ta
       // the reflector's scalars in double-float too (an FP64 square root or
       // division is a long dependent chain on the FP64 pipe)
       float th = red_h[0], tl = red_l[0];
-      for (int w = 1; w < 8; ++w) df::add_to(th, tl, red_h[w], red_l[w]);
+      for (int w = 1; w < TQ_THREADS / 32; ++w) df::add_to(th, tl, red_h[w], red_l[w]);
       const float xh = mjh[j], xl = mjl[j];
       float nh, nl;
       df::sqrt_df(th, tl, nh, nl);
@@ -643,19 +645,21 @@ __global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ ta
     __syncthreads();
     const float bh = sh_bh, bl = sh_bl;
     if (bh != 0.f) {
-      // one aligned 8-lane group per trailing column, 32 columns per round
-      for (int k0 = j + 1; k0 < c; k0 += 32) {
+      // one aligned 8-lane group per trailing column, TQ_THREADS / 8 columns per round
+      for (int k0 = j + 1; k0 < c; k0 += TQ_THREADS / 8) {
         const int k = k0 + (tid >> 3), gl = tid & 7;
         const bool on = k < c;
         float* mkh = Mh + (on ? k : j) * ldm;
         float* mkl = Ml + (on ? k : j) * ldm;
-        float dh = 0.f, dl = 0.f;
+        float dh = 0.f, dl = 0.f, eh = 0.f, el = 0.f;  // two chains for latency
         if (on) {
 #pragma unroll
-          for (int ii = 0; ii < 17; ++ii) {  // rows j .. m - 1, m <= 136
-            const int i = j + gl + 8 * ii;
+          for (int ii = 0; ii < 17; ii += 2) {  // rows j .. m - 1, m <= 136
+            const int i = j + gl + 8 * ii, i2 = i + 8;
             if (i < m) df::dot_acc(mjh[i], mjl[i], mkh[i], mkl[i], dh, dl);
+            if (ii + 1 < 17 && i2 < m) df::dot_acc(mjh[i2], mjl[i2], mkh[i2], mkl[i2], eh, el);
           }
+          df::add_to(dh, dl, eh, el);
         }
         df::group8_sum(dh, dl);
         if (on) {
@@ -675,7 +679,7 @@ __global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ ta
     __syncthreads();
   }
   double* Ro = R + (int64_t)tk.out_slot * c * c;
-  for (int idx = tid; idx < c * c; idx += 256) {
+  for (int idx = tid; idx < c * c; idx += TQ_THREADS) {
     const int rr = idx / c, col = idx % c;
     Ro[idx] = (rr <= col && rr < steps) ? df::join(Mh[col * ldm + rr], Ml[col * ldm + rr]) : 0.0;
   }
@@ -684,7 +688,7 @@ __global__ __launch_bounds__(256) void k_tsqr_df(const TsqrTask* __restrict__ ta
 // The merge of two c x c triangles R = qr([R1; R2]) of k_tsqr_merge (packed
 // triangles, the j-th reflector touching row j of R1 and rows 0..j of R2) in
 // double-float; FP64 in and out.
-__global__ __launch_bounds__(256) void k_tsqr_merge_df(const TsqrTask* __restrict__ tasks, int c,
+__global__ __launch_bounds__(TQ_THREADS) void k_tsqr_merge_df(const TsqrTask* __restrict__ tasks, int c,
                                                        double* __restrict__ R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int pk = c * (c + 1) / 2;
@@ -692,13 +696,13 @@ __global__ __launch_bounds__(256) void k_tsqr_merge_df(const TsqrTask* __restric
   float* Al = Ah + pk;
   float* Bh = Al + pk;                              // R2, packed upper
   float* Bl = Bh + pk;
-  __shared__ float red_h[8], red_l[8];
+  __shared__ float red_h[TQ_THREADS / 32], red_l[TQ_THREADS / 32];
   __shared__ float sh_ah, sh_al, sh_bh, sh_bl, sh_vh, sh_vl;
   const TsqrTask tk = tasks[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* R1 = R + (int64_t)tk.slot[0] * c * c;
   const double* R2 = R + (int64_t)tk.slot[1] * c * c;
-  for (int idx = tid; idx < c * c; idx += 256) {
+  for (int idx = tid; idx < c * c; idx += TQ_THREADS) {
     const int rr = idx / c, col = idx % c;
     if (rr <= col) {
       const int o = col * (col + 1) / 2 + rr;
@@ -710,14 +714,14 @@ __global__ __launch_bounds__(256) void k_tsqr_merge_df(const TsqrTask* __restric
   for (int j = 0; j < c; ++j) {
     const int oj = j * (j + 1) / 2;  // rows 0..j of column j of R2
     float sh = 0.f, sl = 0.f;
-    for (int i = tid; i <= j; i += 256) df::dot_acc(Bh[oj + i], Bl[oj + i], Bh[oj + i], Bl[oj + i], sh, sl);
+    for (int i = tid; i <= j; i += TQ_THREADS) df::dot_acc(Bh[oj + i], Bl[oj + i], Bh[oj + i], Bl[oj + i], sh, sl);
     df::warp_sum(sh, sl);
     if (lane == 0) { red_h[warp] = sh; red_l[warp] = sl; }
     __syncthreads();
     if (tid == 0) {
       // the reflector's scalars in double-float (see k_tsqr_df)
       float th = red_h[0], tl = red_l[0];
-      for (int w = 1; w < 8; ++w) df::add_to(th, tl, red_h[w], red_l[w]);
+      for (int w = 1; w < TQ_THREADS / 32; ++w) df::add_to(th, tl, red_h[w], red_l[w]);
       const float xh = Ah[oj + j], xl = Al[oj + j];
       float sh2, sl2, nh, nl;
       df::mul(xh, xl, xh, xl, sh2, sl2);
@@ -742,19 +746,21 @@ __global__ __launch_bounds__(256) void k_tsqr_merge_df(const TsqrTask* __restric
     __syncthreads();
     const float bh = sh_bh, bl = sh_bl, vh = sh_vh, vl = sh_vl;
     if (bh != 0.f) {
-      // one aligned 8-lane group per trailing column, 32 columns per round
-      for (int k0 = j + 1; k0 < c; k0 += 32) {
+      // one aligned 8-lane group per trailing column, TQ_THREADS / 8 columns per round
+      for (int k0 = j + 1; k0 < c; k0 += TQ_THREADS / 8) {
         const int k = k0 + (tid >> 3), gl = tid & 7;
         const bool on = k < c;
         const int kk = on ? k : j;
         const int ok = kk * (kk + 1) / 2;
-        float dh = 0.f, dl = 0.f;
+        float dh = 0.f, dl = 0.f, eh = 0.f, el = 0.f;  // two chains for latency
         if (on) {
 #pragma unroll
-          for (int ii = 0; ii < 16; ++ii) {  // rows 0 .. j, j < c <= 128
-            const int i = gl + 8 * ii;
+          for (int ii = 0; ii < 16; ii += 2) {  // rows 0 .. j, j < c <= 128
+            const int i = gl + 8 * ii, i2 = i + 8;
             if (i <= j) df::dot_acc(Bh[oj + i], Bl[oj + i], Bh[ok + i], Bl[ok + i], dh, dl);
+            if (i2 <= j) df::dot_acc(Bh[oj + i2], Bl[oj + i2], Bh[ok + i2], Bl[ok + i2], eh, el);
           }
+          df::add_to(dh, dl, eh, el);
         }
         df::group8_sum(dh, dl);
         if (on) {
@@ -777,7 +783,7 @@ __global__ __launch_bounds__(256) void k_tsqr_merge_df(const TsqrTask* __restric
     __syncthreads();
   }
   double* Ro = R + (int64_t)tk.out_slot * c * c;
-  for (int idx = tid; idx < c * c; idx += 256) {
+  for (int idx = tid; idx < c * c; idx += TQ_THREADS) {
     const int rr = idx / c, col = idx % c;
     const int o = col * (col + 1) / 2 + rr;
     Ro[idx] = (rr <= col) ? df::join(Ah[o], Al[o]) : 0.0;
@@ -802,12 +808,12 @@ void launch_tsqr_df(const TsqrTask* tasks, int ntasks, int merge, const double* 
     const size_t smem = (size_t)2 * ldm * c * sizeof(float);
     static std::atomic<uint32_t> done{0};
     raise_smem_limit((const void*)k_tsqr_df, done);
-    k_tsqr_df<<<ntasks, 256, smem, st>>>(tasks, P, ldp, c, R, ldm);
+    k_tsqr_df<<<ntasks, TQ_THREADS, smem, st>>>(tasks, P, ldp, c, R, ldm);
   } else {
     const size_t smem = (size_t)2 * c * (c + 1) * sizeof(float);
     static std::atomic<uint32_t> done{0};
     raise_smem_limit((const void*)k_tsqr_merge_df, done);
-    k_tsqr_merge_df<<<ntasks, 256, smem, st>>>(tasks, c, R);
+    k_tsqr_merge_df<<<ntasks, TQ_THREADS, smem, st>>>(tasks, c, R);
   }
 }
 
