@@ -38,6 +38,32 @@ __device__ __forceinline__ void rot_df(float ch, float cl, float sh, float sl, f
   }
 }
 
+// Rotation of one FP32 Jacobi pair (phase B below): ga = a_p . a_q, al and be
+// the squared norms.  Flags a correlation above big2 (another sweep is due) and
+// returns false when the pair is already orthogonal to tol; otherwise (tc, ts)
+// = (cos, sin) of the angle that zeroes ga (the smaller root of the standard
+// two-sided formula).
+__device__ __forceinline__ bool jacobi_angle32(float ga, float al, float be, float tol,
+                                               float big2, int gl, int& large, float& tc,
+                                               float& ts) {
+  if (gl == 0 && al > 0.f && be > 0.f && (ga / al) * (ga / be) > big2) large = 1;
+  if (!(ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
+  const float zeta = (be - al) / (2.f * ga);
+  const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  tc = 1.f / sqrtf(1.f + t * t);
+  ts = tc * t;
+  return true;
+}
+// the pair's squared norms after the rotation (c^2 al - 2cs ga + s^2 be and
+// s^2 al + 2cs ga + c^2 be, clamped at 0)
+__device__ __forceinline__ void jacobi_norms32(float tc, float ts, float ga, float& np,
+                                               float& nq) {
+  const float al = np, be = nq;
+  const float cs2 = 2.f * tc * ts, c2 = tc * tc, s2 = ts * ts;
+  np = fmaxf(fmaf(c2, al, fmaf(-cs2, ga, s2 * be)), 0.f);
+  nq = fmaxf(fmaf(s2, al, fmaf(cs2, ga, c2 * be)), 0.f);
+}
+
 // SVD of R (c x c, c <= 128) to about 2^-46 relative accuracy for HM_A32, the
 // phases of k_jacobi_mp with every bulk FP64 operation in double-float:
 //   A. column-pivoted Householder QR R P = Q2 R2 (Businger-Golub; DF entries,
@@ -55,10 +81,10 @@ __device__ __forceinline__ void rot_df(float ch, float cl, float sh, float sl, f
 //      descending, the sign convention of k_jacobi_mp.
 // R is scaled by a power of two (exact) so that its largest entry lies in
 // [1, 2): squared column norms then stay inside the float range.
-__global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ node_slot,
-                                                   const double* __restrict__ R, int c,
-                                                   double* __restrict__ W,
-                                                   double* __restrict__ sigma) {
+__global__ __launch_bounds__(512, 1) void k_jacobi_df(const int32_t* __restrict__ node_slot,
+                                                      const double* __restrict__ R, int c,
+                                                      double* __restrict__ W,
+                                                      double* __restrict__ sigma) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int cc = c * c;
   float* reg0 = reinterpret_cast<float*>(smem_raw);
@@ -261,6 +287,7 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
     // that they unroll; the arithmetic and its order are those of the plain loops)
     const float tol = (float)(5.960464477539063e-08 * sqrt((double)c));
     const float big2 = tol;
+    const bool vec = (c & 3) == 0;
     for (int sweep = 0; sweep < 40; ++sweep) {
       if (tid == 0) { rotated = 0; large = 0; }
       __syncthreads();
@@ -278,24 +305,73 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
         const bool valid = p < c && q < c;
         float* ap = X32 + (valid ? p : 0) * c;
         float* aq = X32 + (valid ? q : 0) * c;
-        float ga = 0;
-        if (valid) {
+        if (vec) {
+          // c a multiple of 4: lane gl holds the 16-byte chunks gl, gl + 8, ..
+          // of both columns in registers (one 128-byte row of shared memory per
+          // group and load: no bank conflicts) for the dot product and the
+          // rotation
+          const int c4 = c >> 2;
+          float4 xa[4], xb[4];
+          float ga = 0.f;
+          if (valid) {
 #pragma unroll
-          for (int ii = 0; ii < 16; ++ii) {
-            const int i = gl + 8 * ii;
-            if (i < c) ga = fmaf(ap[i], aq[i], ga);
+            for (int k = 0; k < 4; ++k) {
+              const int ch = gl + 8 * k;
+              if (ch < c4) {
+                xa[k] = reinterpret_cast<const float4*>(ap)[ch];
+                xb[k] = reinterpret_cast<const float4*>(aq)[ch];
+                ga = fmaf(xa[k].x, xb[k].x, ga);
+                ga = fmaf(xa[k].y, xb[k].y, ga);
+                ga = fmaf(xa[k].z, xb[k].z, ga);
+                ga = fmaf(xa[k].w, xb[k].w, ga);
+              }
+            }
           }
-        }
-        ga += __shfl_xor_sync(0xffffffffu, ga, 4);
-        ga += __shfl_xor_sync(0xffffffffu, ga, 2);
-        ga += __shfl_xor_sync(0xffffffffu, ga, 1);
-        if (valid) {
-          const float al = cn32[p], be = cn32[q];
-          if (gl == 0 && al > 0.f && be > 0.f && (ga / al) * (ga / be) > big2) large = 1;
-          if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
-            const float zeta = (be - al) / (2.f * ga);
-            const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-            const float tc = 1.f / sqrtf(1.f + t * t), ts = tc * t;
+          ga += __shfl_xor_sync(0xffffffffu, ga, 4);
+          ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+          ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+          float tc, ts;
+          if (valid && jacobi_angle32(ga, cn32[p], cn32[q], tol, big2, gl, large, tc, ts)) {
+            float4* vp = reinterpret_cast<float4*>(V32 + p * c);
+            float4* vq = reinterpret_cast<float4*>(V32 + q * c);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int ch = gl + 8 * k;
+              if (ch < c4) {
+                const float4 x = xa[k], y = xb[k];
+                reinterpret_cast<float4*>(ap)[ch] =
+                    make_float4(tc * x.x - ts * y.x, tc * x.y - ts * y.y, tc * x.z - ts * y.z,
+                                tc * x.w - ts * y.w);
+                reinterpret_cast<float4*>(aq)[ch] =
+                    make_float4(ts * x.x + tc * y.x, ts * x.y + tc * y.y, ts * x.z + tc * y.z,
+                                ts * x.w + tc * y.w);
+                const float4 u = vp[ch], w = vq[ch];
+                vp[ch] = make_float4(tc * u.x - ts * w.x, tc * u.y - ts * w.y,
+                                     tc * u.z - ts * w.z, tc * u.w - ts * w.w);
+                vq[ch] = make_float4(ts * u.x + tc * w.x, ts * u.y + tc * w.y,
+                                     ts * u.z + tc * w.z, ts * u.w + tc * w.w);
+              }
+            }
+            __syncwarp(0xffu << (8 * (lane >> 3)));  // the group's reads of the norms first
+            if (gl == 0) {
+              jacobi_norms32(tc, ts, ga, cn32[p], cn32[q]);
+              rotated = 1;
+            }
+          }
+        } else {
+          float ga = 0;
+          if (valid) {
+#pragma unroll
+            for (int ii = 0; ii < 16; ++ii) {
+              const int i = gl + 8 * ii;
+              if (i < c) ga = fmaf(ap[i], aq[i], ga);
+            }
+          }
+          ga += __shfl_xor_sync(0xffffffffu, ga, 4);
+          ga += __shfl_xor_sync(0xffffffffu, ga, 2);
+          ga += __shfl_xor_sync(0xffffffffu, ga, 1);
+          float tc, ts;
+          if (valid && jacobi_angle32(ga, cn32[p], cn32[q], tol, big2, gl, large, tc, ts)) {
             float* vp = V32 + p * c;
             float* vq = V32 + q * c;
 #pragma unroll
@@ -316,10 +392,9 @@ __global__ __launch_bounds__(512) void k_jacobi_df(const int32_t* __restrict__ n
                 vq[i] = ts * x + tc * y;
               }
             }
+            __syncwarp(0xffu << (8 * (lane >> 3)));  // the group's reads of the norms first
             if (gl == 0) {
-              const float cs2 = 2.f * tc * ts, c2 = tc * tc, s2 = ts * ts;
-              cn32[p] = fmaxf(fmaf(c2, al, fmaf(-cs2, ga, s2 * be)), 0.f);
-              cn32[q] = fmaxf(fmaf(s2, al, fmaf(cs2, ga, c2 * be)), 0.f);
+              jacobi_norms32(tc, ts, ga, cn32[p], cn32[q]);
               rotated = 1;
             }
           }
