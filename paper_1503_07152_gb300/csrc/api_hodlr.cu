@@ -98,14 +98,9 @@ hm_status hodlr_peel(Ctx<T>& c, const T* U, const T* V, int level, const T* X, T
   return check_launch("peel");
 }
 
-// Orthonormal basis / truncated SVD of the panel P (N x pc) per node of level lv.
-// Writes Q (N x r) and, when want_m, the coefficients M (pc x r per node).
+// The panel width pc must fit the shared-memory QR and SVD kernels.
 template <typename T>
-hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
-                    T* Q, bool want_m, int32_t* rank_lv) {
-  const LevelPlan& lp = c.tree->plans[lv];
-  const int64_t N = c.N;
-  const int r = c.r;
+static hm_status panel_fits(int pc) {
   const size_t lim = 220 * 1024;
   if (pc > 128 || (size_t)(kTsqrRows + 8) * pc * sizeof(T) > lim ||
       (size_t)pc * (pc + 1) * sizeof(T) > lim ||
@@ -113,6 +108,16 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
     set_error("panel too wide for the shared-memory QR in this precision");
     return HM_EUNSUPPORTED;
   }
+  return HM_OK;
+}
+
+// First half of panel_svd: the R factor of every node's panel (TSQR rounds)
+// and its SVD (W, sigma per node).
+template <typename T>
+hm_status panel_qr(Ctx<T>& c, int lv, const T* P, int pc) {
+  HM_TRY(panel_fits<T>(pc));
+  const LevelPlan& lp = c.tree->plans[lv];
+  const int64_t N = c.N;
   mark(c, lv - 1, c.side, HM_PHASE_TSQR);
   for (size_t rd = 0; rd < lp.d_rounds.size(); ++rd) {
     if (sizeof(T) == 8 && c.bf16)  // HM_A32: the Householder work in double-float
@@ -128,6 +133,19 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
                      (double*)c.sig, c.st);
   else
     launch_jacobi<T>(lp.d_final_slot, lp.nnodes, c.Rw, pc, c.W, c.sig, c.st);
+  c.launches += (int)lp.d_rounds.size() + 1;
+  return HM_OK;
+}
+
+// Second half of panel_svd: rank decision and the orthonormal basis Q (N x r)
+// per node of level lv from W, sigma and the panel; when want_m, also the
+// coefficients M (pc x r per node).
+template <typename T>
+hm_status panel_post(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
+                     T* Q, bool want_m, int32_t* rank_lv) {
+  const LevelPlan& lp = c.tree->plans[lv];
+  const int64_t N = c.N;
+  const int r = c.r;
   // Directions of the sample range below floor_rel * sigma_1 are dropped.  In
   // FP64 the floor sits well above rounding noise (1e-12): directions near the
   // noise level are arbitrary functions of the rounding and would capture an
@@ -147,8 +165,17 @@ hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, b
   launch_cholqr<T>(lp.nnodes, c.G, r, rank_lv, c.T2, c.W, c.sig, pc, c.M, want_m ? 1 : 0, c.st);
   launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Q, N, 0, 0, r, c.T2, (int64_t)r * r, r, 0, Q, N, 0,
                    0, r, (T)1, (T)0, c.st, c.bf16 && sizeof(T) == 8);
-  c.launches += (int)lp.d_rounds.size() + 8;
+  c.launches += 7;
   return check_launch("panel svd");
+}
+
+// Orthonormal basis / truncated SVD of the panel P (N x pc) per node of level lv.
+// Writes Q (N x r) and, when want_m, the coefficients M (pc x r per node).
+template <typename T>
+hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
+                    T* Q, bool want_m, int32_t* rank_lv) {
+  HM_TRY(panel_qr(c, lv, P, pc));
+  return panel_post(c, lv, P, pc, mode, kfix, set_eps, Q, want_m, rank_lv);
 }
 
 template <typename T>
@@ -207,61 +234,104 @@ double box_ms(Ctx<T>& c) {
   return ms;
 }
 
+// One level of the HODLR compression in three stages, around the two panel
+// factorizations (panel_qr) of the level:
+//   stage A: X = [Omega_2 | Omega_1], S = A X, peel, gather the A-side panel;
+//   (panel_qr of the A-side panel)
+//   stage B: U bases of the children, X' = [0 U_beta | U_alpha 0], S = A^T X',
+//            peel, gather the A^T-side panel;
+//   (panel_qr of the A^T-side panel)
+//   stage C: V bases, sibling matrices absorbed into U_beta.
 template <typename T>
-hm_status compress_hodlr_t(Ctx<T>& c, hm_handle* h) {
+hm_status hodlr_stage_a(Ctx<T>& c, hm_handle* h, int level) {
   const int64_t N = c.N;
   const int r = c.r;
   const int L = c.tree->L;
-  const int nmax = (int)c.tree->nmax;
+  const int lv = level + 1;
   T* U = (T*)h->U;
   T* V = (T*)h->V;
-  const bool bf16 = c.bf16;
-  for (int level = 0; level < L; ++level) {
-    const int lv = level + 1;
-    T* Ulv = U + (int64_t)(lv - 1) * N * r;
-    T* Vlv = V + (int64_t)(lv - 1) * N * r;
-    int32_t* rank_lv = c.rank_dev + ((int64_t)1 << lv);
-    mark(c, level, 0, HM_PHASE_SAMPLE);
-    launch_gauss_fill<T>(c.X, N, N, r, level, c.seed, bf16, c.tree->d_start, L, c.st);
-    HM_TRY(box(c, 0, c.X, c.S, r));                      // Y_1 = A Omega_2
-    HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));      // Y_2 = A Omega_1
-    nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
-    mark(c, level, 0, HM_PHASE_PEEL);
-    HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 0, -1.0));
-    mark(c, level, 0, HM_PHASE_BASES);
-    launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
-    c.side = 0;
-    HM_TRY(panel_svd(c, lv, c.P, r, 0, 0, false, Ulv, false, c.rank_tmp));
-    mark(c, level, 1, HM_PHASE_SAMPLE);
-    launch_scatter_probe<T>(Ulv, N, c.X, N, N, r, lv, c.tree->d_start, L, c.st);
-    HM_TRY(box(c, 1, c.X, c.S, r));                      // Z_1 = A^T Omega_2
-    HM_TRY(box(c, 1, c.X + N * r, c.S + N * r, r));      // Z_2 = A^T Omega_1
-    nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
-    mark(c, level, 1, HM_PHASE_PEEL);
-    HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 1, -1.0));
-    mark(c, level, 1, HM_PHASE_BASES);
-    launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
-    const int mode = c.mode_tol ? 1 : 2;
-    c.side = 1;
-    HM_TRY(panel_svd(c, lv, c.P, r, mode, c.kfix, level == 0, Vlv, true, rank_lv));
-    // U_beta <- U_beta (W_k S_k R2^T) with the coefficients of the sibling's panel
-    mark(c, level, 1, HM_PHASE_BASES);
-    const LevelPlan& lp = c.tree->plans[lv];
-    launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Ulv, N, 0, 0, r, c.M, (int64_t)r * r, r, 1, Ulv,
-                     N, 0, 0, r, (T)1, (T)0, c.st, c.bf16 && sizeof(T) == 8);
-    c.launches += 6;
-    HM_TRY(check_launch("hodlr level"));
-  }
-  // leaf blocks through the identity probe
+  mark(c, level, 0, HM_PHASE_SAMPLE);
+  launch_gauss_fill<T>(c.X, N, N, r, level, c.seed, c.bf16, c.tree->d_start, L, c.st);
+  HM_TRY(box(c, 0, c.X, c.S, r));                      // Y_1 = A Omega_2
+  HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));      // Y_2 = A Omega_1
+  nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+  mark(c, level, 0, HM_PHASE_PEEL);
+  HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 0, -1.0));
+  mark(c, level, 0, HM_PHASE_BASES);
+  launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
+  c.side = 0;
+  return HM_OK;
+}
+
+template <typename T>
+hm_status hodlr_stage_b(Ctx<T>& c, hm_handle* h, int level) {
+  const int64_t N = c.N;
+  const int r = c.r;
+  const int L = c.tree->L;
+  const int lv = level + 1;
+  T* U = (T*)h->U;
+  T* V = (T*)h->V;
+  T* Ulv = U + (int64_t)(lv - 1) * N * r;
+  HM_TRY(panel_post(c, lv, c.P, r, 0, 0, false, Ulv, false, c.rank_tmp));
+  mark(c, level, 1, HM_PHASE_SAMPLE);
+  launch_scatter_probe<T>(Ulv, N, c.X, N, N, r, lv, c.tree->d_start, L, c.st);
+  HM_TRY(box(c, 1, c.X, c.S, r));                      // Z_1 = A^T Omega_2
+  HM_TRY(box(c, 1, c.X + N * r, c.S + N * r, r));      // Z_2 = A^T Omega_1
+  nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+  mark(c, level, 1, HM_PHASE_PEEL);
+  HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 1, -1.0));
+  mark(c, level, 1, HM_PHASE_BASES);
+  launch_gather_sample<T>(c.S, N, c.P, N, N, r, lv, c.tree->d_start, L, c.st);
+  c.side = 1;
+  return HM_OK;
+}
+
+template <typename T>
+hm_status hodlr_stage_c(Ctx<T>& c, hm_handle* h, int level) {
+  const int64_t N = c.N;
+  const int r = c.r;
+  const int lv = level + 1;
+  T* Ulv = (T*)h->U + (int64_t)(lv - 1) * N * r;
+  T* Vlv = (T*)h->V + (int64_t)(lv - 1) * N * r;
+  int32_t* rank_lv = c.rank_dev + ((int64_t)1 << lv);
+  const int mode = c.mode_tol ? 1 : 2;
+  HM_TRY(panel_post(c, lv, c.P, r, mode, c.kfix, level == 0, Vlv, true, rank_lv));
+  // U_beta <- U_beta (W_k S_k R2^T) with the coefficients of the sibling's panel
+  mark(c, level, 1, HM_PHASE_BASES);
+  const LevelPlan& lp = c.tree->plans[lv];
+  launch_seg_nn<T>(lp.d_nn, lp.n_nn, lp.node0, Ulv, N, 0, 0, r, c.M, (int64_t)r * r, r, 1, Ulv,
+                   N, 0, 0, r, (T)1, (T)0, c.st, c.bf16 && sizeof(T) == 8);
+  c.launches += 6;
+  return check_launch("hodlr level");
+}
+
+// leaf blocks through the identity probe
+template <typename T>
+hm_status hodlr_leaves(Ctx<T>& c, hm_handle* h) {
+  const int64_t N = c.N;
+  const int L = c.tree->L;
+  const int nmax = (int)c.tree->nmax;
   mark(c, L, 0, HM_PHASE_SAMPLE);
   launch_identity_probe<T>(c.XI, N, N, nmax, c.tree->d_start, L, c.st);
   HM_TRY(box(c, 0, c.XI, c.YI, nmax));
   mark(c, L, 0, HM_PHASE_PEEL);
-  HM_TRY(hodlr_peel(c, U, V, L, c.XI, c.YI, nmax, 0, -1.0));
+  HM_TRY(hodlr_peel(c, (T*)h->U, (T*)h->V, L, c.XI, c.YI, nmax, 0, -1.0));
   mark(c, L, 0, HM_PHASE_BASES);
   launch_extract_diag<T>(c.YI, N, (T*)h->D, nmax, c.tree->d_start, c.tree->d_size, L, c.st);
   c.launches += 2;
   return check_launch("hodlr diagonal");
+}
+
+template <typename T>
+hm_status compress_hodlr_t(Ctx<T>& c, hm_handle* h) {
+  for (int level = 0; level < c.tree->L; ++level) {
+    HM_TRY(hodlr_stage_a(c, h, level));
+    HM_TRY(panel_qr(c, level + 1, c.P, c.r));
+    HM_TRY(hodlr_stage_b(c, h, level));
+    HM_TRY(panel_qr(c, level + 1, c.P, c.r));
+    HM_TRY(hodlr_stage_c(c, h, level));
+  }
+  return hodlr_leaves(c, h);
 }
 
 // --------------------------------------------------------------- apply -----
@@ -357,15 +427,21 @@ static hm_status check_opts(const hm_operator* op, const hm_tree* tree, const hm
 
 int opts_r(const hm_opts* o) { return o->mode_tol ? o->r : o->k + o->p; }
 
+namespace hm {
+
+// Allocations and zeroing of one HODLR compression (handle, tree tables,
+// factors, context); t0 recorded on the compression's stream.
 template <typename T>
-static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, const hm_opts* o,
-                                      cudaStream_t st, hm_handle** out) {
+hm_status hodlr_begin(HodlrRun<T>& R, const hm_operator* op, hm_tree* tree, const hm_opts* o,
+                      cudaStream_t st) {
   const int r = opts_r(o);
   if (r > 128 || 2 * r > 256) {
     set_error("compress: r must be at most 128");
     return HM_EUNSUPPORTED;
   }
+  R.o = o;
   hm_handle* h = new hm_handle();
+  R.h = h;
   h->format = HM_FORMAT_HODLR;
   h->prec = o->prec;
   h->n = tree->n;
@@ -379,7 +455,7 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
   if (s == HM_OK) s = device_alloc(&h->V, sizeof(T) * (size_t)tree->L * N * r);
   if (s == HM_OK)
     s = device_alloc(&h->D, sizeof(T) * ((size_t)1 << tree->L) * tree->nmax * tree->nmax);
-  Ctx<T> c;
+  Ctx<T>& c = R.c;
   c.op = op;
   c.tree = &h->tree;
   c.st = st;
@@ -390,25 +466,36 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
   c.kfix = o->k;
   c.tol = o->tol;
   c.bf16 = (o->prec != HM_FP64);
-  int32_t* rank_block = nullptr;
-  if (s == HM_OK) s = device_alloc((void**)&rank_block, sizeof(int32_t) * 2 * ((size_t)1 << (tree->L + 1)));
-  c.rank_dev = rank_block;
-  c.rank_tmp = rank_block + ((size_t)1 << (tree->L + 1));
+  if (s == HM_OK)
+    s = device_alloc((void**)&R.rank_block, sizeof(int32_t) * 2 * ((size_t)1 << (tree->L + 1)));
+  c.rank_dev = R.rank_block;
+  c.rank_tmp = R.rank_block + ((size_t)1 << (tree->L + 1));
   if (s == HM_OK) s = ctx_alloc(c, r, tree->nmax);
-  cudaEvent_t t0, t1;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
+  cudaEventCreate(&R.t0);
+  cudaEventCreate(&R.t1);
   c.profile = profiling_on();
   if (s == HM_OK) {
     cudaMemsetAsync(h->U, 0, sizeof(T) * (size_t)tree->L * N * r, st);
     cudaMemsetAsync(h->V, 0, sizeof(T) * (size_t)tree->L * N * r, st);
-    cudaMemsetAsync(rank_block, 0, sizeof(int32_t) * 2 * ((size_t)1 << (tree->L + 1)), st);
-    cudaEventRecord(t0, st);
-    s = compress_hodlr_t<T>(c, h);
-    mark(c, tree->L, 0, -1);  // end of the last phase
-    cudaEventRecord(t1, st);
+    cudaMemsetAsync(R.rank_block, 0, sizeof(int32_t) * 2 * ((size_t)1 << (tree->L + 1)), st);
+    cudaEventRecord(R.t0, st);
   }
+  return s;
+}
+
+// After the last stage: t1, synchronization, status flags, ranks and info;
+// frees the context.  On success *out receives the handle, otherwise it is
+// destroyed.  s is the status of the stages (HM_OK if they all ran).
+template <typename T>
+hm_status hodlr_end(HodlrRun<T>& R, hm_status s, hm_handle** out) {
+  Ctx<T>& c = R.c;
+  hm_handle* h = R.h;
+  const hm_opts* o = R.o;
+  const hm_tree* tree = h ? &h->tree : nullptr;
+  const cudaStream_t st = c.st;
   if (s == HM_OK) {
+    mark(c, tree->L, 0, -1);  // end of the last phase
+    cudaEventRecord(R.t1, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
       set_error(std::string("compress: ") + cudaGetErrorString(e));
@@ -417,14 +504,16 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
   }
   // a sampling GEMM whose bounded wait gave up wrote NaN: report the timeout
   // itself rather than the non-finite samples it caused
-  if (s == HM_OK) s = dense_take_timeout(op);
+  if (s == HM_OK) s = dense_take_timeout(c.op);
   int32_t flags[4] = {0, 0, 0, 0};
   double eps[2] = {0, 0};
+  const int64_t N = c.N;
+  const int r = c.r;
   if (s == HM_OK) {
     cudaMemcpy(flags, c.flags_dev, sizeof(flags), cudaMemcpyDeviceToHost);
     cudaMemcpy(eps, c.eps_dev, sizeof(eps), cudaMemcpyDeviceToHost);
     h->rank.assign((size_t)1 << (tree->L + 1), 0);
-    cudaMemcpy(h->rank.data(), rank_block, sizeof(int32_t) * h->rank.size(),
+    cudaMemcpy(h->rank.data(), R.rank_block, sizeof(int32_t) * h->rank.size(),
                cudaMemcpyDeviceToHost);
     if (flags[0]) {
       set_error("compress: NaN or Inf in the black-box samples");
@@ -455,22 +544,37 @@ static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, cons
                          sizeof(T) * ((size_t)1 << tree->L) * tree->nmax * tree->nmax);
     in.eps_abs = eps[0];
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventElapsedTime(&ms, R.t0, R.t1);
     in.t_compress_ms = ms;
     in.t_blackbox_ms = box_ms(c);
     in.launches = c.launches;
   }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
+  if (R.t0) cudaEventDestroy(R.t0);
+  if (R.t1) cudaEventDestroy(R.t1);
+  R.t0 = R.t1 = nullptr;
   marks_finish(c, s == HM_OK ? h : nullptr);
   ctx_free(c);
-  if (rank_block) cudaFree(rank_block);
+  if (R.rank_block) cudaFree(R.rank_block);
+  R.rank_block = nullptr;
+  R.h = nullptr;
   if (s != HM_OK) {
-    hm_destroy(h);
+    if (h) hm_destroy(h);
     return s;
   }
   *out = h;
   return HM_OK;
+}
+
+
+}  // namespace hm
+
+template <typename T>
+static hm_status compress_hodlr_entry(const hm_operator* op, hm_tree* tree, const hm_opts* o,
+                                      cudaStream_t st, hm_handle** out) {
+  HodlrRun<T> R;
+  hm_status s = hodlr_begin(R, op, tree, o, st);
+  if (s == HM_OK) s = compress_hodlr_t<T>(R.c, R.h);
+  return hodlr_end(R, s, out);
 }
 
 extern "C" hm_status hm_compress_hodlr(const hm_operator* op, const hm_tree* tree,
@@ -493,7 +597,17 @@ namespace hm {
   template void ctx_free<T>(Ctx<T>&);                                                       \
   template double box_ms<T>(Ctx<T>&);                                                       \
   template void mark<T>(Ctx<T>&, int, int, int);                                            \
-  template void marks_finish<T>(Ctx<T>&, hm_handle*);
+  template void marks_finish<T>(Ctx<T>&, hm_handle*);                                       \
+  template hm_status panel_qr<T>(Ctx<T>&, int, const T*, int);                              \
+  template hm_status panel_post<T>(Ctx<T>&, int, const T*, int, int, int, bool, T*, bool,   \
+                                   int32_t*);                                               \
+  template hm_status hodlr_begin<T>(HodlrRun<T>&, const hm_operator*, hm_tree*,             \
+                                    const hm_opts*, cudaStream_t);                          \
+  template hm_status hodlr_stage_a<T>(Ctx<T>&, hm_handle*, int);                            \
+  template hm_status hodlr_stage_b<T>(Ctx<T>&, hm_handle*, int);                            \
+  template hm_status hodlr_stage_c<T>(Ctx<T>&, hm_handle*, int);                            \
+  template hm_status hodlr_leaves<T>(Ctx<T>&, hm_handle*);                                  \
+  template hm_status hodlr_end<T>(HodlrRun<T>&, hm_status, hm_handle**);
 HM_INST(float)
 HM_INST(double)
 #undef HM_INST

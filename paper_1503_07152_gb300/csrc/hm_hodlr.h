@@ -57,6 +57,11 @@ template <typename T>
 hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
                     T* Q, bool want_m, int32_t* rank_lv);
 template <typename T>
+hm_status panel_qr(Ctx<T>& c, int lv, const T* P, int pc);
+template <typename T>
+hm_status panel_post(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
+                     T* Q, bool want_m, int32_t* rank_lv);
+template <typename T>
 hm_status ctx_alloc(Ctx<T>& c, int pc_max, int64_t extra_cols);
 template <typename T>
 void ctx_free(Ctx<T>& c);
@@ -65,6 +70,34 @@ double box_ms(Ctx<T>& c);
 template <typename T>
 hm_status hodlr_apply_t(const hm_handle* h, int trans, int64_t ncols, const T* X, int64_t ldx,
                         T* Y, int64_t ldy, cudaStream_t st);
+
+// One HODLR compression in flight: its handle, context and timing events.
+template <typename T>
+struct HodlrRun {
+  hm_handle* h = nullptr;
+  Ctx<T> c;
+  int32_t* rank_block = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  const hm_opts* o = nullptr;
+};
+// hm_compress_hodlr in pieces, so that a batch can interleave its operators
+// level by level: begin (allocations, on `st`), per level stage A, panel_qr,
+// stage B, panel_qr, stage C (levels 0 .. L - 1), then the leaves, then end
+// (synchronizes the context's stream, fills the handle's ranks and info; on
+// failure destroys the handle).
+template <typename T>
+hm_status hodlr_begin(HodlrRun<T>& R, const hm_operator* op, hm_tree* tree, const hm_opts* o,
+                      cudaStream_t st);
+template <typename T>
+hm_status hodlr_stage_a(Ctx<T>& c, hm_handle* h, int level);
+template <typename T>
+hm_status hodlr_stage_b(Ctx<T>& c, hm_handle* h, int level);
+template <typename T>
+hm_status hodlr_stage_c(Ctx<T>& c, hm_handle* h, int level);
+template <typename T>
+hm_status hodlr_leaves(Ctx<T>& c, hm_handle* h);
+template <typename T>
+hm_status hodlr_end(HodlrRun<T>& R, hm_status s, hm_handle** out);
 
 }  // namespace hm
 

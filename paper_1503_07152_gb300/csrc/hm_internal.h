@@ -72,6 +72,22 @@ struct TsqrTask {
   int64_t r1[2];
 };
 
+// One node's work item of a level-wide launch that spans several operators'
+// compressions (hm_compress_batched): the block reads its pointers and panel
+// width here instead of from the launch arguments, so that one launch covers
+// every operator's nodes of a level with the same per-node arithmetic as the
+// one-operator launches.
+struct NodeJob {
+  const TsqrTask* task;  // TSQR: the block's task (device memory)
+  const double* P;       // TSQR first round: the panel (column-major, ld = ldp)
+  double* R;             // TSQR: base of the R slots; SVD: the node's c x c R
+  double* W;             // SVD: the node's c x c W slot
+  double* sigma;         // SVD: the node's c singular values
+  int64_t ldp;
+  int32_t c;             // panel width
+  int32_t pad;
+};
+
 // ------------------------------------------------------- launchers --------
 // All launchers enqueue on `st` and return cudaSuccess-style status via
 // check_launch; T is float (mixed) or double (FP64).
@@ -162,6 +178,11 @@ void launch_tsqr_df(const TsqrTask* tasks, int ntasks, int merge, const double* 
                     int c, double* R, cudaStream_t st);
 void launch_jacobi_df(const int32_t* node_slot, int nnodes, const double* R, int c, double* W,
                       double* sigma, cudaStream_t st);
+// The same two kernels over a list of node jobs (one block per job, each with
+// its own panel, R slots and width; cmax = the largest width, which sizes the
+// shared memory).
+void launch_tsqr_df_jobs(const NodeJob* jobs, int njobs, int merge, int cmax, cudaStream_t st);
+void launch_jacobi_df_jobs(const NodeJob* jobs, int njobs, int cmax, cudaStream_t st);
 
 // Rank decision + T1 = W(:, :k) diag(1/sigma) (c x kcap, zero padded).
 // mode 0: numerical range (sigma > floor * sigma1), at most kcap.

@@ -84,8 +84,22 @@ __device__ __forceinline__ void jacobi_norms32(float tc, float ts, float ga, flo
 __global__ __launch_bounds__(512, 1) void k_jacobi_df(const int32_t* __restrict__ node_slot,
                                                       const double* __restrict__ R, int c,
                                                       double* __restrict__ W,
-                                                      double* __restrict__ sigma) {
+                                                      double* __restrict__ sigma,
+                                                      const NodeJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const double* Rs;
+  double *Wn, *sig;
+  if (jobs) {  // a level-wide launch over several operators' nodes
+    const NodeJob& jb = jobs[blockIdx.x];
+    c = jb.c;
+    Rs = jb.R;
+    Wn = jb.W;
+    sig = jb.sigma;
+  } else {
+    Rs = R + (int64_t)node_slot[blockIdx.x] * c * c;
+    Wn = W + (int64_t)blockIdx.x * c * c;
+    sig = sigma + (int64_t)blockIdx.x * c;
+  }
   const int cc = c * c;
   float* reg0 = reinterpret_cast<float*>(smem_raw);
   float* reg1 = reg0 + cc;
@@ -107,9 +121,6 @@ __global__ __launch_bounds__(512, 1) void k_jacobi_df(const int32_t* __restrict_
   __shared__ float pnh[128], pnl[128], ph0[128];  // A: pivoting norms
   __shared__ float sh_ah, sh_al, sh_sh, sh_sl;
   __shared__ int sh_exp;
-  const int node = blockIdx.x;
-  const double* Rs = R + (int64_t)node_slot[node] * cc;
-  double* Wn = W + (int64_t)node * cc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int nthr = blockDim.x;
   const int pg = tid >> 3, gl = tid & 7;
@@ -642,7 +653,7 @@ __global__ __launch_bounds__(512, 1) void k_jacobi_df(const int32_t* __restrict_
     Wn[perm[i] + col * c] = sgn[col] < 0 ? -u : u;
   }
   for (int j = tid; j < c; j += nthr)
-    sigma[(int64_t)node * c + j] = sv[order[j]] > 0.0 ? ldexp(sv[order[j]], ex) : 0.0;
+    sig[j] = sv[order[j]] > 0.0 ? ldexp(sv[order[j]], ex) : 0.0;
 }
 
 
@@ -656,13 +667,23 @@ constexpr int TQ_THREADS = 512;  // threads of the double-float TSQR kernels
 // Writes the c x c R (row-major, upper triangle) in FP64.
 __global__ __launch_bounds__(TQ_THREADS) void k_tsqr_df(const TsqrTask* __restrict__ tasks,
                                                  const double* __restrict__ P, int64_t ldp,
-                                                 int c, double* __restrict__ R, int ldm) {
+                                                 int c, double* __restrict__ R, int ldm,
+                                                 const NodeJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TsqrTask* tkp = tasks + blockIdx.x;
+  if (jobs) {  // a level-wide launch over several operators' nodes
+    const NodeJob& jb = jobs[blockIdx.x];
+    tkp = jb.task;
+    P = jb.P;
+    ldp = jb.ldp;
+    c = jb.c;
+    R = jb.R;
+  }
+  const TsqrTask tk = *tkp;
   float* Mh = reinterpret_cast<float*>(smem_raw);  // column-major, ld = ldm, high parts
   float* Ml = Mh + (size_t)ldm * c;                 // low parts
   __shared__ float red_h[TQ_THREADS / 32], red_l[TQ_THREADS / 32];
   __shared__ float sh_ah, sh_al, sh_bh, sh_bl;
-  const TsqrTask tk = tasks[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int m = 0;
   for (int s = 0; s < tk.nsrc; ++s) {
@@ -763,9 +784,18 @@ __global__ __launch_bounds__(TQ_THREADS) void k_tsqr_df(const TsqrTask* __restri
 // The merge of two c x c triangles R = qr([R1; R2]) of k_tsqr_merge (packed
 // triangles, the j-th reflector touching row j of R1 and rows 0..j of R2) in
 // double-float; FP64 in and out.
-__global__ __launch_bounds__(TQ_THREADS) void k_tsqr_merge_df(const TsqrTask* __restrict__ tasks, int c,
-                                                       double* __restrict__ R) {
+__global__ __launch_bounds__(TQ_THREADS) void k_tsqr_merge_df(const TsqrTask* __restrict__ tasks,
+                                                              int c, double* __restrict__ R,
+                                                              const NodeJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TsqrTask* tkp = tasks + blockIdx.x;
+  if (jobs) {  // a level-wide launch over several operators' nodes
+    const NodeJob& jb = jobs[blockIdx.x];
+    tkp = jb.task;
+    c = jb.c;
+    R = jb.R;
+  }
+  const TsqrTask tk = *tkp;
   const int pk = c * (c + 1) / 2;
   float* Ah = reinterpret_cast<float*>(smem_raw);  // R1, packed upper
   float* Al = Ah + pk;
@@ -773,7 +803,6 @@ __global__ __launch_bounds__(TQ_THREADS) void k_tsqr_merge_df(const TsqrTask* __
   float* Bl = Bh + pk;
   __shared__ float red_h[TQ_THREADS / 32], red_l[TQ_THREADS / 32];
   __shared__ float sh_ah, sh_al, sh_bh, sh_bl, sh_vh, sh_vl;
-  const TsqrTask tk = tasks[blockIdx.x];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* R1 = R + (int64_t)tk.slot[0] * c * c;
   const double* R2 = R + (int64_t)tk.slot[1] * c * c;
@@ -872,7 +901,16 @@ void launch_jacobi_df(const int32_t* node_slot, int nnodes, const double* R, int
   const size_t smem = (size_t)3 * c * c * sizeof(float);
   static std::atomic<uint32_t> done{0};
   raise_smem_limit((const void*)k_jacobi_df, done);
-  k_jacobi_df<<<nnodes, 512, smem, st>>>(node_slot, R, c, W, sigma);
+  k_jacobi_df<<<nnodes, 512, smem, st>>>(node_slot, R, c, W, sigma, nullptr);
+}
+
+void launch_jacobi_df_jobs(const NodeJob* jobs, int njobs, int cmax, cudaStream_t st) {
+  if (njobs <= 0) return;
+  count_launches(1);
+  const size_t smem = (size_t)3 * cmax * cmax * sizeof(float);
+  static std::atomic<uint32_t> done{0};
+  raise_smem_limit((const void*)k_jacobi_df, done);
+  k_jacobi_df<<<njobs, 512, smem, st>>>(nullptr, nullptr, cmax, nullptr, nullptr, jobs);
 }
 
 void launch_tsqr_df(const TsqrTask* tasks, int ntasks, int merge, const double* P, int64_t ldp,
@@ -883,12 +921,29 @@ void launch_tsqr_df(const TsqrTask* tasks, int ntasks, int merge, const double* 
     const size_t smem = (size_t)2 * ldm * c * sizeof(float);
     static std::atomic<uint32_t> done{0};
     raise_smem_limit((const void*)k_tsqr_df, done);
-    k_tsqr_df<<<ntasks, TQ_THREADS, smem, st>>>(tasks, P, ldp, c, R, ldm);
+    k_tsqr_df<<<ntasks, TQ_THREADS, smem, st>>>(tasks, P, ldp, c, R, ldm, nullptr);
   } else {
     const size_t smem = (size_t)2 * c * (c + 1) * sizeof(float);
     static std::atomic<uint32_t> done{0};
     raise_smem_limit((const void*)k_tsqr_merge_df, done);
-    k_tsqr_merge_df<<<ntasks, TQ_THREADS, smem, st>>>(tasks, c, R);
+    k_tsqr_merge_df<<<ntasks, TQ_THREADS, smem, st>>>(tasks, c, R, nullptr);
+  }
+}
+
+void launch_tsqr_df_jobs(const NodeJob* jobs, int njobs, int merge, int cmax, cudaStream_t st) {
+  if (njobs <= 0) return;
+  count_launches(1);
+  if (!merge) {
+    const int ldm = kTsqrRows + 8;
+    const size_t smem = (size_t)2 * ldm * cmax * sizeof(float);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_tsqr_df, done);
+    k_tsqr_df<<<njobs, TQ_THREADS, smem, st>>>(nullptr, nullptr, 0, cmax, nullptr, ldm, jobs);
+  } else {
+    const size_t smem = (size_t)2 * cmax * (cmax + 1) * sizeof(float);
+    static std::atomic<uint32_t> done{0};
+    raise_smem_limit((const void*)k_tsqr_merge_df, done);
+    k_tsqr_merge_df<<<njobs, TQ_THREADS, smem, st>>>(nullptr, cmax, nullptr, jobs);
   }
 }
 

@@ -105,3 +105,45 @@ def test_batched_error_names_the_operator():
 
 def test_batched_empty():
     assert hm.hm_compress_batched([], [], "hodlr") == []
+
+
+def test_batched_a32_level_wide_launches_equal_one_call():
+    """HM_A32, the batch workload's precision: the TSQR rounds and the panel SVD of
+    a level run as one launch over every operator's nodes (operators of uneven N,
+    depth and panel width).  Each node's arithmetic is that of the one-operator
+    call, so every handle must equal the one-call result bit for bit, with fewer
+    launches than the one-operator calls together."""
+    m = 64
+    rng = np.random.default_rng(11)
+    ops, trees, opts, keep = [], [], [], []
+    for i in range(10):
+        N = int(64 * rng.integers(16, 97))
+        k = 4 + 3 * i
+        A = torch.from_numpy(W.dense_from_factors(W.synthetic_hodlr_factors(
+            N, m, k, seed=5000 + i, shift=float(N))).astype(np.float32)).to(DEV)
+        keep.append(A)
+        ops.append(hm.hm_dense_operator_create(A, fp64_blocks=True, tensor_cores=True))
+        trees.append(hm.Tree(N, m))
+        opts.append(dict(k=k, p=10, seed=6000 + i, prec=hm.HM_A32))
+    ones = [hm.hm_compress_hodlr(ops[i], trees[i], **opts[i]) for i in range(len(ops))]
+    torch.cuda.synchronize()
+    n0 = hm.hm_launch_count()
+    ones = [hm.hm_compress_hodlr(ops[i], trees[i], **opts[i]) for i in range(len(ops))]
+    torch.cuda.synchronize()
+    n_one = hm.hm_launch_count() - n0
+    n0 = hm.hm_launch_count()
+    hs = hm.hm_compress_batched(ops, trees, "hodlr", opts, max_concurrency=4)
+    torch.cuda.synchronize()
+    n_batch = hm.hm_launch_count() - n0
+    assert n_batch < n_one, (n_batch, n_one)
+    for i, A in enumerate(keep):
+        N = A.shape[0]
+        Rb = torch.empty((N, N), device=DEV, dtype=torch.float64)
+        R1 = torch.empty_like(Rb)
+        hm.hm_reconstruct_block(hs[i], 0, N, 0, N, Rb)
+        hm.hm_reconstruct_block(ones[i], 0, N, 0, N, R1)
+        torch.cuda.synchronize()
+        assert torch.equal(Rb, R1), i
+        assert hs[i].info["max_rank"] == ones[i].info["max_rank"], i
+        nA = float(A.double().norm())
+        assert float((Rb.T - A.double()).norm()) / nA < 1e-6, i
