@@ -78,11 +78,21 @@ typedef struct {
  * (mode_tol = 0) or tolerance tol (mode_tol = 1).  r = k + p random vectors
  * per level (p: oversampling, Sec. 2.5, default 10).  In tolerance mode r is
  * given directly by `r` (must be > 0).  leaf_size: the tree's m (Sec. 2.7).
- * seed: key of the Philox4x32-10 test matrices.  prec: HM_FP64 or HM_MIXED.
+ * seed: key of the Philox4x32-10 test matrices.  prec: HM_FP64, HM_A32 or HM_MIXED.
  * hbs_id: for hm_compress_hbs, 1 converts to HBS-ID with adaptive ranks
  * (Sec. 4.3), 0 keeps the fixed-rank HBS form.  strict_rank: 1 makes a
  * saturated adaptive rank an error (HM_ERANK_SATURATED) instead of a counter
  * in hm_info.
+ * lookahead: the A-side test matrix of every level is a fresh Gaussian block
+ * (Sec. 3, Sec. 4.2), so its product with A does not depend on the levels
+ * before it; the compression can then apply the black box to the next level's
+ * block on a second stream of its own while it factors the current level's
+ * samples (and to the identity probe during the last level).  The results are
+ * the same bit for bit.  0: on for the library's own black boxes
+ * (hm_dense_operator_create, hm_log_kernel_operator_create), off for a user
+ * callback; 1: on for any black box, which must then enqueue its work on the
+ * stream it is given and accept two calls in flight at once on two streams;
+ * -1: off.  hm_compress_batched does not look ahead.
  */
 typedef struct {
   int32_t mode_tol;
@@ -95,6 +105,7 @@ typedef struct {
   int32_t prec;
   int32_t hbs_id;
   int32_t strict_rank;
+  int32_t lookahead;
 } hm_opts;
 
 typedef struct hm_tree hm_tree;

@@ -31,7 +31,8 @@ class _Operator(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("mode_tol", C.c_int32), ("k", C.c_int32), ("tol", C.c_double), ("p", C.c_int32),
                 ("r", C.c_int32), ("leaf_size", C.c_int32), ("seed", C.c_uint64),
-                ("prec", C.c_int32), ("hbs_id", C.c_int32), ("strict_rank", C.c_int32)]
+                ("prec", C.c_int32), ("hbs_id", C.c_int32), ("strict_rank", C.c_int32),
+                ("lookahead", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -268,7 +269,7 @@ class Handle:
 
 
 def _opts(r=None, k=None, p=10, tol=None, leaf_size=0, seed=2, prec=HM_MIXED, hbs_id=1,
-          strict_rank=0) -> Opts:
+          strict_rank=0, lookahead=0) -> Opts:
     o = Opts()
     if tol is not None:
         o.mode_tol, o.tol, o.r = 1, float(tol), int(r if r is not None else 60)
@@ -276,6 +277,7 @@ def _opts(r=None, k=None, p=10, tol=None, leaf_size=0, seed=2, prec=HM_MIXED, hb
         o.mode_tol, o.k, o.p = 0, int(k), int(p)
         o.r = int(k) + int(p)
     o.leaf_size, o.seed, o.prec, o.hbs_id, o.strict_rank = leaf_size, seed, prec, hbs_id, strict_rank
+    o.lookahead = lookahead
     return o
 
 

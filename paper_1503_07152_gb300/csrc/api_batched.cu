@@ -114,7 +114,7 @@ hm_status batched_hodlr(const std::vector<int>& members, const hm_operator* ops,
   int bad = -1;
   for (int i : members) {
     runs[i].reset(new HodlrRun<T>());
-    s = hodlr_begin(*runs[i], &ops[i], trees[i], &opts[i], streams[i % S]);
+    s = hodlr_begin(*runs[i], &ops[i], trees[i], &opts[i], streams[i % S], false);
     started.push_back(i);
     if (s != HM_OK) { bad = i; break; }
   }

@@ -356,37 +356,42 @@ hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* 
 }
 
 // ---------------------------------------------------------- dense box ------
-static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* X, int64_t ldx,
-                    void* Y, int64_t ldy, void* stream) {
-  hm_dense_ctx* d = (hm_dense_ctx*)ctx;
-  if (!d || n != d->n || ncols < 0) return 1;
-  cudaStream_t st = (cudaStream_t)stream;
+static int dense_slot_apply(hm_dense_ctx* d, int slot, int trans, int64_t n, int64_t ncols,
+                            const void* X, int64_t ldx, void* Y, int64_t ldy, cudaStream_t st) {
+  if (!d || n != d->n || ncols < 0 || slot < 0 || slot > 1) return 1;
+  uint8_t*& flags = slot ? d->flags1 : d->flags;
+  void*& xs = slot ? d->xs1 : d->xs;
+  int64_t& xs_bytes = slot ? d->xs1_bytes : d->xs_bytes;
+  if (!flags && cudaMalloc((void**)&flags, (size_t)d->flags_bytes) != cudaSuccess) {
+    flags = nullptr;
+    return 3;
+  }
   for (int64_t c0 = 0; c0 < ncols; c0 += 1024) {
     const int64_t w = std::min<int64_t>(1024, ncols - c0);
     if (d->dtype == 5) {  // matrix-free log kernel: symmetric, either product
       const int64_t need = gemm_esg_work_bytes(n, w);
-      if (need > d->xs_bytes) {
-        if (d->xs) cudaFree(d->xs);
-        d->xs = nullptr;
-        d->xs_bytes = 0;
-        if (cudaMalloc(&d->xs, (size_t)need) != cudaSuccess) return 3;
-        d->xs_bytes = need;
+      if (need > xs_bytes) {
+        if (xs) cudaFree(xs);
+        xs = nullptr;
+        xs_bytes = 0;
+        if (cudaMalloc(&xs, (size_t)need) != cudaSuccess) return 3;
+        xs_bytes = need;
       }
       if (launch_gemm_esg_gen(d->tabS, d->tabP, d->aexp, n, w, (const double*)X + c0 * ldx, ldx,
-                              (double*)Y + c0 * ldy, ldy, d->xs, d->flags, d->err, st) != 0)
+                              (double*)Y + c0 * ldy, ldy, xs, flags, d->err, st) != 0)
         return 2;
     } else if (d->dtype == 0)
       launch_dense_gemm<double>((const double*)d->A, d->lda, trans, n, w,
                                 (const double*)X + c0 * ldx, ldx, (double*)Y + c0 * ldy, ldy,
-                                d->flags, st);
+                                flags, st);
     else if (d->dtype == 4 && n <= 524288 && gemm_tc_supported((const float*)d->A, d->lda, n)) {
       const int64_t need = gemm_esg_work_bytes(n, w);
-      if (need > d->xs_bytes) {
-        if (d->xs) cudaFree(d->xs);
-        d->xs = nullptr;
-        d->xs_bytes = 0;
-        if (cudaMalloc(&d->xs, (size_t)need) != cudaSuccess) return 3;
-        d->xs_bytes = need;
+      if (need > xs_bytes) {
+        if (xs) cudaFree(xs);
+        xs = nullptr;
+        xs_bytes = 0;
+        if (cudaMalloc(&xs, (size_t)need) != cudaSuccess) return 3;
+        xs_bytes = need;
       }
       if (!d->aexp) {
         if (cudaMalloc(&d->aexp, sizeof(int) * 2 * (size_t)gemm_esg_exp_count(n)) != cudaSuccess)
@@ -394,30 +399,36 @@ static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* 
         launch_esg_scales((const float*)d->A, d->lda, n, d->aexp, st);
       }
       if (launch_gemm_esg((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
-                          ldx, (double*)Y + c0 * ldy, ldy, d->xs, d->aexp, d->flags, d->err,
+                          ldx, (double*)Y + c0 * ldy, ldy, xs, d->aexp, flags, d->err,
                           st) != 0)
         return 2;
     } else if (d->dtype == 2 || d->dtype == 4)
       launch_dense_gemm_a32((const float*)d->A, d->lda, trans, n, w, (const double*)X + c0 * ldx,
-                            ldx, (double*)Y + c0 * ldy, ldy, d->flags, st);
+                            ldx, (double*)Y + c0 * ldy, ldy, flags, st);
     else if (d->dtype == 1 && gemm_tc_supported((const float*)d->A, d->lda, n)) {
       const int64_t need = 2 * gemm_tc_xs_elems(n, w);
-      if (need > d->xs_bytes) {
-        if (d->xs) cudaFree(d->xs);
-        d->xs = nullptr;
-        d->xs_bytes = 0;
-        if (cudaMalloc(&d->xs, (size_t)need) != cudaSuccess) return 3;
-        d->xs_bytes = need;
+      if (need > xs_bytes) {
+        if (xs) cudaFree(xs);
+        xs = nullptr;
+        xs_bytes = 0;
+        if (cudaMalloc(&xs, (size_t)need) != cudaSuccess) return 3;
+        xs_bytes = need;
       }
       if (launch_gemm_tc((const float*)d->A, d->lda, trans, n, w, (const float*)X + c0 * ldx,
-                         ldx, (float*)Y + c0 * ldy, ldy, d->xs, d->flags, d->err, st) != 0)
+                         ldx, (float*)Y + c0 * ldy, ldy, xs, flags, d->err, st) != 0)
         return 2;
     } else  // dtype 3, or a layout TMA cannot address: FP32 on the CUDA-core engine
       launch_dense_gemm<float>((const float*)d->A, d->lda, trans, n, w,
                                (const float*)X + c0 * ldx, ldx, (float*)Y + c0 * ldy, ldy,
-                               d->flags, st);
+                               flags, st);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+static int dense_cb(void* ctx, int trans, int64_t n, int64_t ncols, const void* X, int64_t ldx,
+                    void* Y, int64_t ldy, void* stream) {
+  return dense_slot_apply((hm_dense_ctx*)ctx, 0, trans, n, ncols, X, ldx, Y, ldy,
+                          (cudaStream_t)stream);
 }
 
 hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,
@@ -534,6 +545,8 @@ void hm_dense_operator_destroy(hm_operator* op) {
   if (d->tabP) cudaFree(d->tabP);
   if (d->flags) cudaFree(d->flags);
   if (d->xs) cudaFree(d->xs);
+  if (d->flags1) cudaFree(d->flags1);
+  if (d->xs1) cudaFree(d->xs1);
   if (d->err) cudaFree(d->err);
   if (d->aexp) cudaFree(d->aexp);
   delete d;
@@ -542,6 +555,16 @@ void hm_dense_operator_destroy(hm_operator* op) {
 }
 
 }  // extern "C"
+
+bool hm::library_operator(const hm_operator* op) {
+  return op && op->apply == dense_cb && op->ctx;
+}
+
+int hm::library_apply(const hm_operator* op, int slot, int trans, int64_t ncols, const void* X,
+                      int64_t ldx, void* Y, int64_t ldy, cudaStream_t st) {
+  if (!library_operator(op)) return 1;
+  return dense_slot_apply((hm_dense_ctx*)op->ctx, slot, trans, op->n, ncols, X, ldx, Y, ldy, st);
+}
 
 hm_status hm::dense_take_timeout(const hm_operator* op) {
   if (!op || op->apply != dense_cb || !op->ctx) return HM_OK;

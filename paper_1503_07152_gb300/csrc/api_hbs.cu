@@ -136,7 +136,6 @@ hm_status compress_hbs_t(Ctx<T>& c, HbsState<T>& s, T* D) {
   const int r = c.r;
   const int L = c.tree->L;
   const int nmax = (int)c.tree->nmax;
-  const bool bf16 = c.bf16;
   T* Unext = s.Ucur + N * r;  // two level buffers, swapped by pointer
   T* Vnext = s.Vcur + N * r;
   const int64_t rr = (int64_t)r * r;
@@ -145,10 +144,7 @@ hm_status compress_hbs_t(Ctx<T>& c, HbsState<T>& s, T* D) {
     const LevelPlan& lp = c.tree->plans[lv];
     const int pc = level == 0 ? r : 2 * r;
     mark(c, level, 0, HM_PHASE_SAMPLE);
-    launch_gauss_fill<T>(c.X, N, N, r, level, c.seed, bf16, c.tree->d_start, L, c.st);
-    HM_TRY(box(c, 0, c.X, c.S, r));
-    HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));
-    nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+    HM_TRY(sample_level(c, level));  // X = [Omega_2 | Omega_1], S = A X
     mark(c, level, 0, HM_PHASE_PEEL);
     HM_TRY(hbs_partial_apply(s, level, c.X, N, c.S, N, 2 * r, 0, (T)-1, c.st));
     // Y_loc = [Y(I_a, sample half), U_tau(J_a,:) diag(y_tau)] -> [U_a, y_a] = svd(Y_loc, r)
@@ -190,8 +186,7 @@ hm_status compress_hbs_t(Ctx<T>& c, HbsState<T>& s, T* D) {
     HM_TRY(check_launch("hbs level"));
   }
   mark(c, L, 0, HM_PHASE_SAMPLE);
-  launch_identity_probe<T>(c.XI, N, N, nmax, c.tree->d_start, L, c.st);
-  HM_TRY(box(c, 0, c.XI, c.YI, nmax));
+  HM_TRY(sample_identity(c));
   mark(c, L, 0, HM_PHASE_PEEL);
   HM_TRY(hbs_partial_apply(s, L, c.XI, N, c.YI, N, nmax, 0, (T)-1, c.st));
   mark(c, L, 0, HM_PHASE_BASES);
@@ -455,7 +450,7 @@ void hbs_free(hm_handle* h) {
 
 template <typename T>
 static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const hm_opts* o,
-                                    cudaStream_t st, hm_handle** out) {
+                                    cudaStream_t user_st, hm_handle** out) {
   const int r = opts_r(o);
   if (r > 64) {
     set_error("hm_compress_hbs: r must be at most 64 (2r-column panels)");
@@ -472,17 +467,18 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
   h->n = tree->n;
   h->L = tree->L;
   h->r = r;
-  hm_status s = tree_build(tree->n, tree->leaf, &h->tree);
+  Ctx<T> c;
+  c.op = op;
+  hm_status s = la_begin(c, o, user_st, true);
+  const cudaStream_t st = c.st;  // the compression's stream from here on
+  if (s == HM_OK) s = tree_build(tree->n, tree->leaf, &h->tree);
   if (s == HM_OK) s = tree_plans(&h->tree);
   if (s == HM_OK) s = tree_device(&h->tree, st);
   const int64_t N = tree->n;
   const int L = tree->L;
   const int nheap = 1 << (L + 1);
   const int64_t rr = (int64_t)r * r;
-  Ctx<T> c;
-  c.op = op;
   c.tree = &h->tree;
-  c.st = st;
   c.N = N;
   c.r = r;
   c.seed = o->seed;
@@ -541,6 +537,7 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
       s = hbsid_sweep<T>(c, hs, D, h);
     }
     mark(c, L, 0, -1);  // end of the last phase
+    if (s == HM_OK) s = la_join(c);
     cudaEventRecord(t1, st);
   }
   if (s == HM_OK) {
@@ -592,6 +589,7 @@ static hm_status compress_hbs_entry(const hm_operator* op, hm_tree* tree, const 
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   marks_finish(c, s == HM_OK ? h : nullptr);
+  la_end(c);
   ctx_free(c);
   if (rank_block) cudaFree(rank_block);
   if (sblk) cudaFree(sblk);

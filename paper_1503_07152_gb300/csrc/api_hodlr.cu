@@ -57,13 +57,17 @@ void marks_finish(Ctx<T>& c, hm_handle* h) {
 }
 
 template <typename T>
-hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols) {
+hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols, bool ahead) {
+  const cudaStream_t st = ahead ? c.la_st : c.st;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  cudaEventRecord(e0, c.st);
-  const int rc = c.op->apply(c.op->ctx, trans, c.N, ncols, X, c.N, Y, c.N, c.st);
-  cudaEventRecord(e1, c.st);
+  cudaEventRecord(e0, st);
+  // the library's own black boxes get the scratch slot of their stream
+  const int rc = library_operator(c.op)
+                     ? library_apply(c.op, ahead ? 1 : 0, trans, ncols, X, c.N, Y, c.N, st)
+                     : c.op->apply(c.op->ctx, trans, c.N, ncols, X, c.N, Y, c.N, st);
+  cudaEventRecord(e1, st);
   c.box_events.push_back({e0, e1});
   if (rc != 0) {
     set_error("black-box apply returned " + std::to_string(rc));
@@ -72,6 +76,115 @@ hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols) {
   if (trans) c.cols_At += ncols; else c.cols_A += ncols;
   ++c.launches;
   return check_launch("black-box apply");
+}
+
+template <typename T>
+hm_status la_begin(Ctx<T>& c, const hm_opts* o, cudaStream_t user_st, bool allowed) {
+  c.user_st = user_st;
+  c.st = user_st;
+  c.la = allowed && (o->lookahead == 1 || (o->lookahead == 0 && library_operator(c.op)));
+  if (!c.la) return HM_OK;
+  int least = 0, greatest = 0;
+  HM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  cudaStream_t main_st = nullptr;
+  HM_CUDA_TRY(cudaStreamCreateWithPriority(&main_st, cudaStreamNonBlocking, greatest));
+  c.st = main_st;
+  HM_CUDA_TRY(cudaStreamCreateWithPriority(&c.la_st, cudaStreamNonBlocking, least));
+  HM_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_ready, cudaEventDisableTiming));
+  HM_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_free, cudaEventDisableTiming));
+  HM_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_probe, cudaEventDisableTiming));
+  // both streams start after the work already queued on the caller's stream
+  HM_CUDA_TRY(cudaEventRecord(c.ev_free, user_st));
+  HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_free, 0));
+  HM_CUDA_TRY(cudaStreamWaitEvent(c.la_st, c.ev_free, 0));
+  return HM_OK;
+}
+
+template <typename T>
+hm_status la_join(Ctx<T>& c) {
+  if (!c.la) return HM_OK;
+  // every look-ahead product has been waited for on c.st (sample_level,
+  // sample_identity); c.st's end is the compression's end
+  HM_CUDA_TRY(cudaEventRecord(c.ev_ready, c.la_st));
+  HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_ready, 0));
+  HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));
+  HM_CUDA_TRY(cudaStreamWaitEvent(c.user_st, c.ev_free, 0));
+  return HM_OK;
+}
+
+template <typename T>
+void la_end(Ctx<T>& c) {
+  if (!c.la) return;
+  if (c.la_st) {
+    cudaStreamSynchronize(c.la_st);
+    cudaStreamDestroy(c.la_st);
+  }
+  if (c.st && c.st != c.user_st) {
+    cudaStreamSynchronize(c.st);
+    cudaStreamDestroy(c.st);
+  }
+  const cudaEvent_t evs[3] = {c.ev_ready, c.ev_free, c.ev_probe};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  c.la_st = nullptr;
+  c.ev_ready = c.ev_free = c.ev_probe = nullptr;
+  c.st = c.user_st;
+  c.la = false;
+}
+
+// The look-ahead stream computes level `level`'s test matrix and samples into
+// Xa, Sa once c.st has released them (ev_free).
+template <typename T>
+static hm_status la_issue(Ctx<T>& c, int level) {
+  const int64_t N = c.N;
+  const int r = c.r;
+  HM_CUDA_TRY(cudaStreamWaitEvent(c.la_st, c.ev_free, 0));
+  launch_gauss_fill<T>(c.Xa, N, N, r, level, c.seed, c.bf16, c.tree->d_start, c.tree->L,
+                       c.la_st);
+  HM_TRY(box(c, 0, c.Xa, c.Sa, r, true));                  // Y_1 = A Omega_2
+  HM_TRY(box(c, 0, c.Xa + N * r, c.Sa + N * r, r, true));  // Y_2 = A Omega_1
+  HM_CUDA_TRY(cudaEventRecord(c.ev_ready, c.la_st));
+  return HM_OK;
+}
+
+template <typename T>
+hm_status sample_level(Ctx<T>& c, int level) {
+  const int64_t N = c.N;
+  const int r = c.r;
+  const int L = c.tree->L;
+  if (!c.la) {
+    launch_gauss_fill<T>(c.X, N, N, r, level, c.seed, c.bf16, c.tree->d_start, L, c.st);
+    HM_TRY(box(c, 0, c.X, c.S, r));                  // Y_1 = A Omega_2
+    HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));  // Y_2 = A Omega_1
+  } else {
+    if (level == 0) HM_TRY(la_issue(c, 0));
+    HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_ready, 0));
+    std::swap(c.X, c.Xa);
+    std::swap(c.S, c.Sa);
+    // the previous level's buffers (now Xa, Sa) are free once c.st gets here
+    HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));
+    if (level + 1 < L) {
+      HM_TRY(la_issue(c, level + 1));
+    } else {
+      // the identity probe (XI, YI: buffers of its own) during the last level
+      launch_identity_probe<T>(c.XI, N, N, (int)c.tree->nmax, c.tree->d_start, L, c.la_st);
+      HM_TRY(box(c, 0, c.XI, c.YI, c.tree->nmax, true));
+      HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
+      c.probe_issued = true;
+    }
+  }
+  nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+  return HM_OK;
+}
+
+template <typename T>
+hm_status sample_identity(Ctx<T>& c) {
+  if (c.la && c.probe_issued) {
+    HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_probe, 0));
+    return HM_OK;
+  }
+  launch_identity_probe<T>(c.XI, c.N, c.N, (int)c.tree->nmax, c.tree->d_start, c.tree->L, c.st);
+  return box(c, 0, c.XI, c.YI, c.tree->nmax);
 }
 
 // S(:, 0:ncols) -= A^(level) X (or the transpose), node levels 1..level.
@@ -206,6 +319,10 @@ hm_status ctx_alloc(Ctx<T>& c, int pc_max, int64_t extra_cols) {
     c.eps_dev = a.take<double>(2);
     c.XI = a.take<T>(N * extra_cols);
     c.YI = a.take<T>(N * extra_cols);
+    if (c.la) {
+      c.Xa = a.take<T>(N * 2 * r);
+      c.Sa = a.take<T>(N * 2 * r);
+    }
   };
   HM_TRY(arena_alloc(&c.block, layout));
   HM_CUDA_TRY(cudaMemsetAsync(c.flags_dev, 0, 4 * sizeof(int32_t), c.st));
@@ -251,10 +368,7 @@ hm_status hodlr_stage_a(Ctx<T>& c, hm_handle* h, int level) {
   T* U = (T*)h->U;
   T* V = (T*)h->V;
   mark(c, level, 0, HM_PHASE_SAMPLE);
-  launch_gauss_fill<T>(c.X, N, N, r, level, c.seed, c.bf16, c.tree->d_start, L, c.st);
-  HM_TRY(box(c, 0, c.X, c.S, r));                      // Y_1 = A Omega_2
-  HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));      // Y_2 = A Omega_1
-  nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
+  HM_TRY(sample_level(c, level));  // X = [Omega_2 | Omega_1], S = A X
   mark(c, level, 0, HM_PHASE_PEEL);
   HM_TRY(hodlr_peel(c, U, V, level, c.X, c.S, 2 * r, 0, -1.0));
   mark(c, level, 0, HM_PHASE_BASES);
@@ -312,8 +426,7 @@ hm_status hodlr_leaves(Ctx<T>& c, hm_handle* h) {
   const int L = c.tree->L;
   const int nmax = (int)c.tree->nmax;
   mark(c, L, 0, HM_PHASE_SAMPLE);
-  launch_identity_probe<T>(c.XI, N, N, nmax, c.tree->d_start, L, c.st);
-  HM_TRY(box(c, 0, c.XI, c.YI, nmax));
+  HM_TRY(sample_identity(c));
   mark(c, L, 0, HM_PHASE_PEEL);
   HM_TRY(hodlr_peel(c, (T*)h->U, (T*)h->V, L, c.XI, c.YI, nmax, 0, -1.0));
   mark(c, L, 0, HM_PHASE_BASES);
@@ -433,7 +546,7 @@ namespace hm {
 // factors, context); t0 recorded on the compression's stream.
 template <typename T>
 hm_status hodlr_begin(HodlrRun<T>& R, const hm_operator* op, hm_tree* tree, const hm_opts* o,
-                      cudaStream_t st) {
+                      cudaStream_t user_st, bool lookahead_allowed) {
   const int r = opts_r(o);
   if (r > 128 || 2 * r > 256) {
     set_error("compress: r must be at most 128");
@@ -447,7 +560,11 @@ hm_status hodlr_begin(HodlrRun<T>& R, const hm_operator* op, hm_tree* tree, cons
   h->n = tree->n;
   h->L = tree->L;
   h->r = r;
-  hm_status s = tree_build(tree->n, tree->leaf, &h->tree);
+  Ctx<T>& c = R.c;
+  c.op = op;
+  hm_status s = la_begin(c, o, user_st, lookahead_allowed);
+  const cudaStream_t st = c.st;  // the compression's stream from here on
+  if (s == HM_OK) s = tree_build(tree->n, tree->leaf, &h->tree);
   if (s == HM_OK) s = tree_plans(&h->tree);
   if (s == HM_OK) s = tree_device(&h->tree, st);
   const int64_t N = tree->n;
@@ -455,10 +572,7 @@ hm_status hodlr_begin(HodlrRun<T>& R, const hm_operator* op, hm_tree* tree, cons
   if (s == HM_OK) s = device_alloc(&h->V, sizeof(T) * (size_t)tree->L * N * r);
   if (s == HM_OK)
     s = device_alloc(&h->D, sizeof(T) * ((size_t)1 << tree->L) * tree->nmax * tree->nmax);
-  Ctx<T>& c = R.c;
-  c.op = op;
   c.tree = &h->tree;
-  c.st = st;
   c.N = N;
   c.r = r;
   c.seed = o->seed;
@@ -495,6 +609,9 @@ hm_status hodlr_end(HodlrRun<T>& R, hm_status s, hm_handle** out) {
   const cudaStream_t st = c.st;
   if (s == HM_OK) {
     mark(c, tree->L, 0, -1);  // end of the last phase
+    s = la_join(c);
+  }
+  if (s == HM_OK) {
     cudaEventRecord(R.t1, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -553,6 +670,7 @@ hm_status hodlr_end(HodlrRun<T>& R, hm_status s, hm_handle** out) {
   if (R.t1) cudaEventDestroy(R.t1);
   R.t0 = R.t1 = nullptr;
   marks_finish(c, s == HM_OK ? h : nullptr);
+  la_end(c);
   ctx_free(c);
   if (R.rank_block) cudaFree(R.rank_block);
   R.rank_block = nullptr;
@@ -590,7 +708,12 @@ extern "C" hm_status hm_compress_hodlr(const hm_operator* op, const hm_tree* tre
 
 namespace hm {
 #define HM_INST(T)                                                                          \
-  template hm_status box<T>(Ctx<T>&, int, const T*, T*, int64_t);                           \
+  template hm_status box<T>(Ctx<T>&, int, const T*, T*, int64_t, bool);                     \
+  template hm_status la_begin<T>(Ctx<T>&, const hm_opts*, cudaStream_t, bool);              \
+  template hm_status la_join<T>(Ctx<T>&);                                                   \
+  template void la_end<T>(Ctx<T>&);                                                         \
+  template hm_status sample_level<T>(Ctx<T>&, int);                                         \
+  template hm_status sample_identity<T>(Ctx<T>&);                                           \
   template hm_status panel_svd<T>(Ctx<T>&, int, const T*, int, int, int, bool, T*, bool,    \
                                   int32_t*);                                                \
   template hm_status ctx_alloc<T>(Ctx<T>&, int, int64_t);                                   \
@@ -602,7 +725,7 @@ namespace hm {
   template hm_status panel_post<T>(Ctx<T>&, int, const T*, int, int, int, bool, T*, bool,   \
                                    int32_t*);                                               \
   template hm_status hodlr_begin<T>(HodlrRun<T>&, const hm_operator*, hm_tree*,             \
-                                    const hm_opts*, cudaStream_t);                          \
+                                    const hm_opts*, cudaStream_t, bool);                    \
   template hm_status hodlr_stage_a<T>(Ctx<T>&, hm_handle*, int);                            \
   template hm_status hodlr_stage_b<T>(Ctx<T>&, hm_handle*, int);                            \
   template hm_status hodlr_stage_c<T>(Ctx<T>&, hm_handle*, int);                            \

@@ -39,6 +39,20 @@ struct Ctx {
   bool profile = false;
   int side = 0;  // side of the panel being factored (0: A samples, 1: A^T samples)
   std::vector<Mark> marks;
+  // Look-ahead sampling (sample_level): the A-side test matrix of a level is a
+  // fresh Gaussian block, so its black-box product does not depend on the
+  // levels before it.  With `la` set, st is a high-priority stream of the
+  // compression's own that joins the caller's stream at both ends, and la_st a
+  // low-priority stream on which the next level's samples A Omega (and, after
+  // the last level, the identity probe) are computed into Xa, Sa (XI, YI) while
+  // st factors the current level's panels.  ev_ready: the look-ahead samples
+  // are written; ev_free: st is done with the buffers the look-ahead overwrites;
+  // ev_probe: the identity probe's samples are written.
+  bool la = false;
+  cudaStream_t user_st = nullptr, la_st = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_free = nullptr, ev_probe = nullptr;
+  T *Xa = nullptr, *Sa = nullptr;
+  bool probe_issued = false;
 };
 
 // Records the start of a phase on the compression's stream (no-op unless
@@ -51,8 +65,31 @@ template <typename T>
 void marks_finish(Ctx<T>& c, hm_handle* h);
 bool profiling_on();
 
+// One black-box product Y = op(A) X (ncols columns) on the compression's
+// stream, or on the look-ahead stream when `ahead` is set.
 template <typename T>
-hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols);
+hm_status box(Ctx<T>& c, int trans, const T* X, T* Y, int64_t ncols, bool ahead = false);
+// Look-ahead set-up (before ctx_alloc): decides whether the compression samples
+// one level ahead (o->lookahead: 0 = for the library's own black boxes, 1 =
+// always, -1 = never; `allowed` false turns it off) and, if so, creates the two
+// streams and makes them wait for the work queued on `user_st`.  Sets c.st.
+template <typename T>
+hm_status la_begin(Ctx<T>& c, const hm_opts* o, cudaStream_t user_st, bool allowed);
+// Makes the caller's stream wait for everything the compression enqueued
+// (call after the last launch on c.st; no-op without look-ahead).
+template <typename T>
+hm_status la_join(Ctx<T>& c);
+// Releases the look-ahead streams and events (after c.st has been synchronized
+// or on failure; waits for the look-ahead stream first).
+template <typename T>
+void la_end(Ctx<T>& c);
+// Leaves the level's test matrix in c.X (both halves, N x 2r) and its samples
+// A X in c.S on c.st, computed there or taken from the look-ahead stream.
+template <typename T>
+hm_status sample_level(Ctx<T>& c, int level);
+// Leaves the identity probe in c.XI and A XI in c.YI on c.st.
+template <typename T>
+hm_status sample_identity(Ctx<T>& c);
 template <typename T>
 hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
                     T* Q, bool want_m, int32_t* rank_lv);
@@ -87,7 +124,7 @@ struct HodlrRun {
 // failure destroys the handle).
 template <typename T>
 hm_status hodlr_begin(HodlrRun<T>& R, const hm_operator* op, hm_tree* tree, const hm_opts* o,
-                      cudaStream_t st);
+                      cudaStream_t st, bool lookahead_allowed = true);
 template <typename T>
 hm_status hodlr_stage_a(Ctx<T>& c, hm_handle* h, int level);
 template <typename T>

@@ -39,6 +39,14 @@ long long wait_limit();
 // its GEMMs raise when a bounded wait gave up (HM_ETIMEOUT if it was set).
 // Other black boxes: HM_OK.  Synchronous (the caller has synchronized).
 hm_status dense_take_timeout(const hm_operator* op);
+// True for the black boxes the library makes itself (hm_dense_operator_create,
+// hm_log_kernel_operator_create): they enqueue on the stream they are given and
+// keep separate scratch per slot.
+bool library_operator(const hm_operator* op);
+// The product of a library black box with the scratch of `slot` (0 or 1); the
+// callback's return convention (0 = enqueued).
+int library_apply(const hm_operator* op, int slot, int trans, int64_t ncols, const void* X,
+                  int64_t ldx, void* Y, int64_t ldy, cudaStream_t st);
 // Process-wide count of kernels launched by the library (all devices).
 void count_launches(int n);
 
@@ -335,10 +343,16 @@ struct hm_dense_ctx {
   const void* A = nullptr;
   int64_t n = 0, lda = 0;
   int32_t dtype = 0;
+  // Per-call scratch, one set per slot: slot 0 serves hm_dense_apply and the
+  // callback, slot 1 the look-ahead stream of a compression, so that the two
+  // products of one compression that overlap on the GPU never share scratch.
   uint8_t* flags = nullptr;  // zero-tile flags scratch
   int64_t flags_bytes = 0;
   void* xs = nullptr;        // split copy of X for the tensor-core engine
   int64_t xs_bytes = 0;
+  uint8_t* flags1 = nullptr;  // slot 1 (allocated on its first use)
+  void* xs1 = nullptr;
+  int64_t xs1_bytes = 0;
   int* err = nullptr;        // device flag raised by a kernel that gave up waiting
   int* aexp = nullptr;       // dtype 4 / 5: row (then column) exponents of A per 256-wide window
   float* tabS = nullptr;     // dtype 5 (matrix-free log kernel): S[|i - j|] and P[i + j]
