@@ -130,20 +130,31 @@ void la_end(Ctx<T>& c) {
   c.ev_ready = c.ev_free = c.ev_probe = nullptr;
   c.st = c.user_st;
   c.la = false;
+  c.la_pending = -1;
 }
 
-// The look-ahead stream computes level `level`'s test matrix and samples into
-// Xa, Sa once c.st has released them (ev_free).
 template <typename T>
-static hm_status la_issue(Ctx<T>& c, int level) {
+hm_status la_release(Ctx<T>& c) {
+  if (!c.la || c.la_pending < 0) return HM_OK;
   const int64_t N = c.N;
   const int r = c.r;
+  const int L = c.tree->L;
+  const int lv = c.la_pending;
+  c.la_pending = -1;
+  // c.st has enqueued everything before this point, the last use of Xa, Sa included
+  HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));
   HM_CUDA_TRY(cudaStreamWaitEvent(c.la_st, c.ev_free, 0));
-  launch_gauss_fill<T>(c.Xa, N, N, r, level, c.seed, c.bf16, c.tree->d_start, c.tree->L,
-                       c.la_st);
-  HM_TRY(box(c, 0, c.Xa, c.Sa, r, true));                  // Y_1 = A Omega_2
-  HM_TRY(box(c, 0, c.Xa + N * r, c.Sa + N * r, r, true));  // Y_2 = A Omega_1
-  HM_CUDA_TRY(cudaEventRecord(c.ev_ready, c.la_st));
+  if (lv < L) {
+    launch_gauss_fill<T>(c.Xa, N, N, r, lv, c.seed, c.bf16, c.tree->d_start, L, c.la_st);
+    HM_TRY(box(c, 0, c.Xa, c.Sa, r, true));                  // Y_1 = A Omega_2
+    HM_TRY(box(c, 0, c.Xa + N * r, c.Sa + N * r, r, true));  // Y_2 = A Omega_1
+    HM_CUDA_TRY(cudaEventRecord(c.ev_ready, c.la_st));
+  } else {  // the identity probe (XI, YI: buffers of its own)
+    launch_identity_probe<T>(c.XI, N, N, (int)c.tree->nmax, c.tree->d_start, L, c.la_st);
+    HM_TRY(box(c, 0, c.XI, c.YI, c.tree->nmax, true));
+    HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
+    c.probe_issued = true;
+  }
   return HM_OK;
 }
 
@@ -157,21 +168,12 @@ hm_status sample_level(Ctx<T>& c, int level) {
     HM_TRY(box(c, 0, c.X, c.S, r));                  // Y_1 = A Omega_2
     HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));  // Y_2 = A Omega_1
   } else {
-    if (level == 0) HM_TRY(la_issue(c, 0));
+    if (level == 0) c.la_pending = 0;
+    HM_TRY(la_release(c));  // level 0, or a release point that was not reached
     HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_ready, 0));
     std::swap(c.X, c.Xa);
     std::swap(c.S, c.Sa);
-    // the previous level's buffers (now Xa, Sa) are free once c.st gets here
-    HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));
-    if (level + 1 < L) {
-      HM_TRY(la_issue(c, level + 1));
-    } else {
-      // the identity probe (XI, YI: buffers of its own) during the last level
-      launch_identity_probe<T>(c.XI, N, N, (int)c.tree->nmax, c.tree->d_start, L, c.la_st);
-      HM_TRY(box(c, 0, c.XI, c.YI, c.tree->nmax, true));
-      HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
-      c.probe_issued = true;
-    }
+    c.la_pending = level + 1;  // released from panel_qr (level + 1 == L: the probe)
   }
   nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
   return HM_OK;
@@ -179,6 +181,7 @@ hm_status sample_level(Ctx<T>& c, int level) {
 
 template <typename T>
 hm_status sample_identity(Ctx<T>& c) {
+  HM_TRY(la_release(c));
   if (c.la && c.probe_issued) {
     HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_probe, 0));
     return HM_OK;
@@ -239,6 +242,9 @@ hm_status panel_qr(Ctx<T>& c, int lv, const T* P, int pc) {
     else
       launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rd > 0 ? 1 : 0, P, N, pc,
                      c.Rw, c.st);
+    // the merges and the SVD that follow leave most SMs idle at the coarse
+    // levels: the next level's look-ahead product runs beside them
+    if (rd == 0 && c.side == 0) HM_TRY(la_release(c));
   }
   mark(c, lv - 1, c.side, HM_PHASE_SVD);
   if (sizeof(T) == 8 && c.bf16)  // HM_A32: the FP64 phases in double-float
@@ -714,6 +720,7 @@ namespace hm {
   template void la_end<T>(Ctx<T>&);                                                         \
   template hm_status sample_level<T>(Ctx<T>&, int);                                         \
   template hm_status sample_identity<T>(Ctx<T>&);                                           \
+  template hm_status la_release<T>(Ctx<T>&);                                                \
   template hm_status panel_svd<T>(Ctx<T>&, int, const T*, int, int, int, bool, T*, bool,    \
                                   int32_t*);                                                \
   template hm_status ctx_alloc<T>(Ctx<T>&, int, int64_t);                                   \

@@ -43,16 +43,22 @@ struct Ctx {
   // fresh Gaussian block, so its black-box product does not depend on the
   // levels before it.  With `la` set, st is a high-priority stream of the
   // compression's own that joins the caller's stream at both ends, and la_st a
-  // low-priority stream on which the next level's samples A Omega (and, after
+  // low-priority stream on which the next level's samples A Omega (and, during
   // the last level, the identity probe) are computed into Xa, Sa (XI, YI) while
-  // st factors the current level's panels.  ev_ready: the look-ahead samples
-  // are written; ev_free: st is done with the buffers the look-ahead overwrites;
-  // ev_probe: the identity probe's samples are written.
+  // st factors the current level's panels.  The look-ahead product of a level
+  // is released (la_release) once st has launched the first TSQR round of the
+  // current level's A-side panel, the last wide launch before the per-node
+  // phases that leave most SMs idle.  ev_ready: the look-ahead samples are
+  // written; ev_free: st has reached the release point (and is done with the
+  // buffers the look-ahead overwrites); ev_probe: the identity probe's samples
+  // are written.  la_pending: the level whose samples are released next (L:
+  // the identity probe; -1: none).
   bool la = false;
   cudaStream_t user_st = nullptr, la_st = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_free = nullptr, ev_probe = nullptr;
   T *Xa = nullptr, *Sa = nullptr;
   bool probe_issued = false;
+  int la_pending = -1;
 };
 
 // Records the start of a phase on the compression's stream (no-op unless
@@ -90,6 +96,10 @@ hm_status sample_level(Ctx<T>& c, int level);
 // Leaves the identity probe in c.XI and A XI in c.YI on c.st.
 template <typename T>
 hm_status sample_identity(Ctx<T>& c);
+// Starts the pending look-ahead product on la_st after the work enqueued on
+// c.st so far (no-op without look-ahead or when nothing is pending).
+template <typename T>
+hm_status la_release(Ctx<T>& c);
 template <typename T>
 hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
                     T* Q, bool want_m, int32_t* rank_lv);
