@@ -474,11 +474,10 @@ hm_status hm_hodlr_factored_apply(const hm_tree* tree, int32_t k, const float* U
  * pool at all.
  *  - Scratch: a fixed 8 MiB buffer compiled into the library (reserved on every
  *    device where the library's device code is loaded).  A call needs
- *    4 * (k * (c + 2^(L+1)) + 2^(L+1)) bytes, c = the number of 256-row chunks
- *    over all nodes of levels 1..L (about L * N / 256); larger requests return
+ *    4 * k * (c + 2^(L+1)) bytes, c = the number of 256-row chunks over all
+ *    nodes of levels 1..L (about L * N / 256); larger requests return
  *    HM_EINVAL naming the size, before anything is launched.
- *  - The per-node completion counters in the scratch are cleared by each call
- *    (a memset on the stream, no allocation); every other element a call reads
+ *  - Nothing in the scratch needs to start at zero: every element a call reads
  *    is written earlier in the same call.
  *  - All calls on one device share the one buffer: two calls whose work may
  *    overlap (different streams, or different host threads, without ordering

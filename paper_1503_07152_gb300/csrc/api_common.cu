@@ -220,8 +220,6 @@ static void fact_plan_host(hm_tree* t) {
   }
   t->fbegin[nn] = (int32_t)t->fchunks.size();
   t->n_fchunks = (int)t->fchunks.size();
-  t->fvec4 = true;
-  for (const FactChunk& c : t->fchunks) t->fvec4 = t->fvec4 && c.r0 % 4 == 0;
 }
 
 hm_status tree_plans(hm_tree* t) {

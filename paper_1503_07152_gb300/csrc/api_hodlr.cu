@@ -131,29 +131,41 @@ void la_end(Ctx<T>& c) {
   c.st = c.user_st;
   c.la = false;
   c.la_pending = -1;
+  c.la_part = 0;
 }
 
 template <typename T>
-hm_status la_release(Ctx<T>& c) {
+hm_status la_release(Ctx<T>& c, int part) {
   if (!c.la || c.la_pending < 0) return HM_OK;
   const int64_t N = c.N;
   const int r = c.r;
   const int L = c.tree->L;
   const int lv = c.la_pending;
-  c.la_pending = -1;
-  // c.st has enqueued everything before this point, the last use of Xa, Sa included
-  HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));
-  HM_CUDA_TRY(cudaStreamWaitEvent(c.la_st, c.ev_free, 0));
-  if (lv < L) {
+  // a level's two half-operator products go out one per side of the current
+  // level (each fits beside one side's merges and SVD); the probe goes out whole
+  if (c.la_part == 0 && (part == 0 || part == 2)) {
+    // c.st has enqueued everything before this point, the last use of Xa, Sa included
+    HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));
+    HM_CUDA_TRY(cudaStreamWaitEvent(c.la_st, c.ev_free, 0));
+    if (lv == L) {  // the identity probe (XI, YI: buffers of its own)
+      launch_identity_probe<T>(c.XI, N, N, (int)c.tree->nmax, c.tree->d_start, L, c.la_st);
+      HM_TRY(box(c, 0, c.XI, c.YI, c.tree->nmax, true));
+      HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
+      c.probe_issued = true;
+      c.la_pending = -1;
+      return HM_OK;
+    }
     launch_gauss_fill<T>(c.Xa, N, N, r, lv, c.seed, c.bf16, c.tree->d_start, L, c.la_st);
-    HM_TRY(box(c, 0, c.Xa, c.Sa, r, true));                  // Y_1 = A Omega_2
+    HM_TRY(box(c, 0, c.Xa, c.Sa, r, true));  // Y_1 = A Omega_2
+    c.la_part = 1;
+  }
+  if (c.la_part == 1 && (part == 1 || part == 2)) {
+    HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));  // the release point of this half
+    HM_CUDA_TRY(cudaStreamWaitEvent(c.la_st, c.ev_free, 0));
     HM_TRY(box(c, 0, c.Xa + N * r, c.Sa + N * r, r, true));  // Y_2 = A Omega_1
     HM_CUDA_TRY(cudaEventRecord(c.ev_ready, c.la_st));
-  } else {  // the identity probe (XI, YI: buffers of its own)
-    launch_identity_probe<T>(c.XI, N, N, (int)c.tree->nmax, c.tree->d_start, L, c.la_st);
-    HM_TRY(box(c, 0, c.XI, c.YI, c.tree->nmax, true));
-    HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
-    c.probe_issued = true;
+    c.la_part = 0;
+    c.la_pending = -1;
   }
   return HM_OK;
 }
@@ -169,7 +181,7 @@ hm_status sample_level(Ctx<T>& c, int level) {
     HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));  // Y_2 = A Omega_1
   } else {
     if (level == 0) c.la_pending = 0;
-    HM_TRY(la_release(c));  // level 0, or a release point that was not reached
+    HM_TRY(la_release(c, 2));  // level 0, or release points that were not reached
     HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_ready, 0));
     std::swap(c.X, c.Xa);
     std::swap(c.S, c.Sa);
@@ -181,7 +193,7 @@ hm_status sample_level(Ctx<T>& c, int level) {
 
 template <typename T>
 hm_status sample_identity(Ctx<T>& c) {
-  HM_TRY(la_release(c));
+  HM_TRY(la_release(c, 2));
   if (c.la && c.probe_issued) {
     HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_probe, 0));
     return HM_OK;
@@ -243,8 +255,8 @@ hm_status panel_qr(Ctx<T>& c, int lv, const T* P, int pc) {
       launch_tsqr<T>(lp.d_rounds[rd], (int)lp.tsqr_rounds[rd].size(), rd > 0 ? 1 : 0, P, N, pc,
                      c.Rw, c.st);
     // the merges and the SVD that follow leave most SMs idle at the coarse
-    // levels: the next level's look-ahead product runs beside them
-    if (rd == 0 && c.side == 0) HM_TRY(la_release(c));
+    // levels: a look-ahead product runs beside them
+    if (rd == 0) HM_TRY(la_release(c, c.side));
   }
   mark(c, lv - 1, c.side, HM_PHASE_SVD);
   if (sizeof(T) == 8 && c.bf16)  // HM_A32: the FP64 phases in double-float
@@ -720,7 +732,7 @@ namespace hm {
   template void la_end<T>(Ctx<T>&);                                                         \
   template hm_status sample_level<T>(Ctx<T>&, int);                                         \
   template hm_status sample_identity<T>(Ctx<T>&);                                           \
-  template hm_status la_release<T>(Ctx<T>&);                                                \
+  template hm_status la_release<T>(Ctx<T>&, int);                                           \
   template hm_status panel_svd<T>(Ctx<T>&, int, const T*, int, int, int, bool, T*, bool,    \
                                   int32_t*);                                                \
   template hm_status ctx_alloc<T>(Ctx<T>&, int, int64_t);                                   \

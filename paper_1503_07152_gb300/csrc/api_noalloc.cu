@@ -35,11 +35,12 @@ extern "C" hm_status hm_hodlr_factored_apply_noalloc(const hm_tree* tree, int32_
     set_error("hm_hodlr_factored_apply_noalloc: need tree (L >= 1), 1 <= k <= 64, U, V, D, x, y");
     return HM_EINVAL;
   }
-  // partial projections (one row of k per 256-row chunk of every node), the
-  // coefficients (k per node) and one counter per node, as laid out by the
-  // shared launcher, which also clears the counters on the stream (hm_tree_create
-  // builds the chunk list, so the size is exact here)
-  const size_t need = factored_apply_scratch_bytes(tree, k);
+  // partial projections (one row of k per 256-row chunk of every node) and the
+  // coefficients (k per node), as laid out by the shared launcher
+  // (hm_tree_create builds the chunk list, so n_fchunks is exact here)
+  const size_t nodes = (size_t)1 << (tree->L + 1);
+  const size_t chunks = (size_t)tree->n_fchunks;
+  const size_t need = sizeof(float) * (chunks * (size_t)k + nodes * (size_t)k);
   if (need > kNoallocScratchBytes) {
     set_error("hm_hodlr_factored_apply_noalloc: this tree and k need " + std::to_string(need) +
               " bytes of scratch; the static buffer holds " +

@@ -45,20 +45,23 @@ struct Ctx {
   // compression's own that joins the caller's stream at both ends, and la_st a
   // low-priority stream on which the next level's samples A Omega (and, during
   // the last level, the identity probe) are computed into Xa, Sa (XI, YI) while
-  // st factors the current level's panels.  The look-ahead product of a level
-  // is released (la_release) once st has launched the first TSQR round of the
-  // current level's A-side panel, the last wide launch before the per-node
-  // phases that leave most SMs idle.  ev_ready: the look-ahead samples are
-  // written; ev_free: st has reached the release point (and is done with the
-  // buffers the look-ahead overwrites); ev_probe: the identity probe's samples
-  // are written.  la_pending: the level whose samples are released next (L:
-  // the identity probe; -1: none).
+  // st factors the current level's panels.  The look-ahead test matrix and its
+  // first half-operator product are released (la_release) once st has launched
+  // the first TSQR round of the current level's A-side panel, the last wide
+  // launch before the per-node phases that leave most SMs idle; its second
+  // half-operator product once st has launched the first TSQR round of the
+  // A^T-side panel.  ev_ready: the
+  // look-ahead samples are written; ev_free: st has reached a release point
+  // (and is done with the buffers the look-ahead overwrites); ev_probe: the
+  // identity probe's samples are written.  la_pending: the level whose samples
+  // are released next (L: the identity probe; -1: none); la_part: how many of
+  // its two halves are out.
   bool la = false;
   cudaStream_t user_st = nullptr, la_st = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_free = nullptr, ev_probe = nullptr;
   T *Xa = nullptr, *Sa = nullptr;
   bool probe_issued = false;
-  int la_pending = -1;
+  int la_pending = -1, la_part = 0;
 };
 
 // Records the start of a phase on the compression's stream (no-op unless
@@ -96,10 +99,12 @@ hm_status sample_level(Ctx<T>& c, int level);
 // Leaves the identity probe in c.XI and A XI in c.YI on c.st.
 template <typename T>
 hm_status sample_identity(Ctx<T>& c);
-// Starts the pending look-ahead product on la_st after the work enqueued on
-// c.st so far (no-op without look-ahead or when nothing is pending).
+// Starts pending look-ahead products on la_st after the work enqueued on c.st
+// so far: part 0 the test matrix and the first half-operator product (or the
+// whole identity probe), part 1 the second half, part 2 whatever is pending
+// (no-op without look-ahead or when nothing is pending).
 template <typename T>
-hm_status la_release(Ctx<T>& c);
+hm_status la_release(Ctx<T>& c, int part);
 template <typename T>
 hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
                     T* Q, bool want_m, int32_t* rank_lv);

@@ -279,8 +279,6 @@ struct FactChunk {
 struct hm_tree;
 namespace hm {
 size_t factored_scratch_bytes(const hm_tree* t, int k);
-// Scratch bytes launch_factored_apply uses (partials, node sums, counters).
-size_t factored_apply_scratch_bytes(const hm_tree* t, int k);
 // Checks that the per-leaf kernels' shared memory fits the device (HM_EINVAL
 // naming the sizes otherwise) and raises their limit once per device.
 hm_status factored_check(const hm_tree* t, bool adjoint);
@@ -339,7 +337,6 @@ struct hm_tree {
   const hm::FactChunk* d_fchunks = nullptr;
   const int32_t* d_fbegin = nullptr;
   int n_fchunks = 0;
-  bool fvec4 = false;  // every chunk starts on a multiple of four rows
 };
 
 struct hm_dense_ctx {

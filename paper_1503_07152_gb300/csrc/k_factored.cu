@@ -19,104 +19,72 @@ namespace {
 
 constexpr int kMaxK = 64;
 
-// Four consecutive rows of a column: one 16-byte load when `full` (the rows
-// lie inside the chunk and are 16-byte aligned), else masked scalar loads.
-__device__ __forceinline__ float4 rows4(const float* __restrict__ p, int64_t row0, int64_t r1,
-                                        bool full) {
-  if (full) return __ldg(reinterpret_cast<const float4*>(p + row0));
-  float4 v;
-  v.x = row0 < r1 ? p[row0] : 0.f;
-  v.y = row0 + 1 < r1 ? p[row0 + 1] : 0.f;
-  v.z = row0 + 2 < r1 ? p[row0 + 2] : 0.f;
-  v.w = row0 + 3 < r1 ? p[row0 + 3] : 0.f;
-  return v;
-}
-
-// partial[chunk][0:k] = V_j(rows)^T x(rows); with the second operand pair (the
-// two-call adjoint) partial[chunk][k:2k] = U_j(rows)^T res(rows).  Warp w takes
-// half (w & 1) of the chunk's 256 rows and the columns w/2, w/2 + 4, ...: lane l
-// reads rows 4l .. 4l + 3 of its half of each column as one float4 (512
-// contiguous bytes per warp and column, every column's load in flight at once),
-// forms the 4-term dot product with the same rows of the vector, and the warp
-// adds its 32 lane sums by butterfly shuffles; the two halves are added in
-// shared memory.
-//
-// The per-node sums out[node][0:width] (width = npair k) are formed by the last
-// block of each node to finish (cnt[node] counts the node's finished chunks;
-// it starts at zero and the last block sets it back to zero): it adds the
-// node's chunk partials with 256 / width thread groups (group q takes chunks
-// q, q + groups, ...) and then the group sums in group order, a fixed order.
-// KM: the largest k the launch serves (32 or 64), which sizes the register
-// arrays.
-template <int KM>
+// partial[chunk][0:k] = V_j(rows)^T x(rows); with second operand pair for the
+// adjoint: partial[chunk][k:2k] = U_j(rows)^T res(rows).  Thread t loads row t's k
+// factor entries at once (independent, coalesced loads), the products go to
+// shared memory (row-major, stride k + 1: conflict-free both ways), thread
+// (col, part) sums its 32-row part of a column, and the 8 parts are added.
 __global__ __launch_bounds__(256) void k_fact_partial(const FactChunk* __restrict__ ch,
                                                       int64_t n, int k,
                                                       const float* __restrict__ A0,
                                                       const float* __restrict__ v0,
                                                       const float* __restrict__ A1,
-                                                      const float* __restrict__ v1, int vec4,
-                                                      float* __restrict__ partial,
-                                                      const int32_t* __restrict__ fbegin,
-                                                      int32_t* __restrict__ cnt,
-                                                      float* __restrict__ out) {
-  __shared__ float red[2][2 * kMaxK];
-  __shared__ float sred[256];
-  __shared__ int s_last;
+                                                      const float* __restrict__ v1,
+                                                      float* __restrict__ partial) {
+  extern __shared__ float prod[];  // [256][k + 1]
+  __shared__ float red[8][2 * kMaxK];
   const FactChunk c = ch[blockIdx.x];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, half = w & 1;
+  const int tid = threadIdx.x;
+  const int ldp = k + 1;
+  const int64_t row = c.r0 + tid;
+  const bool live = row < c.r1;
   const int npair = A1 ? 2 : 1;
-  const int width = npair * k;
-  const int64_t row0 = c.r0 + half * 128 + lane * 4;
-  const bool full = vec4 && row0 + 3 < c.r1;
+  const int cl = tid & 31, part = tid >> 5;
   for (int p = 0; p < npair; ++p) {
     const float* A = (p == 0 ? A0 : A1) + (int64_t)(c.level - 1) * n * k;
-    const float4 xv = rows4(p == 0 ? v0 : v1, row0, c.r1, full);
-    float acc[KM / 4];
+    const float xv = live ? (p == 0 ? v0 : v1)[row] : 0.f;
+#pragma unroll 8
+    for (int col = 0; col < k; ++col)
+      prod[tid * ldp + col] = live ? A[row + (int64_t)col * n] * xv : 0.f;
+    __syncthreads();
+    for (int col = cl; col < k; col += 32) {
+      float s = 0.f;
 #pragma unroll
-    for (int i = 0; i < KM / 4; ++i) {
-      const int col = (w >> 1) + 4 * i;
-      float sum = 0.f;
-      if (col < k) {  // uniform over the warp
-        const float4 a = rows4(A + (int64_t)col * n, row0, c.r1, full);
-        sum = fmaf(a.w, xv.w, fmaf(a.z, xv.z, fmaf(a.y, xv.y, a.x * xv.x)));
-      }
-      acc[i] = sum;
+      for (int i = 0; i < 32; ++i) s += prod[(part * 32 + i) * ldp + col];
+      red[part][p * k + col] = s;
     }
-#pragma unroll
-    for (int i = 0; i < KM / 4; ++i) {
-      if ((w >> 1) + 4 * i >= k) break;  // uniform over the warp
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
-      if (lane == 0) red[half][p * k + (w >> 1) + 4 * i] = acc[i];
-    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = tid; e < width; e += 256)
-    partial[(int64_t)blockIdx.x * width + e] = red[0][e] + red[1][e];
-  // per-node sums by the node's last block
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    const int nch = fbegin[c.node + 1] - fbegin[c.node];
-    s_last = atomicAdd(&cnt[c.node], 1) == nch - 1;
+  for (int e = tid; e < npair * k; e += 256) {
+    float s = 0.f;
+    for (int w = 0; w < 8; ++w) s += red[w][e];
+    partial[(int64_t)blockIdx.x * npair * k + e] = s;
   }
-  __syncthreads();
-  if (!s_last) return;  // uniform over the block
-  __threadfence();
-  const int c0 = fbegin[c.node], c1 = fbegin[c.node + 1];
+}
+
+// out[node][e] = sum over the node's chunks (heap ids 2 .. 2^(L+1)-1).  The
+// 256 threads form 256 / width groups; group q sums chunks q, q + groups, ...
+// and the group sums are added in group order (deterministic).  width <= 128.
+__global__ __launch_bounds__(256) void k_fact_reduce(const float* __restrict__ partial,
+                                                     const int32_t* __restrict__ fbegin,
+                                                     int width, int nnodes_total,
+                                                     float* __restrict__ out) {
+  __shared__ float sred[256];
+  const int node = 2 + blockIdx.x;
+  if (node >= nnodes_total) return;  // uniform over the block
+  const int c0 = fbegin[node], c1 = fbegin[node + 1];
   const int groups = 256 / width;
-  const int e = tid % width, q = tid / width;
-  float sum = 0.f;
+  const int t = threadIdx.x, e = t % width, q = t / width;
+  float s = 0.f;
   if (q < groups)
-    for (int cc = c0 + q; cc < c1; cc += groups) sum += __ldcg(&partial[(int64_t)cc * width + e]);
-  sred[tid] = sum;
+    for (int c = c0 + q; c < c1; c += groups) s += partial[(int64_t)c * width + e];
+  sred[t] = s;
   __syncthreads();
-  if (tid < width) {
+  if (t < width) {
     float tot = 0.f;
-    for (int g = 0; g < groups; ++g) tot += sred[g * width + tid];
-    out[(int64_t)c.node * width + tid] = tot;
+    for (int g = 0; g < groups; ++g) tot += sred[g * width + t];
+    out[(int64_t)node * width + t] = tot;
   }
-  if (tid == 0) cnt[c.node] = 0;
 }
 
 // y(I_leaf) = sum_j Uex_j(I_leaf) coef[sib(anc_j)] + op(D_leaf) x(I_leaf); with
@@ -246,6 +214,13 @@ __global__ __launch_bounds__(256) void k_fact_adjoint(
 
 }  // namespace
 
+// dynamic shared memory of k_fact_partial (66.5 KB at k = 64: limit raised once)
+static size_t fact_partial_smem(int k) {
+  static std::atomic<uint32_t> done{0};
+  raise_smem_limit((const void*)k_fact_partial, done);
+  return sizeof(float) * 256 * (size_t)(k + 1);
+}
+
 // dynamic shared memory of the per-leaf kernels: the sibling coefficients of
 // every level plus the leaf's slices of x (and res, D^T res); grows with n_max
 static size_t fact_leaf_smem(const hm_tree* t, bool adjoint) {
@@ -271,59 +246,23 @@ hm_status factored_check(const hm_tree* t, bool adjoint) {
   return HM_OK;
 }
 
-// The float4 path of k_fact_partial needs every chunk to start on a multiple
-// of four rows, n a multiple of four (so every column starts 16-byte aligned)
-// and 16-byte aligned operands.
-static int fact_vec4(const hm_tree* t, const float* A0, const float* v0, const float* A1,
-                     const float* v1) {
-  auto al = [](const float* p) { return p == nullptr || ((uintptr_t)p & 15) == 0; };
-  return t->fvec4 && t->n % 4 == 0 && al(A0) && al(v0) && al(A1) && al(v1) ? 1 : 0;
-}
-
-// Scratch layout shared by the launchers: chunk partials, node sums, then one
-// counter per heap id (zeroed here on the stream: the pass's last blocks reset
-// their counters, so one clear serves every pass of a call).
-static int32_t* fact_counters(const hm_tree* t, float* after, cudaStream_t st) {
-  int32_t* cnt = reinterpret_cast<int32_t*>(after);
-  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)1 << (t->L + 1)), st);
-  return cnt;
-}
-
-static void launch_fact_partial(const hm_tree* t, int k, const float* A0, const float* v0,
-                                const float* A1, const float* v1, float* partial, int32_t* cnt,
-                                float* out, cudaStream_t st) {
-  const int vec4 = fact_vec4(t, A0, v0, A1, v1);
-  if (k <= 32)
-    k_fact_partial<32><<<t->n_fchunks, 256, 0, st>>>(t->d_fchunks, t->n, k, A0, v0, A1, v1, vec4,
-                                                     partial, t->d_fbegin, cnt, out);
-  else
-    k_fact_partial<64><<<t->n_fchunks, 256, 0, st>>>(t->d_fchunks, t->n, k, A0, v0, A1, v1, vec4,
-                                                     partial, t->d_fbegin, cnt, out);
-}
-
-size_t factored_apply_scratch_bytes(const hm_tree* t, int k) {
-  const size_t nodes = (size_t)1 << (t->L + 1);
-  return sizeof(float) * ((size_t)t->n_fchunks * k + nodes * k) + sizeof(int32_t) * nodes;
-}
-
 size_t factored_scratch_bytes(const hm_tree* t, int k) {
   const size_t nodes = (size_t)1 << (t->L + 1);
-  return sizeof(float) * ((size_t)t->n_fchunks * 2 * k + nodes * 2 * k) +
-         sizeof(int32_t) * nodes + 256;
+  return sizeof(float) * ((size_t)t->n_fchunks * 2 * k + nodes * 2 * k) + 256;
 }
 
 void launch_factored_apply(const hm_tree* t, int k, const float* U, const float* V,
                            const float* D, int trans, const float* x, float* y, float* scratch,
                            cudaStream_t st) {
-  count_launches(2);
+  count_launches(3);
   const int L = t->L;
   const int nodes = 1 << (L + 1);
   float* partial = scratch;
   float* coef = scratch + (size_t)t->n_fchunks * k;
-  int32_t* cnt = fact_counters(t, coef + (size_t)nodes * k, st);
   // t_node = Proj(I_node)^T x with Proj = V (H x) or U (H^T x)
-  const float* P = trans ? U : V;
-  launch_fact_partial(t, k, P, x, nullptr, nullptr, partial, cnt, coef, st);
+  k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, trans ? U : V, x, nullptr,
+                                                nullptr, partial);
+  k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, k, nodes, coef);
   const int nmax = (int)t->nmax;
   const size_t smem = fact_leaf_smem(t, false);
   k_fact_expand<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, k,
@@ -335,13 +274,13 @@ void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const floa
                              const float* D, const float* x, const float* res, float scale,
                              float* gx, float* gU, float* gV, float* gD, float* scratch,
                              cudaStream_t st) {
-  count_launches(2);
+  count_launches(3);
   const int L = t->L;
   const int nodes = 1 << (L + 1);
   float* partial = scratch;
   float* coef = scratch + (size_t)t->n_fchunks * 2 * k;
-  int32_t* cnt = fact_counters(t, coef + (size_t)nodes * 2 * k, st);
-  launch_fact_partial(t, k, V, x, U, res, partial, cnt, coef, st);
+  k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, V, x, U, res, partial);
+  k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, 2 * k, nodes, coef);
   const int nmax = (int)t->nmax;
   const size_t smem = fact_leaf_smem(t, true);
   k_fact_adjoint<<<1 << L, 256, smem, st>>>(t->d_start, t->d_size, L, t->n, k, nmax, U, V, D,
@@ -351,8 +290,7 @@ void launch_factored_adjoint(const hm_tree* t, int k, const float* U, const floa
 
 size_t factored_loss_grad_scratch_bytes(const hm_tree* t, int k) {
   const size_t nodes = (size_t)1 << (t->L + 1);
-  return sizeof(float) * ((size_t)t->n_fchunks * k + 2 * nodes * k + 2 * (size_t)t->n) +
-         sizeof(int32_t) * nodes + 512;
+  return sizeof(float) * ((size_t)t->n_fchunks * k + 2 * nodes * k + 2 * (size_t)t->n) + 512;
 }
 
 // y = H x, res = y - b and the adjoint at res, with every factor read twice: the
@@ -362,7 +300,7 @@ void launch_factored_loss_grad(const hm_tree* t, int k, const float* U, const fl
                                const float* D, const float* x, const float* b, float scale,
                                float* y, float* res, float* gx, float* gU, float* gV, float* gD,
                                float* scratch, cudaStream_t st) {
-  count_launches(4);
+  count_launches(6);
   const int L = t->L;
   const int nodes = 1 << (L + 1);
   const int nmax = (int)t->nmax;
@@ -370,13 +308,16 @@ void launch_factored_loss_grad(const hm_tree* t, int k, const float* U, const fl
   float* coef_t = partial + (size_t)t->n_fchunks * k;
   float* coef_s = coef_t + (size_t)nodes * k;
   float* tmp = coef_s + (size_t)nodes * k;
-  int32_t* cnt = fact_counters(t, tmp + 2 * (size_t)t->n, st);
   float* yy = y ? y : tmp;
   float* rr = res ? res : tmp + t->n;
-  launch_fact_partial(t, k, V, x, nullptr, nullptr, partial, cnt, coef_t, st);
+  k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, V, x,
+                                                                   nullptr, nullptr, partial);
+  k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, k, nodes, coef_t);
   k_fact_expand<<<1 << L, 256, fact_leaf_smem(t, false), st>>>(
       t->d_start, t->d_size, L, t->n, k, nmax, k, U, coef_t, D, 0, x, yy, b, rr);
-  launch_fact_partial(t, k, U, rr, nullptr, nullptr, partial, cnt, coef_s, st);
+  k_fact_partial<<<t->n_fchunks, 256, fact_partial_smem(k), st>>>(t->d_fchunks, t->n, k, U, rr,
+                                                                   nullptr, nullptr, partial);
+  k_fact_reduce<<<nodes - 2, 256, 0, st>>>(partial, t->d_fbegin, k, nodes, coef_s);
   k_fact_adjoint<<<1 << L, 256, fact_leaf_smem(t, true), st>>>(
       t->d_start, t->d_size, L, t->n, k, nmax, U, V, D, coef_t, coef_s, k, x, rr, scale, gx, gU,
       gV, gD);

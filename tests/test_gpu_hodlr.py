@@ -299,42 +299,3 @@ def test_dense_apply_a32():
         assert np.max(np.abs(Y.cpu().numpy().T - want)) <= 1e-13 * np.max(np.abs(want))
 
 
-
-def test_factored_loss_grad_in_cuda_graph():
-    """The fused training step captured in a CUDA graph (stream-ordered scratch
-    and the counter clear become graph nodes) and replayed twice equals the
-    eager call bit for bit."""
-    N, m, k = 4096, 256, 32
-    f = W.synthetic_hodlr_factors(N, m, k, seed=8, shift=0.0, dtype=np.float32)
-    t = hm.Tree(N, m)
-    L = f["L"]
-    U = torch.from_numpy(np.stack([np.ascontiguousarray(f["U"][j].T) for j in range(1, L + 1)])).to(DEV)
-    V = torch.from_numpy(np.stack([np.ascontiguousarray(f["V"][j].T) for j in range(1, L + 1)])).to(DEV)
-    D = torch.from_numpy(np.stack([np.ascontiguousarray(d.T) for d in f["D"]])).to(DEV)
-    g = torch.Generator(device=DEV).manual_seed(3)
-    x = torch.randn(N, device=DEV, generator=g)
-    b = torch.randn(N, device=DEV, generator=g)
-    outs = [torch.empty_like(a) for a in (x, x, x, U, V, D)]  # y, r, gx, gU, gV, gD
-
-    def step():
-        hm.hm_hodlr_factored_loss_grad(t, k, U, V, D, x, b, 2.0, *outs)
-    step()
-    torch.cuda.synchronize()
-    eager = [o.clone() for o in outs]
-    for o in outs:
-        o.fill_(float("nan"))
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        step()
-    torch.cuda.current_stream().wait_stream(side)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        step()
-    for _ in range(2):
-        for o in outs:
-            o.fill_(float("nan"))
-        graph.replay()
-        torch.cuda.synchronize()
-        for o, e in zip(outs, eager):
-            assert torch.equal(o, e)
