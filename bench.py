@@ -364,11 +364,15 @@ def batched_bench(hm, torch, dev, count=64):
         ops.append(hm.hm_dense_operator_create(A, fp64_blocks=True, tensor_cores=True))
         trees.append(hm.Tree(N, 64))
         opts.append(dict(k=k, p=10, seed=sp["omega_seed"], prec=hm.HM_A32))
-    hs = hm.hm_compress_batched(ops, trees, "hodlr", opts)  # warm-up (operator scales, plans)
+    # the concurrency (streams of the level-synchronous batch) picked by the
+    # library's autotuner from timed runs of this batch; the handles do not depend on it
+    cands = (4, 8, 16)
+    best, tune_ms = hm.hm_tune_batched(ops, trees, "hodlr", opts, candidates=cands)
+    hs = hm.hm_compress_batched(ops, trees, "hodlr", opts, max_concurrency=best)  # warm-up
     del hs
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hs = hm.hm_compress_batched(ops, trees, "hodlr", opts)
+    hs = hm.hm_compress_batched(ops, trees, "hodlr", opts, max_concurrency=best)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3
     errs = []
@@ -384,6 +388,8 @@ def batched_bench(hm, torch, dev, count=64):
     return {"ops": count, "ms": round(ms, 2), "compressions_per_s": round(count / (ms * 1e-3), 2),
             "n_range": [min(ns), max(ns)], "k_range": [min(sp["k"] for sp in specs), max(sp["k"] for sp in specs)],
             "max_estimate_E": max(errs), "precision": "HM_A32",
+            "autotune": {"candidates": list(cands), "ms": tune_ms, "chosen": best,
+                         "by": "hm_tune_batched (one timed batch per candidate concurrency)"},
             "note": "host wall time of one hm_compress_batched call (all operators resident)"}
 
 

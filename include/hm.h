@@ -272,18 +272,38 @@ hm_status hm_compress_hbs(const hm_operator* op, const hm_tree* tree, const hm_o
  * (each the problem of Sec. 1 on its own): operator i with trees[i] and
  * opts[i] is compressed exactly as hm_compress_hodlr (format HM_FORMAT_HODLR)
  * or hm_compress_hbs (format HM_FORMAT_HBSID) would, and outs[i] receives its
- * handle.  The operators run concurrently, each on an internal stream, from up
- * to max_concurrency host threads (0: 8); their black boxes are therefore
- * called from several threads at once and must allow it (the dense operators
- * of this library do, one operator per entry).  The internal streams start
- * after the work already queued on `stream`; all work is complete when the call
- * returns.  Trees may be shared between operators.  On the first failure every
- * handle of the call is destroyed, outs[] is set to NULL and the error names
- * the operator.
+ * handle, equal bit for bit to the one-call result.  HODLR: level by level from
+ * the calling thread (the loop over the boxes of a level in the HODLR figure of
+ * Sec. 3 taken across operators): each level's black-box products and peels
+ * run per operator on max_concurrency internal streams (0: 8), and each TSQR
+ * round and the panel SVD of the level run as one launch over the nodes of
+ * every HM_A32 operator.  HBS-ID: one hm_compress_hbs per operator, from up to
+ * max_concurrency host threads (0: 8), so the black boxes are called from
+ * several threads at once and must allow it (the dense operators of this
+ * library do, one operator per entry).  The internal streams start after the
+ * work already queued on `stream`; all work is complete when the call returns.
+ * Trees may be shared between operators.  On the first failure every handle of
+ * the call is destroyed, outs[] is set to NULL and the error names the
+ * operator.
  */
 hm_status hm_compress_batched(int32_t nops, const hm_operator* ops, hm_tree* const* trees,
                               const hm_opts* opts, int32_t format, int32_t max_concurrency,
                               void* stream, hm_handle** outs);
+
+/*
+ * Autotuner of hm_compress_batched's concurrency (no counterpart in the paper:
+ * a launch schedule, not a step of the method).  The handles of a batch do
+ * not depend on max_concurrency (the same kernels on the same nodes), only its
+ * time does, and the best value depends on the batch (operator sizes, ranks,
+ * depths) and on the device.  Runs the batch once to warm up, then once per
+ * candidate (candidates[0 .. ncand-1], each >= 1), timing each call on the host
+ * from a synchronized start to its return, destroys the handles, and writes
+ * the fastest candidate to *best and the time of each candidate in ms to
+ * ms_out[0 .. ncand-1] (ms_out may be NULL).  Errors as hm_compress_batched.
+ */
+hm_status hm_tune_batched(int32_t nops, const hm_operator* ops, hm_tree* const* trees,
+                          const hm_opts* opts, int32_t format, const int32_t* candidates,
+                          int32_t ncand, void* stream, int32_t* best, double* ms_out);
 
 /* ---------------------------------------------------------- using it ----- */
 

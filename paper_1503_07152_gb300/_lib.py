@@ -63,6 +63,9 @@ _sig = {
     "hm_compress_hbs": ([C.POINTER(_Operator), _P, C.POINTER(Opts), _P, C.POINTER(_P)], C.c_int),
     "hm_compress_batched": ([C.c_int32, C.POINTER(_Operator), C.POINTER(_P), C.POINTER(Opts), C.c_int32,
                              C.c_int32, _P, C.POINTER(_P)], C.c_int),
+    "hm_tune_batched": ([C.c_int32, C.POINTER(_Operator), C.POINTER(_P), C.POINTER(Opts), C.c_int32,
+                         C.POINTER(C.c_int32), C.c_int32, _P, C.POINTER(C.c_int32),
+                         C.POINTER(C.c_double)], C.c_int),
     "hm_apply": ([_P, C.c_int, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
     "hm_apply_host": ([_P, C.c_int, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
     "hm_reconstruct_block": ([_P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int64, _P], C.c_int),
@@ -313,6 +316,26 @@ def hm_compress_batched(ops: list, trees: list, fmt: str = "hodlr", opts: list |
     _check(lib.hm_compress_batched(n, ops_arr, trees_arr, opts_arr, fmt_id, max_concurrency,
                                    C.c_void_p(_stream(stream)), outs), "hm_compress_batched")
     return [Handle(C.c_void_p(outs[i]), keep=(trees[i], ops[i])) for i in range(n)]
+
+
+def hm_tune_batched(ops: list, trees: list, fmt: str = "hodlr", opts: list | None = None,
+                    candidates=(2, 4, 8, 16), stream=None) -> tuple:
+    """Times hm_compress_batched once per candidate concurrency (after one warm-up
+    call); returns (best, {candidate: ms})."""
+    n = len(ops)
+    if len(trees) != n or (opts is not None and len(opts) != n):
+        raise ValueError("ops, trees and opts must have the same length")
+    opts = opts or [{} for _ in range(n)]
+    ops_arr = (_Operator * n)(*[o.op for o in ops])
+    trees_arr = (_P * n)(*[t.ptr for t in trees])
+    opts_arr = (Opts * n)(*[_opts(**kw) for kw in opts])
+    cand = (C.c_int32 * len(candidates))(*candidates)
+    ms = (C.c_double * len(candidates))()
+    best = C.c_int32()
+    fmt_id = {"hodlr": HM_FORMAT_HODLR, "hbsid": HM_FORMAT_HBSID}[fmt]
+    _check(lib.hm_tune_batched(n, ops_arr, trees_arr, opts_arr, fmt_id, cand, len(candidates),
+                               C.c_void_p(_stream(stream)), C.byref(best), ms), "hm_tune_batched")
+    return best.value, {int(c): float(m) for c, m in zip(candidates, ms)}
 
 
 def hm_apply(h: Handle, trans: int, X: torch.Tensor, Y: torch.Tensor, stream=None) -> None:

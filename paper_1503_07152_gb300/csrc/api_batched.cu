@@ -12,6 +12,7 @@
 // HBS-ID runs the one-operator path concurrently from a pool of host threads.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <memory>
 #include <string>
 #include <thread>
@@ -329,5 +330,46 @@ extern "C" hm_status hm_compress_batched(int32_t nops, const hm_operator* ops,
       set_error("hm_compress_batched: operator " + std::to_string(i) + ": " + msg[i]);
       return status[i];
     }
+  return HM_OK;
+}
+
+extern "C" hm_status hm_tune_batched(int32_t nops, const hm_operator* ops, hm_tree* const* trees,
+                                     const hm_opts* opts, int32_t format,
+                                     const int32_t* candidates, int32_t ncand, void* stream,
+                                     int32_t* best, double* ms_out) {
+  clear_error();
+  if (nops < 1 || !candidates || ncand < 1 || !best) {
+    set_error("hm_tune_batched: need nops >= 1, candidates, ncand >= 1 and best");
+    return HM_EINVAL;
+  }
+  for (int32_t c = 0; c < ncand; ++c)
+    if (candidates[c] < 1) {
+      set_error("hm_tune_batched: every candidate must be >= 1");
+      return HM_EINVAL;
+    }
+  std::vector<hm_handle*> outs((size_t)nops, nullptr);
+  auto run = [&](int32_t conc, double* ms) -> hm_status {
+    HM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    HM_TRY(hm_compress_batched(nops, ops, trees, opts, format, conc, stream, outs.data()));
+    const auto t1 = std::chrono::steady_clock::now();
+    for (hm_handle*& h : outs) {
+      hm_destroy(h);
+      h = nullptr;
+    }
+    if (ms) *ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    return HM_OK;
+  };
+  HM_TRY(run(candidates[0], nullptr));  // warm-up: operator scales, plans, scratch
+  double best_ms = 0.0;
+  for (int32_t c = 0; c < ncand; ++c) {
+    double ms = 0.0;
+    HM_TRY(run(candidates[c], &ms));
+    if (ms_out) ms_out[c] = ms;
+    if (c == 0 || ms < best_ms) {
+      best_ms = ms;
+      *best = candidates[c];
+    }
+  }
   return HM_OK;
 }

@@ -147,3 +147,28 @@ def test_batched_a32_level_wide_launches_equal_one_call():
         assert hs[i].info["max_rank"] == ones[i].info["max_rank"], i
         nA = float(A.double().norm())
         assert float((Rb.T - A.double()).norm()) / nA < 1e-6, i
+
+
+def test_tune_batched_concurrency():
+    """hm_tune_batched times the batch once per candidate concurrency and picks
+    the fastest; the handles do not depend on the concurrency, so a batch run
+    at the chosen value and at another one give the same matrices bit for bit."""
+    m = 64
+    ops, trees, opts, keep = [], [], [], []
+    for i, (N, k) in enumerate(SPECS):
+        A = torch.from_numpy(W.dense_from_factors(W.synthetic_hodlr_factors(
+            N, m, k, seed=1000 + i, shift=float(N))).astype(np.float32)).to(DEV)
+        keep.append(A)
+        ops.append(hm.hm_dense_operator_create(A, fp64_blocks=True, tensor_cores=True))
+        trees.append(hm.Tree(N, m))
+        opts.append(dict(k=k, p=10, seed=2000 + i, prec=hm.HM_A32))
+    best, ms = hm.hm_tune_batched(ops, trees, "hodlr", opts, candidates=(1, 2, 4))
+    assert best in (1, 2, 4) and set(ms) == {1, 2, 4}
+    assert all(v > 0.0 for v in ms.values()) and ms[best] == min(ms.values())
+    other = 1 if best != 1 else 4
+    hb = hm.hm_compress_batched(ops, trees, "hodlr", opts, max_concurrency=best)
+    ho = hm.hm_compress_batched(ops, trees, "hodlr", opts, max_concurrency=other)
+    for i, (N, _) in enumerate(SPECS):
+        assert torch.equal(dense_of(hb[i], N), dense_of(ho[i], N)), i
+    with pytest.raises(hm.HmError):
+        hm.hm_tune_batched(ops, trees, "hodlr", opts, candidates=(0,))
