@@ -56,6 +56,11 @@ def test_argument_errors_before_device_use():
     with pytest.raises(hm.HmError):
         hm.hm_compress_hodlr(op, t, tol=2.0, r=8, stream=0)
     assert hm.hm_version().startswith("hm")
+    # the batch autotuner checks its candidates before running anything
+    for cands in [(0,), (4, -1), ()]:
+        with pytest.raises(hm.HmError) as e:
+            hm.hm_tune_batched([op], [t], "hodlr", [dict(k=4, p=2)], candidates=cands, stream=0)
+        assert e.value.status == 1
 
 
 def test_load_rejects_garbage_without_a_device(tmp_path):
