@@ -132,29 +132,62 @@ void la_end(Ctx<T>& c) {
   c.la = false;
   c.la_pending = -1;
   c.la_part = 0;
+  c.la_cur = -1;
+  c.probe_next = 0;
+}
+
+// The identity probe's product in pieces of kProbeCols columns (one column
+// tile of the sampling GEMM each), so that the look-ahead stream can place them
+// in the coarse levels' idle windows; the in-order path takes the same pieces,
+// so both give the same products.
+constexpr int64_t kProbeCols = 64;
+
+template <typename T>
+static int probe_pieces(const Ctx<T>& c) {
+  return (int)((c.tree->nmax + kProbeCols - 1) / kProbeCols);
 }
 
 template <typename T>
-hm_status la_release(Ctx<T>& c, int part) {
-  if (!c.la || c.la_pending < 0) return HM_OK;
+static hm_status probe_piece(Ctx<T>& c, int j, bool ahead) {
+  const int64_t c0 = j * kProbeCols;
+  const int64_t w = std::min<int64_t>(kProbeCols, c.tree->nmax - c0);
+  return box(c, 0, c.XI + c.N * c0, c.YI + c.N * c0, w, ahead);
+}
+
+// Look-ahead stream: the next pieces of the identity probe (count of them,
+// all that remain if count < 0) after the work enqueued on c.st so far.
+template <typename T>
+static hm_status la_probe(Ctx<T>& c, int count) {
+  const int np = probe_pieces(c);
+  if (c.probe_next >= np || count == 0) return HM_OK;
+  HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));
+  HM_CUDA_TRY(cudaStreamWaitEvent(c.la_st, c.ev_free, 0));
+  if (c.probe_next == 0)
+    launch_identity_probe<T>(c.XI, c.N, c.N, (int)c.tree->nmax, c.tree->d_start, c.tree->L,
+                             c.la_st);
+  for (int k = 0; c.probe_next < np && (count < 0 || k < count); ++k)
+    HM_TRY(probe_piece(c, c.probe_next++, true));
+  if (c.probe_next == np) {
+    HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
+    c.probe_issued = true;
+  }
+  return HM_OK;
+}
+
+// Look-ahead stream: the pending level's test matrix and first half-operator
+// product (part 0), its second half (part 1), or whatever of them is pending
+// (part 2), after the work enqueued on c.st so far.
+template <typename T>
+static hm_status la_halves(Ctx<T>& c, int part) {
+  if (c.la_pending < 0) return HM_OK;
   const int64_t N = c.N;
   const int r = c.r;
   const int L = c.tree->L;
   const int lv = c.la_pending;
-  // a level's two half-operator products go out one per side of the current
-  // level (each fits beside one side's merges and SVD); the probe goes out whole
   if (c.la_part == 0 && (part == 0 || part == 2)) {
     // c.st has enqueued everything before this point, the last use of Xa, Sa included
     HM_CUDA_TRY(cudaEventRecord(c.ev_free, c.st));
     HM_CUDA_TRY(cudaStreamWaitEvent(c.la_st, c.ev_free, 0));
-    if (lv == L) {  // the identity probe (XI, YI: buffers of its own)
-      launch_identity_probe<T>(c.XI, N, N, (int)c.tree->nmax, c.tree->d_start, L, c.la_st);
-      HM_TRY(box(c, 0, c.XI, c.YI, c.tree->nmax, true));
-      HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
-      c.probe_issued = true;
-      c.la_pending = -1;
-      return HM_OK;
-    }
     launch_gauss_fill<T>(c.Xa, N, N, r, lv, c.seed, c.bf16, c.tree->d_start, L, c.la_st);
     HM_TRY(box(c, 0, c.Xa, c.Sa, r, true));  // Y_1 = A Omega_2
     c.la_part = 1;
@@ -171,6 +204,20 @@ hm_status la_release(Ctx<T>& c, int part) {
 }
 
 template <typename T>
+hm_status la_release(Ctx<T>& c, int side) {
+  if (!c.la) return HM_OK;
+  // a level's two half-operator products go out one per side of the current
+  // level (each fits beside one side's merges and SVD)
+  HM_TRY(la_halves(c, side));
+  // the identity probe: one piece per side from level 1 on (the coarse levels'
+  // windows have room beside the half-operator products), what is left at the
+  // last level's A side
+  if (side == 0 && c.la_cur == c.tree->L - 1) return la_probe(c, -1);
+  if (c.la_cur >= 1) return la_probe(c, 1);
+  return HM_OK;
+}
+
+template <typename T>
 hm_status sample_level(Ctx<T>& c, int level) {
   const int64_t N = c.N;
   const int r = c.r;
@@ -181,11 +228,12 @@ hm_status sample_level(Ctx<T>& c, int level) {
     HM_TRY(box(c, 0, c.X + N * r, c.S + N * r, r));  // Y_2 = A Omega_1
   } else {
     if (level == 0) c.la_pending = 0;
-    HM_TRY(la_release(c, 2));  // level 0, or release points that were not reached
+    HM_TRY(la_halves(c, 2));  // level 0, or release points that were not reached
     HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_ready, 0));
     std::swap(c.X, c.Xa);
     std::swap(c.S, c.Sa);
-    c.la_pending = level + 1;  // released from panel_qr (level + 1 == L: the probe)
+    c.la_cur = level;
+    c.la_pending = level + 1 < L ? level + 1 : -1;  // released from panel_qr
   }
   nonfinite_check_launch(c.S, N * 2 * r, sizeof(T) == 8, c.flags_dev, c.st);
   return HM_OK;
@@ -193,13 +241,14 @@ hm_status sample_level(Ctx<T>& c, int level) {
 
 template <typename T>
 hm_status sample_identity(Ctx<T>& c) {
-  HM_TRY(la_release(c, 2));
-  if (c.la && c.probe_issued) {
+  if (c.la) {
+    HM_TRY(la_probe(c, -1));
     HM_CUDA_TRY(cudaStreamWaitEvent(c.st, c.ev_probe, 0));
     return HM_OK;
   }
   launch_identity_probe<T>(c.XI, c.N, c.N, (int)c.tree->nmax, c.tree->d_start, c.tree->L, c.st);
-  return box(c, 0, c.XI, c.YI, c.tree->nmax);
+  for (int j = 0; j < probe_pieces(c); ++j) HM_TRY(probe_piece(c, j, false));
+  return HM_OK;
 }
 
 // S(:, 0:ncols) -= A^(level) X (or the transpose), node levels 1..level.

@@ -50,18 +50,20 @@ struct Ctx {
   // the first TSQR round of the current level's A-side panel, the last wide
   // launch before the per-node phases that leave most SMs idle; its second
   // half-operator product once st has launched the first TSQR round of the
-  // A^T-side panel.  ev_ready: the
-  // look-ahead samples are written; ev_free: st has reached a release point
-  // (and is done with the buffers the look-ahead overwrites); ev_probe: the
-  // identity probe's samples are written.  la_pending: the level whose samples
-  // are released next (L: the identity probe; -1: none); la_part: how many of
-  // its two halves are out.
+  // A^T-side panel.  The identity probe's product goes out in 64-column pieces,
+  // one per release point from level 1 on.  ev_ready: the look-ahead samples
+  // are written; ev_free: st has reached a release point (and is done with the
+  // buffers the look-ahead overwrites); ev_probe: the identity probe's samples
+  // are written.  la_pending: the level whose samples are released next (-1:
+  // none); la_part: how many of its two halves are out.
   bool la = false;
   cudaStream_t user_st = nullptr, la_st = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_free = nullptr, ev_probe = nullptr;
   T *Xa = nullptr, *Sa = nullptr;
   bool probe_issued = false;
   int la_pending = -1, la_part = 0;
+  int la_cur = -1;      // the level whose panels c.st is factoring
+  int probe_next = 0;   // the next identity-probe piece to release
 };
 
 // Records the start of a phase on the compression's stream (no-op unless
@@ -99,12 +101,13 @@ hm_status sample_level(Ctx<T>& c, int level);
 // Leaves the identity probe in c.XI and A XI in c.YI on c.st.
 template <typename T>
 hm_status sample_identity(Ctx<T>& c);
-// Starts pending look-ahead products on la_st after the work enqueued on c.st
-// so far: part 0 the test matrix and the first half-operator product (or the
-// whole identity probe), part 1 the second half, part 2 whatever is pending
-// (no-op without look-ahead or when nothing is pending).
+// Release point of the look-ahead stream, reached when c.st has launched the
+// first TSQR round of the current level's `side` panel: the pending level's
+// half-operator product of that side and, from level 1 on, the next piece of
+// the identity probe (all that is left at the last level's A side) start on
+// la_st after the work enqueued on c.st so far (no-op without look-ahead).
 template <typename T>
-hm_status la_release(Ctx<T>& c, int part);
+hm_status la_release(Ctx<T>& c, int side);
 template <typename T>
 hm_status panel_svd(Ctx<T>& c, int lv, const T* P, int pc, int mode, int kfix, bool set_eps,
                     T* Q, bool want_m, int32_t* rank_lv);
