@@ -153,9 +153,9 @@ hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* 
  * the tensor cores (three-way BF16 split, FP32 accumulation drained into
  * compensated FP32 sums); 2: float matrix, double blocks with FP64 products and
  * sums (HM_A32); 3: as 1 on the CUDA cores (FP32 FMA, compensated sums); 4: as 2
- * on the tensor cores: rows of A (whole rows) and columns of X (per 256-row
- * window) are cut into four 8-bit integer BF16 slices under a power-of-two
- * scale, the products of each order are summed exactly in FP32 accumulators
+ * on the tensor cores: rows of A (per 256-wide window of columns) and columns
+ * of X (per 256-row window) are cut into four 8-bit integer BF16 slices under a
+ * power-of-two scale, the products of each order are summed exactly in FP32 accumulators
  * over 256-wide K windows, orders above 5 are
  * dropped (relative weight <= 2^-32), and the window sums are added in FP32
  * double-float; results whose magnitude exceeds the FP32 range are not
@@ -167,7 +167,13 @@ hm_status hm_tree_node(const hm_tree* t, int64_t node, int64_t* start, int64_t* 
  * grow a device workspace (the BF16 split of X) on first use of a larger block
  * and need a 16-byte aligned A with lda % 4 == 0 and n >= 128 (TMA); other
  * layouts run on the CUDA cores (dtype 3, resp. 2).  The returned operator's ctx is released by
- * hm_dense_operator_destroy.
+ * hm_dense_operator_destroy.  Per-call scratch (zero-tile flags, the split of
+ * X) comes in two sets: one for calls through the callback or hm_dense_apply,
+ * one for a compression's look-ahead stream (hm_opts.lookahead), so one
+ * compression may have a product of each kind in flight.  Calls that use the
+ * same set and may overlap on the GPU (one operator applied from two streams,
+ * or compressed by two calls at once) race on it: give each concurrent user an
+ * operator of its own.
  */
 hm_status hm_dense_operator_create(const void* A, int64_t n, int64_t lda, int32_t dtype,
                                    hm_operator* out);
