@@ -45,7 +45,7 @@ typedef enum {
   HM_ERANK_SATURATED = 5,  /* strict mode only: an adaptive rank reached r */
   HM_ENONFINITE = 6,       /* NaN/Inf detected in the samples */
   HM_ETIMEOUT = 7,         /* a bounded device-side wait gave up */
-  HM_EUNSUPPORTED = 8      /* valid request outside what this build supports */
+  HM_EUNSUPPORTED = 8      /* valid request outside what this library version supports */
 } hm_status;
 
 /* HM_FP64: FP64 operator and pipeline.  HM_MIXED: FP32 samples, bases and
@@ -446,7 +446,7 @@ void hm_product_operator_destroy(hm_operator* op);
  * infos of the loaded handle equal the saved one's bit for bit).  Solver
  * factors are not stored: call hm_hodlr_factorize after loading.  hm_load
  * returns HM_EINVAL for a file that is not a complete, uncorrupted checkpoint.
- * The format is this build's: native byte order and struct layout.
+ * The format is this library version's: native byte order and struct layout.
  */
 hm_status hm_save(const hm_handle* h, const char* path);
 hm_status hm_load(const char* path, void* stream, hm_handle** out);

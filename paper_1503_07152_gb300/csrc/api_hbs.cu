@@ -615,7 +615,7 @@ extern "C" hm_status hm_compress_hbs(const hm_operator* op, const hm_tree* tree,
     return HM_EINVAL;
   }
   if (!opts->hbs_id) {
-    set_error("hm_compress_hbs: this build returns HBS-ID handles (set hbs_id = 1)");
+    set_error("hm_compress_hbs: this library returns HBS-ID handles only (set hbs_id = 1)");
     return HM_EUNSUPPORTED;
   }
   *out = nullptr;
