@@ -310,7 +310,7 @@ def adjoint_bench(hm, torch, dev, steps, warmup):
             step()
         torch.cuda.current_stream().wait_stream(side)
         graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
+        with torch.cuda.graph(graph, capture_error_mode="thread_local"):
             step()
         for _ in range(warmup):
             graph.replay()
