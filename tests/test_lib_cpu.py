@@ -73,3 +73,22 @@ def test_load_rejects_garbage_without_a_device(tmp_path):
     with pytest.raises(hm.HmError) as e:
         hm.hm_load(str(tmp_path / "missing.hm"), stream=0)
     assert e.value.status == 1
+
+
+def test_factored_and_operator_arguments_checked_before_device_use():
+    """The factored applies and the operator constructors reject bad arguments
+    (HM_EINVAL) before any device call, as include/hm.h states."""
+    t = hm.Tree(1024, 64)
+    for k in (0, 65):
+        for fn in (hm.hm_hodlr_factored_apply, hm.hm_hodlr_factored_apply_noalloc):
+            with pytest.raises(hm.HmError) as e:
+                fn(t, k, None, None, None, None, None, stream=0)
+            assert e.value.status == 1
+    with pytest.raises(hm.HmError) as e:  # null factors
+        hm.hm_hodlr_factored_apply(t, 8, None, None, None, None, None, stream=0)
+    assert e.value.status == 1
+    for n in (1, 524289):
+        with pytest.raises(hm.HmError) as e:
+            hm.hm_log_kernel_operator_create(n)
+        assert e.value.status == 1
+    assert hm.hm_compress_batched([], [], "hodlr", stream=0) == []
