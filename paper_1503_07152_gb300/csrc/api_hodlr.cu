@@ -167,10 +167,7 @@ static hm_status la_probe(Ctx<T>& c, int count) {
                              c.la_st);
   for (int k = 0; c.probe_next < np && (count < 0 || k < count); ++k)
     HM_TRY(probe_piece(c, c.probe_next++, true));
-  if (c.probe_next == np) {
-    HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
-    c.probe_issued = true;
-  }
+  if (c.probe_next == np) HM_CUDA_TRY(cudaEventRecord(c.ev_probe, c.la_st));
   return HM_OK;
 }
 

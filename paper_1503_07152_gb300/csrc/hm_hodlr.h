@@ -60,7 +60,6 @@ struct Ctx {
   cudaStream_t user_st = nullptr, la_st = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_free = nullptr, ev_probe = nullptr;
   T *Xa = nullptr, *Sa = nullptr;
-  bool probe_issued = false;
   int la_pending = -1, la_part = 0;
   int la_cur = -1;      // the level whose panels c.st is factoring
   int probe_next = 0;   // the next identity-probe piece to release
